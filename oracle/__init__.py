@@ -1,0 +1,180 @@
+"""CPU oracle for the sparse UCC path (test infrastructure only).
+
+Only the tests, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline
+leg may import this package.  It shares no code with the CUDA library in
+``paper_2301_05726_gb300``; the two meet only through the seeded inputs of
+``paper_2301_05726_gb300.synth`` (which holds none of the method's
+arithmetic).
+
+``ucc_oracle.cpp`` is the sparse reference (Eq. 3 factor by factor on a
+``std::unordered_map``, Slater-Condon energy, checkpointed adjoint);
+``dense.py`` is an independent state-vector brute force used to pin it.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ucc_oracle.cpp")
+_LIB_PATH = os.path.join(_HERE, "libucc_oracle.so")
+_lib = None
+_lock = threading.Lock()
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with g++ (no fused multiply-add contraction)."""
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-shared", "-fPIC",
+                               "-o", tmp, _SRC])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class _Counts(ctypes.Structure):
+    _fields_ = [("rotations", ctypes.c_longlong), ("created", ctypes.c_longlong),
+                ("dropped_new", ctypes.c_longlong), ("dropped_old", ctypes.c_longlong),
+                ("cut", ctypes.c_longlong)]
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(build())
+        vp, dp, ip, u64p = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), \
+            ctypes.POINTER(ctypes.c_uint64)
+        lib.orc_problem_new.restype = vp
+        lib.orc_problem_new.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_int, ip]
+        lib.orc_problem_free.argtypes = [vp]
+        lib.orc_apply.restype = vp
+        lib.orc_apply.argtypes = [vp, dp, ctypes.c_int, ctypes.c_double, ctypes.c_longlong, ctypes.c_longlong,
+                                  ctypes.POINTER(_Counts)]
+        lib.orc_wf_from_arrays.restype = vp
+        lib.orc_wf_from_arrays.argtypes = [ctypes.c_longlong, u64p, dp]
+        lib.orc_wf_size.restype = ctypes.c_longlong
+        lib.orc_wf_size.argtypes = [vp]
+        lib.orc_wf_export.argtypes = [vp, u64p, dp]
+        lib.orc_wf_free.argtypes = [vp]
+        lib.orc_sigma.argtypes = [vp, vp, ctypes.c_int, dp]
+        lib.orc_energy.argtypes = [vp, vp, ctypes.c_int, dp, dp]
+        lib.orc_sigma_at.argtypes = [vp, vp, ctypes.c_longlong, u64p, dp]
+        lib.orc_hmat.restype = ctypes.c_double
+        lib.orc_hmat.argtypes = [vp, ctypes.c_uint64, ctypes.c_uint64]
+        lib.orc_tau.restype = ctypes.c_int
+        lib.orc_tau.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, u64p]
+        lib.orc_gradient.argtypes = [vp, dp, ctypes.c_double, ctypes.c_longlong, ctypes.c_longlong, ctypes.c_int,
+                                     dp, dp]
+        _lib = lib
+        return lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+class Oracle:
+    """One problem loaded into the oracle (integrals + factor list)."""
+
+    def __init__(self, prob):
+        self.lib = _load()
+        self.prob = prob
+        self._h = np.ascontiguousarray(prob.h, dtype=np.float64)
+        self._g = np.ascontiguousarray(prob.g, dtype=np.float64)
+        self._exc = np.ascontiguousarray(prob.exc, dtype=np.int32)
+        self.handle = self.lib.orc_problem_new(
+            prob.n_spatial, prob.n_alpha, prob.n_beta, _dp(self._h), _dp(self._g), int(self._exc.shape[0]),
+            self._exc.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            self.lib.orc_problem_free(h)
+            self.handle = None
+
+    def _theta(self, theta):
+        t = self.prob.theta if theta is None else theta
+        return np.ascontiguousarray(t, dtype=np.float64)
+
+    def apply(self, theta=None, eps=None, n_factors=None, n_max=0, n_cut=0):
+        """Eq. 3 on the reference with the eps rule.  Returns (keys, amps, counts)
+        sorted by key; counts has rotations/created/dropped_new/dropped_old/cut."""
+        th = self._theta(theta)
+        eps = self.prob.eps if eps is None else eps
+        nf = len(th) if n_factors is None else int(n_factors)
+        cnt = _Counts()
+        wf = self.lib.orc_apply(self.handle, _dp(th), nf, float(eps), int(n_max), int(n_cut), ctypes.byref(cnt))
+        keys, amps = _export(self.lib, wf)
+        self.lib.orc_wf_free(wf)
+        counts = {f: getattr(cnt, f) for f, _ in _Counts._fields_}
+        return keys, amps, counts
+
+    def _wf(self, keys, amps):
+        keys = np.ascontiguousarray(keys, dtype=np.uint64)
+        amps = np.ascontiguousarray(amps, dtype=np.float64)
+        return self.lib.orc_wf_from_arrays(len(keys), keys.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                           _dp(amps))
+
+    def energy(self, keys, amps, route="lookup"):
+        """(E, <psi|psi>) of the map keys -> amps; route 'lookup' or 'pairwise'."""
+        wf = self._wf(keys, amps)
+        E, n2 = ctypes.c_double(), ctypes.c_double()
+        self.lib.orc_energy(self.handle, wf, 1 if route == "pairwise" else 0, ctypes.byref(E), ctypes.byref(n2))
+        self.lib.orc_wf_free(wf)
+        return E.value, n2.value
+
+    def sigma(self, keys, amps, route="lookup"):
+        """sigma_I = sum_J <I|H|J> c_J over the map, in sorted-key order."""
+        wf = self._wf(keys, amps)
+        n = self.lib.orc_wf_size(wf)
+        sk, _ = _export(self.lib, wf)
+        out = np.zeros(n)
+        self.lib.orc_sigma(self.handle, wf, 1 if route == "pairwise" else 0, _dp(out))
+        self.lib.orc_wf_free(wf)
+        return sk, out
+
+    def sigma_at(self, keys, amps, query):
+        """sigma at the given determinants only (one by one)."""
+        wf = self._wf(keys, amps)
+        q = np.ascontiguousarray(query, dtype=np.uint64)
+        out = np.zeros(len(q))
+        self.lib.orc_sigma_at(self.handle, wf, len(q), q.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), _dp(out))
+        self.lib.orc_wf_free(wf)
+        return out
+
+    def hmat(self, I, J):
+        return self.lib.orc_hmat(self.handle, int(I), int(J))
+
+    def tau(self, k, det, dagger=False):
+        out = ctypes.c_uint64()
+        s = self.lib.orc_tau(self.handle, int(k), 1 if dagger else 0, int(det), ctypes.byref(out))
+        return (s, out.value) if s else (0, None)
+
+    def run_energy(self, theta=None, eps=None, n_factors=None, n_max=0, n_cut=0):
+        keys, amps, _ = self.apply(theta, eps, n_factors, n_max, n_cut)
+        return self.energy(keys, amps)[0]
+
+    def gradient(self, theta=None, eps=None, stride=0, n_max=0, n_cut=0):
+        """(E, dE/dtheta) by the checkpointed adjoint sweep (stride 0 = ceil(sqrt K))."""
+        th = self._theta(theta)
+        eps = self.prob.eps if eps is None else eps
+        g = np.zeros(len(th))
+        E = ctypes.c_double()
+        self.lib.orc_gradient(self.handle, _dp(th), float(eps), int(n_max), int(n_cut), int(stride),
+                              ctypes.byref(E), _dp(g))
+        return E.value, g
+
+
+def _export(lib, wf):
+    n = lib.orc_wf_size(wf)
+    keys = np.zeros(n, dtype=np.uint64)
+    amps = np.zeros(n, dtype=np.float64)
+    if n:
+        lib.orc_wf_export(wf, keys.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), _dp(amps))
+    return keys, amps
