@@ -1,0 +1,312 @@
+"""Benchmark of the sparse-wavefunction UCC hot path on one GB300.
+
+A step is one full evaluation on the 64-spin-orbital workload: the ordered
+product of UCC factors applied to the reference with eps pruning (Eq. 3,
+Methods section), E = <psi|H|psi>/<psi|psi>, and dE/dtheta for every factor
+by the adjoint sweep.  The JSON line reports
+
+  value  = forward det-rotations per second of full-evaluation time (each
+           linked determinant pair rotated by one factor is one det-rotation;
+           the count is the oracle's and the kernel's, which agree exactly),
+  e2e    = the same metric through the public C-ABI call with host buffers
+           (theta uploaded from pinned host memory, E and dE/dtheta read back
+           every step),
+  evals_per_s, apply-only det-rotations/s, the roofline of the dominant kernel,
+  clocks sampled during the timed region, and the CPU oracle timed on a
+  bounded prefix of the same workload (cpu_baseline).
+
+``--impl reference`` times the CPU oracle (the repository's plain reference
+implementation; the paper ships no code) on a bounded prefix sample of the same
+workload and prints the same metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "UCC det-rotations/s; energy+adjoint-gradient evals/s at 64 qubits vs plain"
+UNIT = "det-rotations/s"
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="cfg4", help="cfg4 (default) or cfgN[:prefix] for exploration")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
+    return ap.parse_args()
+
+
+def workload(spec):
+    from paper_2301_05726_gb300 import synth
+    name, _, pre = spec.partition(":")
+    cfg = int(name.replace("cfg", ""))
+    prob = synth.config_problem(cfg)
+    if pre:
+        prob = prob.prefix(int(pre))
+    return prob
+
+
+def peaks():
+    try:
+        with open(PEAKS_PATH) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_sample(prob, seconds, with_grad=True):
+    """Time the CPU oracle on a prefix of the workload sized to ~`seconds`.
+    Returns (forward rotations per eval second, evals/s, description, prefix)."""
+    import oracle
+    o = oracle.Oracle(prob)
+    pre = 16
+    best = None
+    while True:
+        sub = prob.prefix(min(pre, prob.n_exc))
+        os_ = oracle.Oracle(sub)
+        t0 = time.perf_counter()
+        _, _, cnt = os_.apply()
+        E, g = os_.gradient() if with_grad else (None, None)
+        dt = time.perf_counter() - t0
+        best = (cnt["rotations"], dt, sub.n_exc)
+        if dt > seconds / 4 or sub.n_exc >= prob.n_exc:
+            break
+        pre *= 2
+    del o
+    rot, dt, nf = best
+    return rot / dt, 1.0 / dt, nf, dt
+
+
+def run_reference(args, prob):
+    import torch  # noqa: F401  (same environment as the other arm)
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    per_step = max(1.0, 60.0 / max(1, args.steps + args.warmup))
+    rates = []
+    desc = None
+    for s in range(args.warmup + args.steps):
+        r, evals, nf, dt = oracle_sample(prob, per_step * 4)
+        if s >= args.warmup:
+            rates.append(r)
+            desc = f"{prob.name} first {nf} of {prob.n_exc} factors: apply + energy + adjoint, {dt:.1f}s"
+    val = sorted(rates)[len(rates) // 2]
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": prob.name, "n_so": prob.n_so, "n_elec": prob.n_elec, "n_factors": prob.n_exc,
+                       "eps": prob.eps},
+            "cpu_baseline": {"kind": "oracle", "value": val, "unit": UNIT, "cores": 1, "sample": desc},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def flush_l2(buf):
+    buf.add_(1.0)
+
+
+def run_ours(args, prob):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    from paper_2301_05726_gb300 import build
+    if rank == 0 or world == 1:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    from paper_2301_05726_gb300.api import UCCContext
+
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    ctx = UCCContext(prob)
+    flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)  # 256 MB > L2
+    theta_host = torch.tensor(prob.theta, dtype=torch.float64).pin_memory()
+    grad_host = torch.empty(prob.n_exc, dtype=torch.float64).pin_memory()
+    grad_dev = torch.empty(prob.n_exc, dtype=torch.float64, device=dev)
+
+    def step_device():
+        E, _ = ctx.gradient(out=grad_dev)
+        return E
+
+    for _ in range(args.warmup):
+        flush_l2(flush)
+        step_device()
+    torch.cuda.synchronize()
+    st = ctx.stats()
+    rot_per_eval = st["rotations"]
+
+    # Device-timed region: inputs resident, CUDA events on the library's stream.
+    sampler = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    times, launches = [], 0
+    phase = {"apply_ms": 0.0, "energy_ms": 0.0, "reverse_ms": 0.0}
+    for _ in range(args.steps):
+        flush_l2(flush)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        step_device()
+        ev1.record(stream)
+        ev1.synchronize()
+        times.append(ev0.elapsed_time(ev1))
+        s = ctx.stats()
+        launches += s["kernel_launches"]
+        for k in phase:
+            phase[k] += s[k]
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = max(times) if False else sum(times) / len(times)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = rot_per_eval * world / (ms / 1e3)
+
+    # End to end through the public API with host buffers.
+    e2e_times = []
+    for _ in range(max(1, args.steps)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.set_theta(theta_host.numpy())
+        E, g = ctx.gradient()
+        grad_host.copy_(torch.from_numpy(g))
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_ms = 1e3 * sum(e2e_times) / len(e2e_times)
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    st = ctx.stats()
+    hbm, peak_kind = peaks()
+    n_steps = len(times)
+    apply_ms = phase["apply_ms"] / n_steps
+    energy_ms = phase["energy_ms"] / n_steps
+    reverse_ms = phase["reverse_ms"] / n_steps
+    # Dominant kernel's roofline (algorithmic bytes).
+    fwd_bytes = 8.0 * st.get("scanned", 0) + 48.0 * st["rotations"] + 32.0 * st["created"]
+    sig_bytes = 24.0 * st["n_det"] + 16.0 * st.get("sigma_probes", 0) + 8.0 * st.get("sigma_hits", 0)
+    if energy_ms >= apply_ms:
+        dom = {"kernel": "k_sigma", "bound": "hbm", "achieved": sig_bytes / (energy_ms / 1e3) / 1e9,
+               "launch_ms": energy_ms, "launches_per_step": 1}
+    else:
+        nf = max(1, prob.n_exc)
+        dom = {"kernel": "k_forward", "bound": "hbm", "achieved": fwd_bytes / (apply_ms / 1e3) / 1e9,
+               "launch_ms": apply_ms / nf, "launches_per_step": nf}
+    roof = {"bound": dom["bound"], "achieved": dom["achieved"], "peak": hbm, "unit": "GB/s",
+            "frac": dom["achieved"] / hbm, "traffic": None, "kernel": dom["kernel"],
+            "peak_kind": peak_kind, "avg_launch_ms": dom["launch_ms"]}
+    cpu = None
+    if not args.no_cpu_baseline:
+        r, evals, nf, dt = oracle_sample(prob, args.cpu_seconds)
+        cpu = {"value": r, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{prob.name}: first {nf} of {prob.n_exc} factors, apply + energy + adjoint in {dt:.1f}s"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": prob.name, "n_so": prob.n_so, "n_elec": prob.n_elec, "n_factors": prob.n_exc,
+                   "eps": prob.eps, "n_det": st["n_det"], "l2": "inputs larger than L2 + 256 MB flush per step",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "evals_per_s": world * 1e3 / ms,
+        "apply_det_rotations_per_s": st["rotations"] / (apply_ms / 1e3) if apply_ms > 0 else None,
+        "phase_ms": {"apply": apply_ms, "energy": energy_ms, "reverse": reverse_ms},
+        "e2e": {"value": rot_per_eval * world / (e2e_ms / 1e3), "unit": UNIT,
+                "h2d_bytes_per_step": 8 * prob.n_exc, "d2h_bytes_per_step": 8 * prob.n_exc + 8},
+        "gpu_launches": launches,
+        "roofline": roof,
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    prob = workload(args.workload)
+    if args.impl == "reference":
+        run_reference(args, prob)
+    else:
+        run_ours(args, prob)
+
+
+if __name__ == "__main__":
+    main()

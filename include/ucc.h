@@ -1,0 +1,181 @@
+/*
+ * ucc.h - C ABI of the GB300 sparse-wavefunction UCC library (libucc.so).
+ *
+ * The library implements the data-parallel hot path of the sparse
+ * wavefunction circuit simulator of Mullinax & Tubman (arXiv 2301.05726):
+ * the factorised unitary-coupled-cluster state of Eq. 3,
+ *     |psi> = U_K ... U_2 U_1 |Psi_0>,   U_k = exp(theta_k (tau_k - tau_k^+))
+ * (Eqs. 4-5), held as a sparse map from 64-bit determinant bit strings to
+ * FP64 amplitudes, with amplitudes below eps discarded after every factor
+ * (Methods section), the energy <psi|H|psi>/<psi|psi> of the molecular
+ * Hamiltonian built from one- and two-electron integrals (Methods section),
+ * and dE/dtheta for every factor by one reverse (adjoint) sweep.
+ *
+ * Conventions shared by every call:
+ *   - spin-orbital p = 2*spatial + spin (0 = alpha, 1 = beta); bit p of a
+ *     determinant key is the Jordan-Wigner qubit of spin-orbital p; at most
+ *     64 spin-orbitals (the paper's 32-orbital restriction, Methods section);
+ *   - the reference |Psi_0> occupies spatial orbitals 0..n_alpha-1 (alpha)
+ *     and 0..n_beta-1 (beta);
+ *   - excitation row k = (i, j, a, b) is tau_k = a+_a a+_b a_j a_i; a single
+ *     is (i, -1, a, -1), tau_k = a+_a a_i; row 0 is applied first (it is the
+ *     rightmost factor of Eq. 3);
+ *   - a_p and a+_p carry the Jordan-Wigner sign (-1)^(occupied modes below p);
+ *   - on a linked pair tau|E> = s|D> a factor rotates
+ *         c_E' = cos(t) c_E - s sin(t) c_D,   c_D' = cos(t) c_D + s sin(t) c_E
+ *     (two rounded products and one rounded sum each, no fused multiply-add),
+ *     a missing member enters as +0.0 and is created, and afterwards both
+ *     members are dropped if |c| < eps (strict);
+ *   - cos(theta) and sin(theta) are evaluated once on the host (libm).
+ *
+ * Ownership: the caller owns every pointer it passes; inputs are copied during
+ * the call.  The library owns its device state (allocated with cudaMalloc on
+ * the device current at ucc_create) and frees it in ucc_destroy.  All device
+ * work is enqueued on the caller's stream (a cudaStream_t passed as void*;
+ * NULL = legacy default stream).  A call that returns host values
+ * synchronises that stream before returning.
+ *
+ * Errors: every call returns a ucc_status; nothing aborts, traps or exits.
+ * ucc_last_error() returns a thread-local message for the last failing call
+ * of the calling thread.  Device-side failures (a hash probe that exceeds its
+ * bound, an internal inconsistency) are reported through a device error word
+ * and returned as UCC_ECUDA or UCC_ECAPACITY by the next synchronising call.
+ */
+#ifndef UCC_H_
+#define UCC_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ucc_ctx ucc_ctx; /* opaque, library-owned */
+
+typedef enum {
+  UCC_OK = 0,
+  UCC_EINVAL = 1,    /* malformed argument (sizes, indices, spin, NaN theta) */
+  UCC_ENOMEM = 2,    /* a device or pinned-host allocation failed */
+  UCC_ECAPACITY = 3, /* the wavefunction outgrew max_entries or device memory */
+  UCC_ETIMEOUT = 4,  /* a bounded device wait gave up */
+  UCC_ECUDA = 5,     /* a CUDA runtime error or a device error word */
+  UCC_ESTATE = 6     /* call out of order (e.g. energy before apply) */
+} ucc_status;
+
+/* One- and two-electron integrals in the spatial-orbital basis (Methods
+ * section: the paper takes them from PySCF).  h: n_spatial^2 row-major,
+ * symmetric.  g: n_spatial^4 row-major chemist notation (pq|rs) with 8-fold
+ * symmetry.  Host pointers.  e_nuc is added to every returned energy. */
+typedef struct {
+  int32_t n_spatial, n_alpha, n_beta;
+  double e_nuc;
+  const double* h;
+  const double* g;
+} ucc_hamiltonian;
+
+/* The factor list of Eq. 3 (Eq. 2's singles and doubles, already ordered and
+ * truncated as the Methods section describes).  idx: n_exc x 4 int32 host
+ * array of spin-orbital rows (i, j, a, b), singles (i, -1, a, -1); the four
+ * indices of a row must be distinct, < 2*n_spatial, and spin-conserving.
+ * theta: n_exc host doubles (NULL = all zero). */
+typedef struct {
+  int32_t n_exc;
+  const int32_t* idx;
+  const double* theta;
+} ucc_ansatz;
+
+/* Run options.  Zero-initialise and set what you need. */
+typedef struct {
+  int64_t n_max, n_cut; /* Methods-section truncation: if more than n_max
+                           determinants remain after a factor keep the n_cut of
+                           largest |c| (ties: smaller key).  0 = off. */
+  int64_t max_entries;  /* hard cap on stored determinants, 0 = device memory */
+  int32_t probe_width;  /* lanes per hash probe: 1, 2, 4 or 8; 0 = autotuned */
+  int32_t reserved[5];
+} ucc_options;
+
+/* Counters of the last apply / gradient call. */
+typedef struct {
+  int64_t n_det;            /* live determinants after the last factor */
+  int64_t rotations;        /* linked pairs rotated (det-rotations), forward */
+  int64_t created;          /* partners that entered the map */
+  int64_t dropped_new;      /* partners computed below eps, never stored */
+  int64_t dropped_old;      /* stored entries that fell below eps */
+  int64_t cut;              /* entries removed by the n_max/n_cut rule */
+  int64_t peak_entries;     /* largest stored count (incl. dropped slots) */
+  int64_t capacity_entries; /* current entry capacity */
+  int64_t hash_slots;       /* current hash-table size */
+  int64_t rebuilds;         /* compactions / growths during the last run */
+  int64_t tape_entries;     /* adjoint kill-tape records (gradient only) */
+  int64_t kernel_launches;  /* kernels this library launched in the last call */
+  int64_t scanned;          /* determinant keys read by the forward factor steps */
+  int64_t sigma_probes;     /* hash lookups of the last energy evaluation */
+  int64_t sigma_hits;       /* of which found a live determinant */
+  int64_t reverse_pairs;    /* linked pairs handled by the reverse sweep */
+  double apply_ms;          /* device time of the last forward pass */
+  double energy_ms;         /* device time of the last energy evaluation */
+  double reverse_ms;        /* device time of the last reverse sweep */
+} ucc_stats;
+
+/* Create a context: validate and upload the problem (h, g, the factor table
+ * with host-evaluated cos/sin).  The stream is stored and used by every later
+ * call on this context.  Returns UCC_EINVAL for n_spatial > 32 or < 1,
+ * electron counts out of range, a malformed or spin-violating excitation row,
+ * or a NaN/inf theta. */
+ucc_status ucc_create(const ucc_hamiltonian* ham, const ucc_ansatz* ansatz, void* cuda_stream, ucc_ctx** out);
+
+/* Replace all n_exc angles.  theta is a host pointer (on_device = 0) or a
+ * device pointer on the context's device (on_device = 1). */
+ucc_status ucc_set_theta(ucc_ctx* ctx, const double* theta, int on_device);
+
+/* Set run options (copied).  NULL restores the defaults (no cut, autotuned
+ * probe width, no entry cap). */
+ucc_status ucc_set_options(ucc_ctx* ctx, const ucc_options* opt);
+
+/* Build psi = U_K ... U_1 |Psi_0> on the device, dropping |c| < eps after
+ * every factor (Eq. 3; Methods section).  eps >= 0.  Synchronises the stream
+ * at chunk boundaries to size the table (it grows on demand). */
+ucc_status ucc_apply(ucc_ctx* ctx, double eps);
+
+/* E = <psi|H|psi>/<psi|psi> + e_nuc and norm2 = <psi|psi> of the last
+ * applied state (Results section's UCCSD energy; Slater-Condon rules).
+ * UCC_ESTATE if no state is held.  Synchronises. */
+ucc_status ucc_energy(ucc_ctx* ctx, double* E, double* norm2);
+
+/* Apply, energy and the adjoint sweep in one call: E and dE/dtheta_k for all
+ * n_exc factors.  grad is a host (on_device = 0) or device (on_device = 1)
+ * array of n_exc doubles.  With eps > 0 (or a cut) the derivative is that of
+ * the truncated map with the kept sets held fixed.  The sweep leaves no
+ * usable state (a later ucc_energy returns UCC_ESTATE).  Synchronises. */
+ucc_status ucc_gradient(ucc_ctx* ctx, double eps, double* E, double* grad, int on_device);
+
+/* Copy the live determinants of the held state (unordered) into caller
+ * buffers of capacity cap: keys, amps, and optionally sigma = P_S H psi from
+ * the last energy evaluation (NULL to skip).  Host or device pointers
+ * (on_device).  *n receives the count; UCC_ECAPACITY (and *n set) if cap is
+ * too small.  Synchronises. */
+ucc_status ucc_get_wavefunction(ucc_ctx* ctx, size_t cap, size_t* n, uint64_t* keys, double* amps, double* sigma,
+                                int on_device);
+
+/* Counters of the last call.  Does not synchronise beyond what that call did. */
+ucc_status ucc_get_stats(const ucc_ctx* ctx, ucc_stats* out);
+
+/* Energies and gradients of n_jobs independent contexts (molecules or theta
+ * vectors of uneven size) from one persistent launch per phase: E[j] and
+ * grads[j][0..n_exc_j) (host pointers; grads may be NULL for energy only).
+ * All contexts must live on the same device and use the same stream as
+ * jobs[0].  Synchronises. */
+ucc_status ucc_batch_run(int n_jobs, ucc_ctx* const* jobs, double eps, double* E, double* const* grads);
+
+/* Thread-local message of the last failing call on this thread. */
+const char* ucc_last_error(void);
+
+/* Free a context (NULL is a no-op).  Synchronises its stream first. */
+void ucc_destroy(ucc_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* UCC_H_ */

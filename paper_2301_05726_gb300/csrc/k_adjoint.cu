@@ -1,0 +1,174 @@
+// Reverse (adjoint) sweep: dE/dtheta_k for every factor in one pass K..1.
+//
+// With the prune sets held fixed, psi_k = P_k U_k psi_{k-1} and
+//   dE/dtheta_k = 2 <lambda_{k-1}| A_k psi_{k-1}>,
+//   mu_K = P_K (H psi - E psi)/<psi|psi>,
+//   lambda_{k-1} = U_k^T mu_k,  mu_{k-1} = P_{k-1} lambda_{k-1},
+// where A_k = tau_k - tau_k^+ maps a linked pair (E, D = s tau E) as
+// A|E> = s|D>, A|D> = -s|E>, so  <lambda|A psi> = sum_pairs s (lam_D psi_E - lam_E psi_D).
+//
+// psi_{k-1} is recovered from psi_k in place: both members of a pair by the
+// inverse rotation, a lone member by dividing out cos(theta) (its partner was
+// absent before the factor and fell below eps after it).  The only values the
+// forward pass destroys are those of stored entries that fell below eps; the
+// forward pass records them (the kill tape) and step k re-inserts its records
+// before the pair sweep.  Entries created by factor k (born[] == k) leave the
+// table when the sweep passes k.
+
+#include "ucc_device.cuh"
+
+namespace ucc {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+// Re-insert the entries factor k dropped, with their values just before the
+// drop, a zero adjoint, and their original birth factor.
+__global__ void __launch_bounds__(kThreads) k_tape_reinsert(Table t, Tape tape, int k) {
+  const unsigned long long hi = min(tape.off[k + 1], tape.cap);
+  const unsigned long long lo = min(tape.off[k], hi);
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long x = lo + (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; x < hi; x += stride) {
+    const unsigned long long key = tape.key[x];
+    const double val = tape.val[x];
+    const unsigned int born = tape.born[x];
+    Lookup r = find1(t, key, 0u);
+    if (r.state == ALIVE) {
+      raise_error(t.cnt, ERR_CONSISTENCY);
+    } else if (r.state == DEAD_OLD || r.state == DEAD_NOW) {
+      t.amps[r.idx] = val;
+      t.lam[r.idx] = 0.0;
+      t.born[r.idx] = born;
+    } else {
+      insert_new(t, key, val, born, r.slot, true, true);
+    }
+  }
+}
+
+template <int G>
+__global__ void __launch_bounds__(kThreads) k_reverse(Table t, const Factor* __restrict__ factors, int k,
+                                                       unsigned int stamp, double* grad) {
+  const Factor f = factors[k];
+  const unsigned long long m = f.occ | f.vir;
+  const unsigned long long n = min(*((volatile unsigned long long*)&t.cnt->n_tail), t.cap_n);
+  const unsigned int lane = threadIdx.x & 31u;
+  const unsigned long long warp = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const unsigned long long nwarps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
+  const unsigned int kk = (unsigned int)k;
+  double acc = 0.0;
+  unsigned int pairs = 0;
+  for (unsigned long long base = warp * 32ull; base < n; base += nwarps * 32ull) {
+    const unsigned long long i = base + lane;
+    bool act = i < n;
+    unsigned long long X = 0;
+    double cX = 0.0;
+    bool ex = false;
+    if (act) {
+      X = t.keys[i];
+      ex = ((X & f.occ) == f.occ) && ((X & f.vir) == 0ull);
+      const bool de = ((X & f.vir) == f.vir) && ((X & f.occ) == 0ull);
+      act = ex || de;
+      if (act) {
+        cX = t.amps[i];
+        act = !is_dead(cX);
+      }
+    }
+    const unsigned long long Y = X ^ m;
+    Lookup r = findG<G>(t, Y, act, stamp);
+    if (!act) continue;
+    const bool partner_live = (r.state == ALIVE);
+    if (!ex && (partner_live || r.state == DEAD_NOW)) continue;  // E's thread owns the pair
+    const unsigned long long E = ex ? X : Y;
+    const int parity = (__popcll(E & f.pmask) + f.pconst) & 1;
+    const double sg = parity ? -1.0 : 1.0;
+    const double ss = parity ? -f.s : f.s;
+    const double muX = t.lam[i];
+    ++pairs;
+    if (partner_live) {
+      // Both members stored: (e, d) = U^T (e', d'), (lamE, lamD) = U^T (muE, muD).
+      const double e1 = cX, d1 = r.amp;
+      const double muE = muX, muD = t.lam[r.idx];
+      const double e0 = __dadd_rn(__dmul_rn(f.c, e1), __dmul_rn(ss, d1));
+      const double d0 = __dsub_rn(__dmul_rn(f.c, d1), __dmul_rn(ss, e1));
+      const double lE = __dadd_rn(__dmul_rn(f.c, muE), __dmul_rn(ss, muD));
+      const double lD = __dsub_rn(__dmul_rn(f.c, muD), __dmul_rn(ss, muE));
+      acc += sg * (lD * e0 - lE * d0);
+      if (t.born[i] == kk) {
+        t.amps[i] = dead_value(stamp);
+      } else {
+        t.amps[i] = e0;
+        t.lam[i] = lE;
+      }
+      if (t.born[r.idx] == kk) {
+        t.amps[r.idx] = dead_value(stamp);
+      } else {
+        t.amps[r.idx] = d0;
+        t.lam[r.idx] = lD;
+      }
+    } else if (ex) {
+      // E alone: D was absent before the factor, c_E' = cos c_E.
+      const double e0 = __ddiv_rn(cX, f.c);
+      const double lE = __dmul_rn(f.c, muX);
+      const double lD = -__dmul_rn(ss, muX);
+      acc += sg * (lD * e0);
+      t.amps[i] = e0;
+      t.lam[i] = lE;
+    } else {
+      // D alone: E was absent before the factor, c_D' = cos c_D.
+      const double d0 = __ddiv_rn(cX, f.c);
+      const double lD = __dmul_rn(f.c, muX);
+      const double lE = __dmul_rn(ss, muX);
+      acc += sg * (-lE * d0);
+      t.amps[i] = d0;
+      t.lam[i] = lD;
+    }
+  }
+  {
+    __shared__ unsigned long long s_pairs;
+    if (threadIdx.x == 0) s_pairs = 0;
+    __syncthreads();
+    if (pairs) atomicAdd(&s_pairs, (unsigned long long)pairs);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_pairs) atomicAdd(&t.cnt->rev_pairs, s_pairs);
+  }
+  const double b = block_sum(acc);
+  if (threadIdx.x == 0) t.partials[blockIdx.x] = b;
+  if (last_block_arrive(t.cnt)) {
+    double s = 0.0;
+    for (unsigned int x = threadIdx.x; x < gridDim.x; x += blockDim.x) s += ld_cg(&t.partials[x]);
+    s = block_sum(s);
+    if (threadIdx.x == 0) {
+      grad[k] = 2.0 * s;
+      t.cnt->done = 0u;
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_tape_reinsert(const Table& t, const Tape& tape, int k, int grid, cudaStream_t st) {
+  k_tape_reinsert<<<grid, kThreads, 0, st>>>(t, tape, k);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reverse(const Table& t, const Factor* factors, int k, unsigned int stamp, double* grad,
+                           int probe_width, int grid, cudaStream_t st) {
+  switch (probe_width) {
+    case 2:
+      k_reverse<2><<<grid, kThreads, 0, st>>>(t, factors, k, stamp, grad);
+      break;
+    case 4:
+      k_reverse<4><<<grid, kThreads, 0, st>>>(t, factors, k, stamp, grad);
+      break;
+    case 8:
+      k_reverse<8><<<grid, kThreads, 0, st>>>(t, factors, k, stamp, grad);
+      break;
+    default:
+      k_reverse<1><<<grid, kThreads, 0, st>>>(t, factors, k, stamp, grad);
+      break;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace ucc

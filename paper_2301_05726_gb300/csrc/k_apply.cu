@@ -1,0 +1,299 @@
+// Forward kernels: one factor of Eq. 3 per launch, plus table maintenance.
+//
+// Data layout (HBM): compacted structure-of-arrays keys[] (uint64) and
+// amps[] (fp64) scanned with coalesced loads, an open-addressing hash of
+// 16-byte slots {key, index} for partner lookups, and (gradient runs) born[]
+// (uint32, the factor that created each entry) plus an append-only kill tape.
+
+#include "ucc_device.cuh"
+
+namespace ucc {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ void block_add_counts(Counters* c, unsigned long long rot, unsigned long long cre,
+                                                 unsigned long long dnew, unsigned long long dold,
+                                                 long long dead_delta) {
+  __shared__ unsigned long long s_rot, s_cre, s_dnew, s_dold;
+  __shared__ long long s_dead;
+  if (threadIdx.x == 0) {
+    s_rot = s_cre = s_dnew = s_dold = 0;
+    s_dead = 0;
+  }
+  __syncthreads();
+  if (rot) atomicAdd(&s_rot, rot);
+  if (cre) atomicAdd(&s_cre, cre);
+  if (dnew) atomicAdd(&s_dnew, dnew);
+  if (dold) atomicAdd(&s_dold, dold);
+  if (dead_delta) atomicAdd((unsigned long long*)&s_dead, (unsigned long long)dead_delta);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (s_rot) atomicAdd(&c->rotations, s_rot);
+    if (s_cre) atomicAdd(&c->created, s_cre);
+    if (s_dnew) atomicAdd(&c->dropped_new, s_dnew);
+    if (s_dold) atomicAdd(&c->dropped_old, s_dold);
+    if (s_dead) atomicAdd(&c->n_dead, (unsigned long long)s_dead);
+  }
+}
+
+__device__ __forceinline__ void record_kill(const Table& t, const Tape& tape, unsigned long long key, double val,
+                                            unsigned int born) {
+  unsigned long long ti = aggregated_add(&t.cnt->tape_n);
+  if (ti < tape.cap) {
+    tape.key[ti] = key;
+    tape.val[ti] = val;
+    tape.born[ti] = born;
+  } else {
+    raise_error(t.cnt, ERR_TAPE_FULL);
+  }
+}
+
+// One factor U_k on every stored determinant.  Each linked pair (E, D = tau E)
+// is rotated exactly once: by the thread of E when E is stored and live at the
+// start of the step, otherwise by the thread of D.  Entries dropped during
+// this step carry this step's stamp, so a D-thread can tell "E was live when
+// the step began" (live or DEAD_NOW) from "E absent" (ABSENT or DEAD_OLD).
+template <int G, bool RECORD>
+__global__ void __launch_bounds__(kThreads) k_forward(Table t, const Factor* __restrict__ factors, int k, double eps,
+                                                       unsigned int stamp, Tape tape) {
+  __shared__ int s_skip;
+  if (threadIdx.x == 0) s_skip = *((volatile int*)&t.cnt->stop_k) >= 0;
+  __syncthreads();
+  const bool skip = s_skip != 0;
+  unsigned long long rot = 0, cre = 0, dnew = 0, dold = 0;
+  long long dead_delta = 0;
+  if (!skip) {
+    const Factor f = factors[k];
+    const unsigned long long m = f.occ | f.vir;
+    const unsigned long long n = min(*((volatile unsigned long long*)&t.cnt->n_scan), t.cap_n);
+    const unsigned int lane = threadIdx.x & 31u;
+    const unsigned long long warp = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const unsigned long long nwarps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
+    for (unsigned long long base = warp * 32ull; base < n; base += nwarps * 32ull) {
+      const unsigned long long i = base + lane;
+      bool act = i < n;
+      unsigned long long X = 0;
+      double cX = 0.0;
+      bool ex = false;
+      if (act) {
+        X = t.keys[i];
+        ex = ((X & f.occ) == f.occ) && ((X & f.vir) == 0ull);
+        const bool de = ((X & f.vir) == f.vir) && ((X & f.occ) == 0ull);
+        act = ex || de;
+        if (act) {
+          cX = t.amps[i];
+          act = !is_dead(cX);
+        }
+      }
+      const unsigned long long Y = X ^ m;
+      Lookup r = findG<G>(t, Y, act, stamp);
+      if (!act) continue;
+      const bool partner_live = (r.state == ALIVE);
+      if (!ex && (partner_live || r.state == DEAD_NOW)) continue;  // E's thread owns the pair
+      if (ex && r.state == DEAD_NOW) {
+        raise_error(t.cnt, ERR_CONSISTENCY);
+        continue;
+      }
+      const unsigned long long E = ex ? X : Y;
+      const int parity = (__popcll(E & f.pmask) + f.pconst) & 1;
+      const double ss = parity ? -f.s : f.s;  // s * sin(theta), exact
+      const double cE = ex ? cX : 0.0;
+      const double cD = ex ? (partner_live ? r.amp : 0.0) : cX;
+      // c_E' = cos c_E - s sin c_D ;  c_D' = cos c_D + s sin c_E  (no contraction)
+      const double nE = __dsub_rn(__dmul_rn(f.c, cE), __dmul_rn(ss, cD));
+      const double nD = __dadd_rn(__dmul_rn(f.c, cD), __dmul_rn(ss, cE));
+      const double nX = ex ? nE : nD;
+      const double nY = ex ? nD : nE;
+      ++rot;
+      // The thread's own entry.
+      if (fabs(nX) < eps) {
+        if (RECORD) record_kill(t, tape, X, nX, t.born[i]);
+        t.amps[i] = dead_value(stamp);
+        ++dold;
+        ++dead_delta;
+      } else {
+        t.amps[i] = nX;
+      }
+      // The partner.
+      if (partner_live) {
+        if (fabs(nY) < eps) {
+          if (RECORD) record_kill(t, tape, Y, nY, t.born[r.idx]);
+          t.amps[r.idx] = dead_value(stamp);
+          ++dold;
+          ++dead_delta;
+        } else {
+          t.amps[r.idx] = nY;
+        }
+      } else if (fabs(nY) < eps) {
+        ++dnew;
+      } else if (r.state == DEAD_OLD) {
+        // Revive a dropped key as a fresh entry past the scan range and point
+        // its slot there.  (Reviving in place would let the old index's scan
+        // thread, if it runs later in this step, see a live entry that was
+        // not live when the step began and rotate the pair a second time.)
+        const unsigned long long idx = aggregated_add(&t.cnt->n_tail);
+        if (idx < t.cap_n) {
+          t.keys[idx] = Y;
+          t.amps[idx] = nY;
+          if (RECORD) t.born[idx] = (unsigned int)k;
+          t.slots[r.slot].idx = idx;
+        } else {
+          raise_error(t.cnt, ERR_CAPACITY);
+        }
+        ++cre;
+      } else {
+        insert_new(t, Y, nY, (unsigned int)k, r.slot, RECORD, false);
+        ++cre;
+      }
+    }
+  }
+  block_add_counts(t.cnt, rot, cre, dnew, dold, dead_delta);
+  if (last_block_arrive(t.cnt) && threadIdx.x == 0) {
+    Counters* c = t.cnt;
+    c->done = 0u;
+    if (!skip) {
+      const unsigned long long nt = ld_cg(&c->n_tail);
+      c->scanned += ld_cg(&c->n_scan);
+      c->n_scan = nt;
+      unsigned long long tn = 0;
+      if (RECORD) {
+        tn = ld_cg(&c->tape_n);
+        tape.off[k + 1] = tn;
+      }
+      // Room for factor k+1: it can append at most nt entries and drop at
+      // most nt; the hash must stay at most 75% full afterwards.
+      const unsigned long long slots = t.slot_mask + 1ull;
+      const bool room = 2ull * nt <= t.cap_n && 8ull * nt <= 3ull * slots && (!RECORD || tn + nt <= tape.cap);
+      if (!room) c->stop_k = k + 1;
+    }
+  }
+}
+
+// Copy the live entries of `from` into `to` (unordered), counting in new_n.
+__global__ void __launch_bounds__(kThreads) k_compact(Table from, Table to, int with_born) {
+  const unsigned long long n = min(*((volatile unsigned long long*)&from.cnt->n_tail), from.cap_n);
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const double a = from.amps[i];
+    if (is_dead(a)) continue;
+    const unsigned long long j = aggregated_add(&from.cnt->new_n);
+    if (j >= to.cap_n) {
+      raise_error(from.cnt, ERR_CAPACITY);
+      continue;
+    }
+    to.keys[j] = from.keys[i];
+    to.amps[j] = a;
+    if (with_born) to.born[j] = from.born[i];
+  }
+}
+
+// Insert entries [0, new_n) into an empty slot array.
+__global__ void __launch_bounds__(kThreads) k_rehash(Table t) {
+  const unsigned long long n = min(*((volatile unsigned long long*)&t.cnt->new_n), t.cap_n);
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const unsigned long long key = t.keys[i];
+    const unsigned long long s = claim_slot(t, key, mix64(key));
+    if (s != ~0ull) t.slots[s].idx = i;
+  }
+}
+
+__global__ void k_finish_rebuild(Table t) {
+  Counters* c = t.cnt;
+  const unsigned long long n = min(*((volatile unsigned long long*)&c->new_n), t.cap_n);
+  c->n_tail = n;
+  c->n_scan = n;
+  c->n_dead = 0;
+  c->new_n = 0;
+  const unsigned long long slots = t.slot_mask + 1ull;
+  if (c->stop_k >= 0 && 2ull * n <= t.cap_n && 8ull * n <= 3ull * slots) c->stop_k = -1;
+}
+
+// Gather live entries into caller buffers (unordered).
+__global__ void __launch_bounds__(kThreads) k_export(Table t, unsigned long long cap, unsigned long long* keys,
+                                                      double* amps, double* sigma) {
+  const unsigned long long n = min(*((volatile unsigned long long*)&t.cnt->n_tail), t.cap_n);
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const double a = t.amps[i];
+    if (is_dead(a)) continue;
+    const unsigned long long j = aggregated_add(&t.cnt->new_n);
+    if (j < cap) {
+      keys[j] = t.keys[i];
+      amps[j] = a;
+      if (sigma) sigma[j] = t.sigma[i];
+    }
+  }
+}
+
+// psi = {HF: 1.0}; the slots are already zero.
+__global__ void k_reset(Table t, unsigned long long hf) {
+  Counters* c = t.cnt;
+  t.keys[0] = hf;
+  t.amps[0] = 1.0;
+  if (t.born) t.born[0] = BORN_INITIAL;
+  const unsigned long long s = mix64(hf) & t.slot_mask;
+  t.slots[s].key = hf;
+  t.slots[s].idx = 0;
+  c->n_tail = 1;
+  c->n_scan = 1;
+  c->stop_k = -1;
+}
+
+}  // namespace
+
+cudaError_t launch_reset(const Table& t, unsigned long long hf, cudaStream_t st) {
+  k_reset<<<1, 1, 0, st>>>(t, hf);
+  return cudaGetLastError();
+}
+
+template <bool RECORD>
+static cudaError_t forward_g(const Table& t, const Factor* factors, int k, double eps, unsigned int stamp,
+                             const Tape& tape, int pw, int grid, cudaStream_t st) {
+  switch (pw) {
+    case 2:
+      k_forward<2, RECORD><<<grid, kThreads, 0, st>>>(t, factors, k, eps, stamp, tape);
+      break;
+    case 4:
+      k_forward<4, RECORD><<<grid, kThreads, 0, st>>>(t, factors, k, eps, stamp, tape);
+      break;
+    case 8:
+      k_forward<8, RECORD><<<grid, kThreads, 0, st>>>(t, factors, k, eps, stamp, tape);
+      break;
+    default:
+      k_forward<1, RECORD><<<grid, kThreads, 0, st>>>(t, factors, k, eps, stamp, tape);
+      break;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_forward(const Table& t, const Factor* factors, int k, double eps, unsigned int stamp, int record,
+                           const Tape& tape, int probe_width, int grid, cudaStream_t st) {
+  return record ? forward_g<true>(t, factors, k, eps, stamp, tape, probe_width, grid, st)
+                : forward_g<false>(t, factors, k, eps, stamp, tape, probe_width, grid, st);
+}
+
+cudaError_t launch_compact(const Table& from, const Table& to, int with_born, int grid, cudaStream_t st) {
+  k_compact<<<grid, kThreads, 0, st>>>(from, to, with_born);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rehash(const Table& t, int grid, cudaStream_t st) {
+  k_rehash<<<grid, kThreads, 0, st>>>(t);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finish_rebuild(const Table& t, cudaStream_t st) {
+  k_finish_rebuild<<<1, 1, 0, st>>>(t);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_export(const Table& t, unsigned long long cap, unsigned long long* keys, double* amps,
+                          double* sigma, int grid, cudaStream_t st) {
+  k_export<<<grid, kThreads, 0, st>>>(t, cap, keys, amps, sigma);
+  return cudaGetLastError();
+}
+
+}  // namespace ucc

@@ -1,0 +1,251 @@
+// Device helpers: hashing, probing, dropped-entry tags, reductions.
+#pragma once
+
+#include <cooperative_groups.h>
+#include <stdint.h>
+
+#include "ucc_internal.h"
+
+namespace ucc {
+namespace cg = cooperative_groups;
+
+// Probe steps before a lookup gives up and raises ERR_PROBE_BOUND.  The host
+// keeps the table at most 75% full, where linear probing needs a handful of
+// steps; the bound only guarantees termination.
+constexpr int MAX_PROBE = 1 << 14;
+
+// 64-bit finalizer of SplitMix64 (Steele, Lea and Flood, "Fast splittable
+// pseudorandom number generators", 2014): a bijective mix of all key bits.
+__device__ __forceinline__ unsigned long long mix64(unsigned long long x) {
+  x ^= x >> 30;
+  x *= 0xbf58476d1ce4e5b9ULL;
+  x ^= x >> 27;
+  x *= 0x94d049bb133111ebULL;
+  x ^= x >> 31;
+  return x;
+}
+
+// A dropped entry keeps its key and slot; its amplitude becomes a quiet NaN
+// whose low 32 bits name the step that dropped it.  Live amplitudes are never
+// NaN (finite inputs, finite cos/sin).
+constexpr unsigned int DEAD_TAG_HI = 0x7FFC0000u;
+
+__device__ __forceinline__ double dead_value(unsigned int stamp) {
+  return __longlong_as_double((long long)(((unsigned long long)DEAD_TAG_HI << 32) | stamp));
+}
+__device__ __forceinline__ bool is_dead(double v) {
+  return (unsigned int)((unsigned long long)__double_as_longlong(v) >> 32) == DEAD_TAG_HI;
+}
+__device__ __forceinline__ unsigned int dead_stamp(double v) {
+  return (unsigned int)((unsigned long long)__double_as_longlong(v) & 0xFFFFFFFFull);
+}
+
+__device__ __forceinline__ void raise_error(Counters* c, int bit) { atomicOr(&c->error, bit); }
+
+// Result of looking a key up.
+enum Found : int { ABSENT = 0, ALIVE = 1, DEAD_NOW = 2, DEAD_OLD = 3 };
+
+struct Lookup {
+  int state;                 // Found
+  unsigned long long slot;   // slot of the key, or the first empty slot (ABSENT)
+  unsigned long long idx;    // entry index (ALIVE / DEAD_*)
+  double amp;                // amplitude (ALIVE)
+};
+
+__device__ __forceinline__ void classify(const Table& t, unsigned long long idx, unsigned int stamp, Lookup& r) {
+  r.idx = idx;
+  double a = t.amps[idx];
+  if (!is_dead(a)) {
+    r.state = ALIVE;
+    r.amp = a;
+  } else {
+    r.state = dead_stamp(a) == stamp ? DEAD_NOW : DEAD_OLD;
+  }
+}
+
+// Single-lane linear probe.
+__device__ __forceinline__ Lookup find1(const Table& t, unsigned long long key, unsigned int stamp) {
+  Lookup r;
+  r.state = ABSENT;
+  r.idx = 0;
+  r.amp = 0.0;
+  unsigned long long h = mix64(key) & t.slot_mask;
+  for (int step = 0; step < MAX_PROBE; ++step) {
+    Slot s = t.slots[h];
+    if (s.key == key) {
+      r.slot = h;
+      classify(t, s.idx, stamp, r);
+      return r;
+    }
+    if (s.key == 0ull) {
+      r.slot = h;
+      return r;
+    }
+    h = (h + 1) & t.slot_mask;
+  }
+  raise_error(t.cnt, ERR_PROBE_BOUND);
+  r.slot = ~0ull;
+  return r;
+}
+
+// Group-cooperative linear probe: the G lanes of a group read G consecutive
+// slots in one step and vote.  Every lane of the warp must call it (inactive
+// lanes pass active = false); each lane receives the result of its own query.
+template <int G>
+__device__ __forceinline__ Lookup findG(const Table& t, unsigned long long key, bool active, unsigned int stamp) {
+  if constexpr (G == 1) {
+    Lookup r;
+    r.state = ABSENT;
+    r.idx = 0;
+    r.amp = 0.0;
+    r.slot = 0;
+    if (active) r = find1(t, key, stamp);
+    return r;
+  } else {
+    const unsigned int lane = threadIdx.x & 31u;
+    const unsigned int gbase = lane & ~(unsigned)(G - 1);
+    const unsigned int sub = lane - gbase;
+    const unsigned int gmask = (G == 32 ? 0xFFFFFFFFu : (((1u << G) - 1u) << gbase));
+    Lookup mine;
+    mine.state = ABSENT;
+    mine.idx = 0;
+    mine.amp = 0.0;
+    mine.slot = 0;
+    for (int q = 0; q < G; ++q) {
+      const unsigned int src = gbase + q;
+      unsigned long long qk = __shfl_sync(0xFFFFFFFFu, key, src);
+      bool qa = __shfl_sync(0xFFFFFFFFu, active, src);
+      // Group-uniform: every lane of the group sees the same qk / qa.
+      unsigned long long res_slot = 0, res_idx = 0;
+      int res_state = ABSENT;
+      bool decided = !qa;
+      unsigned long long h = mix64(qk) & t.slot_mask;
+      for (int step = 0; step < MAX_PROBE / G; ++step) {
+        // All lanes of the warp run this loop in lock step (the trip count is
+        // warp-uniform via the ballot below), so full-mask votes are safe.
+        unsigned long long my = (h + sub) & t.slot_mask;
+        Slot s;
+        s.key = 1ull;
+        s.idx = 0;
+        if (!decided) s = t.slots[my];
+        unsigned int hit = __ballot_sync(0xFFFFFFFFu, !decided && s.key == qk) & gmask;
+        unsigned int emp = __ballot_sync(0xFFFFFFFFu, !decided && s.key == 0ull) & gmask;
+        if (!decided) {
+          if (hit) {
+            int w = __ffs(hit) - 1;
+            res_slot = __shfl_sync(gmask, my, w);
+            res_idx = __shfl_sync(gmask, s.idx, w);
+            res_state = ALIVE;  // refined by classify below
+            decided = true;
+          } else if (emp) {
+            int w = __ffs(emp) - 1;
+            res_slot = __shfl_sync(gmask, my, w);
+            res_state = ABSENT;
+            decided = true;
+          } else {
+            h = (h + G) & t.slot_mask;
+          }
+        }
+        if (__all_sync(0xFFFFFFFFu, decided)) break;
+        if (step == MAX_PROBE / G - 1 && !decided) raise_error(t.cnt, ERR_PROBE_BOUND);
+      }
+      if (lane == src && qa) {
+        mine.slot = res_slot;
+        if (res_state == ALIVE) {
+          classify(t, res_idx, stamp, mine);
+        } else {
+          mine.state = ABSENT;
+        }
+      }
+    }
+    return mine;
+  }
+}
+
+// Claim an empty slot for key, starting at the slot a failed lookup ended on.
+// Only one lane ever inserts a given key during a step, so a lost CAS means
+// another key took the slot and the probe moves on.
+__device__ __forceinline__ unsigned long long claim_slot(const Table& t, unsigned long long key,
+                                                         unsigned long long start) {
+  unsigned long long h = start & t.slot_mask;
+  for (int step = 0; step < MAX_PROBE; ++step) {
+    unsigned long long prev = atomicCAS(&t.slots[h].key, 0ull, key);
+    if (prev == 0ull) return h;
+    if (prev == key) {
+      raise_error(t.cnt, ERR_CONSISTENCY);
+      return h;
+    }
+    h = (h + 1) & t.slot_mask;
+  }
+  raise_error(t.cnt, ERR_PROBE_BOUND);
+  return ~0ull;
+}
+
+// Warp-aggregated increment of a device counter: the lanes that reach this
+// call together share one atomicAdd and receive consecutive values.
+__device__ __forceinline__ unsigned long long aggregated_add(unsigned long long* counter) {
+  cg::coalesced_group g = cg::coalesced_threads();
+  unsigned long long base = 0;
+  if (g.thread_rank() == 0) base = atomicAdd(counter, (unsigned long long)g.size());
+  base = g.shfl(base, 0);
+  return base + g.thread_rank();
+}
+
+// Append (key, amp) as a new entry and point a slot at it.
+__device__ __forceinline__ bool insert_new(const Table& t, unsigned long long key, double amp, unsigned int born,
+                                           unsigned long long start_slot, bool with_born, bool with_lam) {
+  unsigned long long s = claim_slot(t, key, start_slot);
+  unsigned long long idx = aggregated_add(&t.cnt->n_tail);
+  if (idx >= t.cap_n || s == ~0ull) {
+    raise_error(t.cnt, ERR_CAPACITY);
+    return false;
+  }
+  t.keys[idx] = key;
+  t.amps[idx] = amp;
+  if (with_born) t.born[idx] = born;
+  if (with_lam) t.lam[idx] = 0.0;
+  t.slots[s].idx = idx;
+  return true;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+  return v;
+}
+
+// Block-wide sum; result valid in thread 0.  blockDim.x <= 1024.
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double red[32];
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (w == 0) {
+    r = (l < (int)(blockDim.x >> 5)) ? red[l] : 0.0;
+    r = warp_sum(r);
+  }
+  return r;
+}
+
+// "Last block" pattern: every block calls this once at its end; it returns
+// true in exactly one block, after all other blocks' prior writes are visible.
+__device__ __forceinline__ bool last_block_arrive(Counters* c) {
+  __shared__ bool last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    unsigned int prev = atomicAdd(&c->done, 1u);
+    last = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (last) __threadfence();
+  return last;
+}
+
+// Loads that bypass L1 (values other blocks wrote in this kernel).
+__device__ __forceinline__ unsigned long long ld_cg(const unsigned long long* p) { return __ldcg(p); }
+__device__ __forceinline__ double ld_cg(const double* p) { return __ldcg(p); }
+
+}  // namespace ucc

@@ -1,0 +1,105 @@
+// Internal types shared by the CUDA translation units of libucc.so.
+// Not part of the public ABI (include/ucc.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ucc {
+
+// One factor U_k of Eq. 3 as the kernels need it.  tau_k = a+_a a+_b a_j a_i.
+//   occ, vir : bit masks of {i, j} and {a, b};
+//   pmask, pconst : the Jordan-Wigner sign of tau_k|E> is
+//                   (-1)^(popc(E & pmask) + pconst) for every E that tau_k
+//                   excites (the four annihilate/create steps each count the
+//                   occupied modes below their index; the counts differ from
+//                   popc(E & below(x)) only by index comparisons, folded into
+//                   pconst);
+//   c, s : cos(theta_k), sin(theta_k) from the host's libm.
+struct Factor {
+  unsigned long long occ, vir, pmask;
+  double c, s;
+  int pconst, is_double;
+};
+static_assert(sizeof(Factor) == 48, "Factor layout");
+
+// Open-addressing hash slot: key 0 = empty (no valid determinant has zero
+// electrons); idx = position of the entry in the compacted arrays.
+struct __align__(16) Slot {
+  unsigned long long key, idx;
+};
+
+// Device-resident counters of one run, zeroed at reset.
+struct Counters {
+  unsigned long long n_tail;  // entries appended to the compacted arrays (incl. dropped)
+  unsigned long long n_scan;  // entries the current step scans (fixed per step)
+  unsigned long long n_dead;  // entries dropped since the last rebuild
+  unsigned long long tape_n;  // kill-tape records
+  unsigned long long rotations, created, dropped_new, dropped_old;
+  unsigned long long new_n;   // output count of compaction / export
+  unsigned long long scanned; // keys read by forward steps (sum of n_scan)
+  unsigned long long sig_probes, sig_hits;  // hash probes / hits of the energy pass
+  unsigned long long rev_pairs;             // pairs handled by the reverse sweep
+  unsigned int done;          // last-block arrival counter
+  int stop_k;                 // first factor skipped for lack of room (-1: none)
+  int error;                  // device error word (bit flags below)
+  int pad;
+  double e_num, norm2;        // <psi|H|psi>, <psi|psi> of the last energy pass
+};
+
+enum DeviceError : int {
+  ERR_PROBE_BOUND = 1,   // a probe ran past its step bound (table too full)
+  ERR_CONSISTENCY = 2,   // a state the algorithm excludes was observed
+  ERR_TAPE_FULL = 4,     // kill tape capacity exceeded
+  ERR_CAPACITY = 8       // entry allocation past capacity
+};
+
+// Everything a kernel needs to address the wavefunction table.
+struct Table {
+  unsigned long long* keys;  // [cap_n] determinant keys
+  double* amps;              // [cap_n] amplitudes; a dropped entry holds a tagged NaN
+  unsigned int* born;        // [cap_n] factor that created the entry (gradient runs)
+  double* lam;               // [cap_n] adjoint vector (gradient runs)
+  double* sigma;             // [cap_n] P_S H psi (energy runs)
+  Slot* slots;               // [slot_mask + 1]
+  unsigned long long slot_mask;
+  unsigned long long cap_n;
+  Counters* cnt;
+  double* partials;          // [grid] per-block partial sums
+};
+
+struct Tape {
+  unsigned long long* key;
+  double* val;
+  unsigned int* born;
+  unsigned long long* off;  // [K + 1] tape_n at the start of factor k
+  unsigned long long cap;
+};
+
+// Spatial integrals for the energy kernel.
+struct Integrals {
+  const double* h;  // [n^2]
+  const double* g;  // [n^4] chemist (pq|rs)
+  int n;            // spatial orbitals
+  int n_so;
+};
+
+constexpr unsigned int BORN_INITIAL = 0xFFFFFFFFu;  // the reference determinant
+
+// --- launch wrappers (each returns the launch's cudaError_t) ---------------
+cudaError_t launch_reset(const Table& t, unsigned long long hf, cudaStream_t st);
+cudaError_t launch_forward(const Table& t, const Factor* factors, int k, double eps, unsigned int stamp,
+                           int record, const Tape& tape, int probe_width, int grid, cudaStream_t st);
+cudaError_t launch_compact(const Table& from, const Table& to, int with_born, int grid, cudaStream_t st);
+cudaError_t launch_rehash(const Table& t, int grid, cudaStream_t st);
+cudaError_t launch_finish_rebuild(const Table& t, cudaStream_t st);
+cudaError_t launch_export(const Table& t, unsigned long long cap, unsigned long long* keys, double* amps,
+                          double* sigma, int grid, cudaStream_t st);
+cudaError_t launch_sigma(const Table& t, const Integrals& in, int grid, cudaStream_t st);
+cudaError_t launch_lambda_init(const Table& t, int grid, cudaStream_t st);
+cudaError_t launch_tape_reinsert(const Table& t, const Tape& tape, int k, int grid, cudaStream_t st);
+cudaError_t launch_reverse(const Table& t, const Factor* factors, int k, unsigned int stamp, double* grad,
+                           int probe_width, int grid, cudaStream_t st);
+int sigma_smem_bytes(int n_so);
+
+}  // namespace ucc
