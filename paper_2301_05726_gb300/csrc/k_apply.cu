@@ -57,7 +57,7 @@ __device__ __forceinline__ void record_kill(const Table& t, const Tape& tape, un
 // the step began" (live or DEAD_NOW) from "E absent" (ABSENT or DEAD_OLD).
 template <int G, bool RECORD>
 __global__ void __launch_bounds__(kThreads) k_forward(Table t, const Factor* __restrict__ factors, int k, double eps,
-                                                       unsigned int stamp, Tape tape) {
+                                                       unsigned int stamp, Tape tape, unsigned long long n_max) {
   __shared__ int s_skip;
   if (threadIdx.x == 0) s_skip = *((volatile int*)&t.cnt->stop_k) >= 0;
   __syncthreads();
@@ -166,7 +166,10 @@ __global__ void __launch_bounds__(kThreads) k_forward(Table t, const Factor* __r
       // most nt; the hash must stay at most 75% full afterwards.
       const unsigned long long slots = t.slot_mask + 1ull;
       const bool room = 2ull * nt <= t.cap_n && 8ull * nt <= 3ull * slots && (!RECORD || tn + nt <= tape.cap);
-      if (!room) c->stop_k = k + 1;
+      // Methods-section truncation is due when more than n_max entries live.
+      const bool cut = n_max > 0 && nt - ld_cg(&c->n_dead) > n_max;
+      if (cut) c->cut_pending = 1;
+      if (!room || cut) c->stop_k = k + 1;
     }
   }
 }
@@ -251,28 +254,28 @@ cudaError_t launch_reset(const Table& t, unsigned long long hf, cudaStream_t st)
 
 template <bool RECORD>
 static cudaError_t forward_g(const Table& t, const Factor* factors, int k, double eps, unsigned int stamp,
-                             const Tape& tape, int pw, int grid, cudaStream_t st) {
+                             const Tape& tape, unsigned long long n_max, int pw, int grid, cudaStream_t st) {
   switch (pw) {
     case 2:
-      k_forward<2, RECORD><<<grid, kThreads, 0, st>>>(t, factors, k, eps, stamp, tape);
+      k_forward<2, RECORD><<<grid, kThreads, 0, st>>>(t, factors, k, eps, stamp, tape, n_max);
       break;
     case 4:
-      k_forward<4, RECORD><<<grid, kThreads, 0, st>>>(t, factors, k, eps, stamp, tape);
+      k_forward<4, RECORD><<<grid, kThreads, 0, st>>>(t, factors, k, eps, stamp, tape, n_max);
       break;
     case 8:
-      k_forward<8, RECORD><<<grid, kThreads, 0, st>>>(t, factors, k, eps, stamp, tape);
+      k_forward<8, RECORD><<<grid, kThreads, 0, st>>>(t, factors, k, eps, stamp, tape, n_max);
       break;
     default:
-      k_forward<1, RECORD><<<grid, kThreads, 0, st>>>(t, factors, k, eps, stamp, tape);
+      k_forward<1, RECORD><<<grid, kThreads, 0, st>>>(t, factors, k, eps, stamp, tape, n_max);
       break;
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_forward(const Table& t, const Factor* factors, int k, double eps, unsigned int stamp, int record,
-                           const Tape& tape, int probe_width, int grid, cudaStream_t st) {
-  return record ? forward_g<true>(t, factors, k, eps, stamp, tape, probe_width, grid, st)
-                : forward_g<false>(t, factors, k, eps, stamp, tape, probe_width, grid, st);
+                           const Tape& tape, unsigned long long n_max, int probe_width, int grid, cudaStream_t st) {
+  return record ? forward_g<true>(t, factors, k, eps, stamp, tape, n_max, probe_width, grid, st)
+                : forward_g<false>(t, factors, k, eps, stamp, tape, n_max, probe_width, grid, st);
 }
 
 cudaError_t launch_compact(const Table& from, const Table& to, int with_born, int grid, cudaStream_t st) {

@@ -24,6 +24,12 @@ ucc_status fail(ucc_status s, const std::string& msg) {
   return s;
 }
 
+}  // namespace
+
+void ucc::set_last_error(const char* msg) { g_last_error = msg; }
+
+namespace {
+
 #define CUDA_TRY(expr)                                                                                   \
   do {                                                                                                   \
     cudaError_t e_ = (expr);                                                                             \
@@ -117,6 +123,7 @@ struct ucc_ctx {
   int partial_cap = 0;
   Counters* d_cnt = nullptr;
   Counters* h_cnt = nullptr;  // pinned mirror
+  SelectState* d_sel = nullptr;
   Arrays cur, spare;
   // kill tape
   unsigned long long* t_key = nullptr;
@@ -301,15 +308,40 @@ int pick_probe_width(ucc_ctx* c) {
   return c->probe_width;
 }
 
-// Factors [0, K) on the reference, growing the table whenever the device
-// reports that the next factor might not fit.
+// Make room for the next factor: it may append one entry per stored entry
+// (and, in gradient runs, drop as many onto the tape).  Compacts when a
+// quarter of the stored entries are dropped ones.
+ucc_status ensure_room(ucc_ctx* c, bool record) {
+  UCC_TRY(read_counters(c));
+  const Counters h = *c->h_cnt;  // copy: later reads overwrite the mirror
+  const unsigned long long live = h.n_tail - h.n_dead;
+  if (c->opt.max_entries > 0 && live > (unsigned long long)c->opt.max_entries)
+    return fail(UCC_ECAPACITY, "wavefunction exceeds max_entries (" + std::to_string(live) + " live)");
+  const bool room = 2 * h.n_tail <= c->cur.cap_n && 8 * h.n_tail <= 3 * c->cur.n_slots;
+  const bool sparse = h.n_dead > 4096 && h.n_dead * 4 > h.n_tail;
+  if (record) UCC_TRY(ensure_tape(c, h.tape_n + 2 * live + (1 << 12)));
+  if (!room || sparse) {
+    unsigned long long cap = c->cur.cap_n;
+    if (2 * live > cap || 8 * live > 3 * c->cur.n_slots) cap = std::max<unsigned long long>(4 * live, 1 << 12);
+    UCC_TRY(rebuild(c, cap));
+    UCC_TRY(read_counters(c));
+  }
+  return UCC_OK;
+}
+
+// Factors [0, K) on the reference.  The last block of each factor flags a
+// stop when the next factor might not fit or when the Methods-section cut is
+// due; later launches in the chunk then skip, and the host cuts / grows and
+// resumes at the flagged factor.
 ucc_status run_forward(ucc_ctx* c, double eps, bool record) {
   if (!(eps >= 0.0) || std::isinf(eps)) return fail(UCC_EINVAL, "eps must be finite and >= 0");
   UCC_TRY(reset_state(c, record));
   const int pw = pick_probe_width(c);
   const int chunk = 64;
+  const unsigned long long n_max = c->opt.n_max > 0 ? (unsigned long long)c->opt.n_max : 0ull;
   int k = 0;
   unsigned long long n_known = 1;
+  long long cut_total = 0;
   CUDA_TRY(cudaEventRecord(c->ev[0], c->stream));
   while (k < c->K) {
     int end = std::min(c->K, k + chunk);
@@ -321,7 +353,7 @@ ucc_status run_forward(ucc_ctx* c, double eps, bool record) {
     if (k < 0 || end > c->K) return fail(UCC_ECUDA, "factor index out of range");
     for (int kk = k; kk < end; ++kk) {
       CUDA_TRY(launch_forward(c->table(), c->d_factors, kk, eps, (unsigned int)(kk + 1), record ? 1 : 0, c->tape(),
-                              pw, grid, c->stream));
+                              n_max, pw, grid, c->stream));
       c->launches++;
     }
     UCC_TRY(read_counters(c));
@@ -329,24 +361,30 @@ ucc_status run_forward(ucc_ctx* c, double eps, bool record) {
     n_known = h.n_tail;
     c->stats.peak_entries = std::max<long long>(c->stats.peak_entries, (long long)h.n_tail);
     if (h.stop_k >= 0) {
-      // Grow: next factor may double the entries (and the tape).
-      unsigned long long live = h.n_tail - h.n_dead;
-      unsigned long long need = std::max<unsigned long long>(4 * live, 1 << 12);
-      if (c->opt.max_entries > 0 && live * 2 > (unsigned long long)c->opt.max_entries)
-        return fail(UCC_ECAPACITY, "wavefunction exceeds max_entries (" + std::to_string(live) + " live)");
-      if (record) UCC_TRY(ensure_tape(c, h.tape_n + 2 * live + (1 << 12)));
-      UCC_TRY(rebuild(c, std::max<unsigned long long>(need, c->cur.cap_n)));
+      const int resume = h.stop_k;
+      if (resume <= k || resume > end) return fail(UCC_ECUDA, "invalid resume factor");
+      if (h.cut_pending) {
+        const unsigned long long before = h.n_tail - h.n_dead;
+        CUDA_TRY(launch_select_cut(c->table(), c->d_sel, (unsigned long long)c->opt.n_cut, (unsigned int)resume,
+                                   record ? 1 : 0, c->tape(), resume - 1, c->full_grid(), c->stream, &c->launches));
+        UCC_TRY(read_counters(c));
+        const unsigned long long after = c->h_cnt->n_tail - c->h_cnt->n_dead;
+        if (after != (unsigned long long)c->opt.n_cut)
+          return fail(UCC_ECUDA, "truncation kept " + std::to_string(after) + " entries, expected " +
+                                     std::to_string(c->opt.n_cut));
+        cut_total += (long long)(before - after);
+      }
+      UCC_TRY(ensure_room(c, record));
+      const int minus_one = -1, zero = 0;
+      CUDA_TRY(cudaMemcpyAsync(&c->d_cnt->stop_k, &minus_one, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+      CUDA_TRY(cudaMemcpyAsync(&c->d_cnt->cut_pending, &zero, sizeof(int), cudaMemcpyHostToDevice, c->stream));
       UCC_TRY(read_counters(c));
-      if (c->h_cnt->stop_k >= 0) return fail(UCC_ECAPACITY, "table growth did not make room");
       n_known = c->h_cnt->n_tail;
-      if (h.stop_k < k || h.stop_k > c->K) return fail(UCC_ECUDA, "invalid resume factor");
-      k = h.stop_k;
+      k = resume;
       continue;
     }
     // Compact when a quarter of the stored entries are dropped ones.
-    if (h.n_dead > 4096 && h.n_dead * 4 > h.n_tail) {
-      UCC_TRY(rebuild(c, c->cur.cap_n));
-    }
+    if (h.n_dead > 4096 && h.n_dead * 4 > h.n_tail) UCC_TRY(rebuild(c, c->cur.cap_n));
     k = end;
   }
   CUDA_TRY(cudaEventRecord(c->ev[1], c->stream));
@@ -357,6 +395,7 @@ ucc_status run_forward(ucc_ctx* c, double eps, bool record) {
   c->stats.created = (long long)h.created;
   c->stats.dropped_new = (long long)h.dropped_new;
   c->stats.dropped_old = (long long)h.dropped_old;
+  c->stats.cut = cut_total;
   c->stats.tape_entries = (long long)h.tape_n;
   c->stats.scanned = (long long)h.scanned;
   c->stats.capacity_entries = (long long)c->cur.cap_n;
@@ -521,6 +560,7 @@ void destroy(ucc_ctx* c) {
   dfree(c->d_grad);
   dfree(c->d_partials);
   dfree(c->d_cnt);
+  dfree(c->d_sel);
   dfree(c->t_key);
   dfree(c->t_val);
   dfree(c->t_born);
@@ -568,6 +608,7 @@ ucc_status ucc_create(const ucc_hamiltonian* ham, const ucc_ansatz* an, void* cu
   if ((s = dalloc(&c->d_g, n * n * n * n)) != UCC_OK) return bail(s);
   if ((s = dalloc(&c->d_grad, std::max(1, c->K))) != UCC_OK) return bail(s);
   if ((s = dalloc(&c->d_cnt, 1)) != UCC_OK) return bail(s);
+  if ((s = dalloc(&c->d_sel, 1)) != UCC_OK) return bail(s);
   if ((s = dalloc(&c->t_off, (size_t)c->K + 1)) != UCC_OK) return bail(s);
   if ((s = ensure_partials(c, c->full_grid())) != UCC_OK) return bail(s);
   if (cudaMallocHost((void**)&c->h_cnt, sizeof(Counters)) != cudaSuccess)
@@ -608,7 +649,6 @@ ucc_status ucc_set_options(ucc_ctx* c, const ucc_options* opt) {
   if (o.n_max > 0 && (o.n_cut <= 0 || o.n_cut > o.n_max)) return fail(UCC_EINVAL, "need 0 < n_cut <= n_max");
   if (o.probe_width != 0 && o.probe_width != 1 && o.probe_width != 2 && o.probe_width != 4 && o.probe_width != 8)
     return fail(UCC_EINVAL, "probe_width must be 0, 1, 2, 4 or 8");
-  if (o.n_max > 0) return fail(UCC_EINVAL, "n_max/n_cut truncation is not available in this build");
   c->opt = o;
   return UCC_OK;
 }

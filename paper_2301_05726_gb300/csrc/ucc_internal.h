@@ -41,9 +41,9 @@ struct Counters {
   unsigned long long sig_probes, sig_hits;  // hash probes / hits of the energy pass
   unsigned long long rev_pairs;             // pairs handled by the reverse sweep
   unsigned int done;          // last-block arrival counter
-  int stop_k;                 // first factor skipped for lack of room (-1: none)
+  int stop_k;                 // first factor skipped: no room, or a cut is due (-1: none)
   int error;                  // device error word (bit flags below)
-  int pad;
+  int cut_pending;            // more than n_max live entries after factor stop_k - 1
   double e_num, norm2;        // <psi|H|psi>, <psi|psi> of the last energy pass
 };
 
@@ -84,12 +84,24 @@ struct Integrals {
   int n_so;
 };
 
+// Radix-selection state of the N_MAX / N_CUT truncation.
+struct SelectState {
+  unsigned long long prefix, target;          // |c| bits of the threshold, rank left inside it
+  unsigned long long key_prefix, key_target;  // key tie-break among |c| == threshold
+  unsigned long long count_eq, cut_total;
+  int need_keys, pad;
+  unsigned long long hist[256];
+};
+
 constexpr unsigned int BORN_INITIAL = 0xFFFFFFFFu;  // the reference determinant
 
 // --- launch wrappers (each returns the launch's cudaError_t) ---------------
 cudaError_t launch_reset(const Table& t, unsigned long long hf, cudaStream_t st);
 cudaError_t launch_forward(const Table& t, const Factor* factors, int k, double eps, unsigned int stamp,
-                           int record, const Tape& tape, int probe_width, int grid, cudaStream_t st);
+                           int record, const Tape& tape, unsigned long long n_max, int probe_width, int grid,
+                           cudaStream_t st);
+cudaError_t launch_select_cut(const Table& t, SelectState* sel, unsigned long long n_cut, unsigned int stamp,
+                              int record, const Tape& tape, int k, int grid, cudaStream_t st, long long* launches);
 cudaError_t launch_compact(const Table& from, const Table& to, int with_born, int grid, cudaStream_t st);
 cudaError_t launch_rehash(const Table& t, int grid, cudaStream_t st);
 cudaError_t launch_finish_rebuild(const Table& t, cudaStream_t st);
@@ -101,5 +113,7 @@ cudaError_t launch_tape_reinsert(const Table& t, const Tape& tape, int k, int gr
 cudaError_t launch_reverse(const Table& t, const Factor* factors, int k, unsigned int stamp, double* grad,
                            int probe_width, int grid, cudaStream_t st);
 int sigma_smem_bytes(int n_so);
+// Message returned by ucc_last_error() on the calling thread.
+void set_last_error(const char* msg);
 
 }  // namespace ucc

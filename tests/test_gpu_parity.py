@@ -246,3 +246,41 @@ def test_theta_on_device_and_autograd(torch_cuda):
     E.backward()
     assert abs(E.item() - E_ref) <= E_TOL
     assert torch.max(torch.abs(theta.grad.cpu() - torch.tensor(g_ref))).item() <= G_TOL
+
+
+# ---------------------------------------------------------------------------
+# Methods-section truncation (N_MAX / N_CUT) on the device
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("case,n_max,n_cut", [
+    ("cfg3_prefix150", 200000, 125000),
+    ("cfg4_prefix300", 50000, 31250),
+    ("pruned_small", 3000, 1875),
+])
+def test_truncation_bit_exact(torch_cuda, case, n_max, n_cut):
+    if case == "cfg3_prefix150":
+        prob = synth.config_problem(3).prefix(150)
+    elif case == "cfg4_prefix300":
+        prob = synth.config_problem(4).prefix(300)
+    else:
+        prob = small_pruned()
+    ok, oa, oc = oracle_for(prob).apply(n_max=n_max, n_cut=n_cut)
+    assert oc["cut"] > 0
+    ctx = ctx_for(prob)
+    ctx.set_options(n_max=n_max, n_cut=n_cut)
+    ctx.apply()
+    gk, ga = ctx.wavefunction()
+    st = ctx.stats()
+    assert_same_state(gk, ga, ok, oa)
+    assert st["cut"] == oc["cut"]
+    assert st["rotations"] == oc["rotations"]
+
+
+def test_truncation_gradient(torch_cuda):
+    prob = small_pruned()
+    E_ref, g_ref = oracle_for(prob).gradient(n_max=3000, n_cut=1875)
+    ctx = ctx_for(prob)
+    ctx.set_options(n_max=3000, n_cut=1875)
+    E, g = ctx.gradient()
+    assert abs(E - E_ref) <= E_TOL
+    assert np.max(np.abs(g - g_ref)) <= G_TOL
+    assert ctx.stats()["cut"] > 0
