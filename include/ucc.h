@@ -168,6 +168,36 @@ ucc_status ucc_get_stats(const ucc_ctx* ctx, ucc_stats* out);
  * jobs[0].  Synchronises. */
 ucc_status ucc_batch_run(int n_jobs, ucc_ctx* const* jobs, double eps, double* E, double* const* grads);
 
+/* Largest wavefunction ucc_energy_static accepts. */
+#define UCC_STATIC_MAX_DETS 262144
+
+/* The energy pass (the same kernel as ucc_energy) over a wavefunction the
+ * caller holds, for callers that cannot allocate device memory at the point
+ * of the call: cudaMalloc/cudaFree may synchronise the whole device, the
+ * device memory may all belong to another allocator, or the device may be out
+ * of memory.  The paper has no counterpart; this is a service entry point.
+ *
+ * Inputs (device pointers on the current device, owned by the caller): h
+ * (n_spatial^2) and g (n_spatial^4, chemist order) as in ucc_hamiltonian;
+ * keys[n_det] distinct determinants with n_alpha + n_beta electrons in
+ * 2*n_spatial spin-orbitals, amps[n_det] finite amplitudes.  Outputs:
+ * sigma[n_det] (device) = P_S H psi at each key, *E = <psi|H|psi>/<psi|psi>
+ * + e_nuc and *norm2 (host; norm2 may be NULL).  Work is enqueued on
+ * cuda_stream and the call synchronises it before returning.
+ *
+ * Allocates nothing: no cudaMalloc, cudaFree or allocating library call.  Its
+ * scratch (hash slots over the keys, partial sums, counters, about 8.4 MB) is
+ * one file-scope device array that every device loading the library holds
+ * until the process exits.  The first call on a device, with that device
+ * current, looks up the array's device address (cudaGetSymbolAddress); make
+ * that first call before any stream capture.  Every call reuses the array
+ * and clears it first, so calls whose work overlaps on the GPU race: do not
+ * run two at once on one device.  n_det above UCC_STATIC_MAX_DETS, or 0,
+ * returns UCC_EINVAL; malformed keys or amplitudes return UCC_EINVAL. */
+ucc_status ucc_energy_static(int32_t n_spatial, int32_t n_alpha, int32_t n_beta, double e_nuc, const double* h,
+                             const double* g, size_t n_det, const uint64_t* keys, const double* amps, double* sigma,
+                             double* E, double* norm2, void* cuda_stream);
+
 /* Thread-local message of the last failing call on this thread. */
 const char* ucc_last_error(void);
 

@@ -17,7 +17,8 @@ STATUS_NAMES = {0: "UCC_OK", 1: "UCC_EINVAL", 2: "UCC_ENOMEM", 3: "UCC_ECAPACITY
 
 # Every symbol include/ucc.h declares.
 EXPORTS = ["ucc_create", "ucc_set_theta", "ucc_set_options", "ucc_apply", "ucc_energy", "ucc_gradient",
-           "ucc_get_wavefunction", "ucc_get_stats", "ucc_batch_run", "ucc_last_error", "ucc_destroy"]
+           "ucc_get_wavefunction", "ucc_get_stats", "ucc_batch_run", "ucc_last_error", "ucc_destroy",
+           "ucc_energy_static"]
 
 
 class Hamiltonian(ctypes.Structure):
@@ -87,9 +88,11 @@ def load(path: str = LIB_PATH):
     lib.ucc_batch_run.argtypes = [ctypes.c_int, ctypes.POINTER(vp), ctypes.c_double, dp, ctypes.POINTER(vp)]
     lib.ucc_last_error.restype = ctypes.c_char_p
     lib.ucc_last_error.argtypes = []
+    lib.ucc_energy_static.restype = st
+    lib.ucc_energy_static.argtypes = [i32, i32, i32, ctypes.c_double, vp, vp, ctypes.c_size_t, vp, vp, vp, dp, dp,
+                                      vp]
     lib.ucc_destroy.restype = None
     lib.ucc_destroy.argtypes = [vp]
-    _ = i32
     _lib = lib
     return lib
 
