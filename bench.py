@@ -40,7 +40,7 @@ FALLBACK_HBM_GBS = 6800.0
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cfg4", help="cfg4 (default) or cfgN[:prefix] for exploration")
@@ -172,8 +172,14 @@ def flush_l2(buf):
     buf.add_(1.0)
 
 
+def _roofline(kernel, bytes_, ms, launches, hbm, peak_kind):
+    ach = bytes_ / (ms / 1e3) / 1e9 if ms > 0 else 0.0
+    return {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": None,
+            "kernel": kernel, "peak_kind": peak_kind, "launches": launches,
+            "avg_launch_ms": ms / max(1, launches), "algorithmic_bytes": bytes_, "total_ms": ms}
+
+
 def run_ours(args, prob):
-    import numpy as np
     import torch
     import torch.distributed as dist
 
@@ -206,8 +212,6 @@ def run_ours(args, prob):
         flush_l2(flush)
         step_device()
     torch.cuda.synchronize()
-    st = ctx.stats()
-    rot_per_eval = st["rotations"]
 
     # Device-timed region: inputs resident, CUDA events on the library's stream.
     sampler = ClockSampler(local)
@@ -215,8 +219,8 @@ def run_ours(args, prob):
         dist.barrier()
     torch.cuda.synchronize()
     sampler.start()
-    times, launches = [], 0
-    phase = {"apply_ms": 0.0, "energy_ms": 0.0, "reverse_ms": 0.0}
+    times = []
+    tot = {}
     for _ in range(args.steps):
         flush_l2(flush)
         ev0 = torch.cuda.Event(enable_timing=True)
@@ -226,10 +230,8 @@ def run_ours(args, prob):
         ev1.record(stream)
         ev1.synchronize()
         times.append(ev0.elapsed_time(ev1))
-        s = ctx.stats()
-        launches += s["kernel_launches"]
-        for k in phase:
-            phase[k] += s[k]
+        for k, v in ctx.stats().items():
+            tot[k] = tot.get(k, 0) + v
     torch.cuda.synchronize()
     clocks = sampler.stop()
     ms = sum(times) / len(times)
@@ -237,6 +239,8 @@ def run_ours(args, prob):
         t = torch.tensor([ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
+    n_steps = len(times)
+    rot_per_eval = tot["rotations"] / n_steps
     value = rot_per_eval * world / (ms / 1e3)
 
     # End to end through the public API with host buffers.
@@ -250,29 +254,35 @@ def run_ours(args, prob):
         e2e_times.append(time.perf_counter() - t0)
     e2e_ms = 1e3 * sum(e2e_times) / len(e2e_times) if e2e_times else float("nan")
 
+    # "Plain": per-theta central differences on the GPU need 2K + 1 energy
+    # evaluations (apply + energy); one is measured, the total extrapolated.
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx.apply()
+    ctx.energy()
+    torch.cuda.synchronize()
+    energy_eval_s = time.perf_counter() - t0
+    plain_s = (2 * prob.n_exc + 1) * energy_eval_s
+
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
         return
-    st = ctx.stats()
     hbm, peak_kind = peaks()
-    n_steps = len(times)
-    apply_ms = phase["apply_ms"] / n_steps
-    energy_ms = phase["energy_ms"] / n_steps
-    reverse_ms = phase["reverse_ms"] / n_steps
-    # Dominant kernel's roofline (algorithmic bytes).
-    fwd_bytes = 8.0 * st.get("scanned", 0) + 48.0 * st["rotations"] + 32.0 * st["created"]
-    sig_bytes = 24.0 * st["n_det"] + 16.0 * st.get("sigma_probes", 0) + 8.0 * st.get("sigma_hits", 0)
-    if energy_ms >= apply_ms:
-        dom = {"kernel": "k_sigma", "bound": "hbm", "achieved": sig_bytes / (energy_ms / 1e3) / 1e9,
-               "launch_ms": energy_ms, "launches_per_step": 1}
-    else:
-        nf = max(1, prob.n_exc)
-        dom = {"kernel": "k_forward", "bound": "hbm", "achieved": fwd_bytes / (apply_ms / 1e3) / 1e9,
-               "launch_ms": apply_ms / nf, "launches_per_step": nf}
-    roof = {"bound": dom["bound"], "achieved": dom["achieved"], "peak": hbm, "unit": "GB/s",
-            "frac": dom["achieved"] / hbm, "traffic": None, "kernel": dom["kernel"],
-            "peak_kind": peak_kind, "avg_launch_ms": dom["launch_ms"]}
+    fwd_bytes = 8.0 * (tot["scanned"] + tot["recompute_scanned"]) + \
+        48.0 * (tot["rotations"] + tot["recompute_rotations"]) + 32.0 * (tot["created"] + tot["recompute_created"])
+    sig_bytes = 24.0 * tot["n_det"] + 16.0 * tot["sigma_probes"] + 8.0 * tot["sigma_hits"]
+    rev_bytes = 80.0 * tot["reverse_pairs"]
+    kernels = {
+        "k_forward": _roofline("k_forward", fwd_bytes, tot["forward_kernel_ms"], tot["forward_launches"], hbm,
+                               peak_kind),
+        "k_sigma": _roofline("k_sigma", sig_bytes, tot["energy_ms"], n_steps, hbm, peak_kind),
+        "k_reverse": _roofline("k_reverse", rev_bytes, tot["reverse_kernel_ms"], tot["reverse_launches"], hbm,
+                               peak_kind),
+    }
+    dom = max(kernels.values(), key=lambda r: r["total_ms"])
+    roof = {k: dom[k] for k in ("bound", "achieved", "peak", "unit", "frac", "traffic", "kernel", "peak_kind",
+                                "avg_launch_ms")}
     cpu = None
     if not args.no_cpu_baseline:
         r, evals, nf, dt = oracle_sample(prob, args.cpu_seconds)
@@ -283,17 +293,22 @@ def run_ours(args, prob):
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": prob.name, "n_so": prob.n_so, "n_elec": prob.n_elec, "n_factors": prob.n_exc,
-                   "eps": prob.eps, "n_det": st["n_det"], "l2": "inputs larger than L2 + 256 MB flush per step",
+                   "eps": prob.eps, "n_max": prob.n_max, "n_cut": prob.n_cut, "n_det": tot["n_det"] // n_steps,
+                   "l2": "table larger than L2 + 256 MB flush per step",
                    "parallelism": "replicas" if world > 1 else "single"},
         "evals_per_s": world * 1e3 / ms,
-        "apply_det_rotations_per_s": st["rotations"] / (apply_ms / 1e3) if apply_ms > 0 else None,
-        "phase_ms": {"apply": apply_ms, "energy": energy_ms, "reverse": reverse_ms},
-        # theta enters through ucc_set_theta as the factor table (occ/vir/sign
-        # masks, cos, sin: 48 B per factor); E and dE/dtheta come back.
+        "apply_det_rotations_per_s": tot["rotations"] / (tot["apply_ms"] / 1e3) if tot["apply_ms"] > 0 else None,
+        "phase_ms": {"forward": tot["apply_ms"] / n_steps, "energy": tot["energy_ms"] / n_steps,
+                     "reverse_incl_recompute": tot["reverse_ms"] / n_steps},
+        "vs_plain": {"plain": "per-theta central differences on the GPU, 2K+1 energy evaluations",
+                     "energy_eval_s": energy_eval_s, "plain_gradient_s_extrapolated": plain_s,
+                     "adjoint_gradient_s": ms / 1e3, "speedup": plain_s / (ms / 1e3)},
         "e2e": {"value": rot_per_eval * world / (e2e_ms / 1e3), "unit": UNIT,
                 "h2d_bytes_per_step": 48 * prob.n_exc, "d2h_bytes_per_step": 8 * prob.n_exc + 8},
-        "gpu_launches": launches,
+        "gpu_launches": int(tot["kernel_launches"]),
         "roofline": roof,
+        "kernels": {k: {x: v[x] for x in ("achieved", "frac", "launches", "avg_launch_ms", "total_ms")}
+                    for k, v in kernels.items()},
         "clocks": clocks,
         "cpu_baseline": cpu,
     }

@@ -92,7 +92,9 @@ typedef struct {
                            largest |c| (ties: smaller key).  0 = off. */
   int64_t max_entries;  /* hard cap on stored determinants, 0 = device memory */
   int32_t probe_width;  /* lanes per hash probe: 1, 2, 4 or 8; 0 = autotuned */
-  int32_t reserved[5];
+  int32_t checkpoint_stride; /* gradient: factors between snapshots of psi; 0 =
+                                ceil(sqrt(K)) with a cut, else one segment */
+  int32_t reserved[4];
 } ucc_options;
 
 /* Counters of the last apply / gradient call. */
@@ -113,9 +115,16 @@ typedef struct {
   int64_t sigma_probes;     /* hash lookups of the last energy evaluation */
   int64_t sigma_hits;       /* of which found a live determinant */
   int64_t reverse_pairs;    /* linked pairs handled by the reverse sweep */
+  int64_t recompute_scanned;   /* gradient: keys read while recomputing segments */
+  int64_t recompute_rotations; /* gradient: pairs rotated while recomputing segments */
+  int64_t recompute_created;   /* gradient: entries created while recomputing segments */
+  int64_t forward_launches;    /* forward factor launches (incl. recomputation) */
+  int64_t reverse_launches;    /* reverse factor launches */
   double apply_ms;          /* device time of the last forward pass */
   double energy_ms;         /* device time of the last energy evaluation */
   double reverse_ms;        /* device time of the last reverse sweep */
+  double forward_kernel_ms; /* device time of the forward factor launches alone */
+  double reverse_kernel_ms; /* device time of the reverse factor launches alone */
 } ucc_stats;
 
 /* Create a context: validate and upload the problem (h, g, the factor table

@@ -102,11 +102,18 @@ class Oracle:
         t = self.prob.theta if theta is None else theta
         return np.ascontiguousarray(t, dtype=np.float64)
 
-    def apply(self, theta=None, eps=None, n_factors=None, n_max=0, n_cut=0):
-        """Eq. 3 on the reference with the eps rule.  Returns (keys, amps, counts)
-        sorted by key; counts has rotations/created/dropped_new/dropped_old/cut."""
+    def _cut(self, n_max, n_cut):
+        if n_max is None:
+            return int(getattr(self.prob, "n_max", 0)), int(getattr(self.prob, "n_cut", 0))
+        return int(n_max), int(n_cut or 0)
+
+    def apply(self, theta=None, eps=None, n_factors=None, n_max=None, n_cut=None):
+        """Eq. 3 on the reference with the eps rule (and the problem's N_MAX/N_CUT
+        cut unless given).  Returns (keys, amps, counts) sorted by key; counts has
+        rotations/created/dropped_new/dropped_old/cut."""
         th = self._theta(theta)
         eps = self.prob.eps if eps is None else eps
+        n_max, n_cut = self._cut(n_max, n_cut)
         nf = len(th) if n_factors is None else int(n_factors)
         cnt = _Counts()
         wf = self.lib.orc_apply(self.handle, _dp(th), nf, float(eps), int(n_max), int(n_cut), ctypes.byref(cnt))
@@ -156,14 +163,15 @@ class Oracle:
         s = self.lib.orc_tau(self.handle, int(k), 1 if dagger else 0, int(det), ctypes.byref(out))
         return (s, out.value) if s else (0, None)
 
-    def run_energy(self, theta=None, eps=None, n_factors=None, n_max=0, n_cut=0):
+    def run_energy(self, theta=None, eps=None, n_factors=None, n_max=None, n_cut=None):
         keys, amps, _ = self.apply(theta, eps, n_factors, n_max, n_cut)
         return self.energy(keys, amps)[0]
 
-    def gradient(self, theta=None, eps=None, stride=0, n_max=0, n_cut=0):
+    def gradient(self, theta=None, eps=None, stride=0, n_max=None, n_cut=None):
         """(E, dE/dtheta) by the checkpointed adjoint sweep (stride 0 = ceil(sqrt K))."""
         th = self._theta(theta)
         eps = self.prob.eps if eps is None else eps
+        n_max, n_cut = self._cut(n_max, n_cut)
         g = np.zeros(len(th))
         E = ctypes.c_double()
         self.lib.orc_gradient(self.handle, _dp(th), float(eps), int(n_max), int(n_cut), int(stride),

@@ -34,15 +34,18 @@ class Ansatz(ctypes.Structure):
 
 class Options(ctypes.Structure):
     _fields_ = [("n_max", ctypes.c_int64), ("n_cut", ctypes.c_int64), ("max_entries", ctypes.c_int64),
-                ("probe_width", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("probe_width", ctypes.c_int32), ("checkpoint_stride", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
 
 
 class Stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in (
         "n_det", "rotations", "created", "dropped_new", "dropped_old", "cut", "peak_entries", "capacity_entries",
         "hash_slots", "rebuilds", "tape_entries", "kernel_launches", "scanned", "sigma_probes", "sigma_hits",
-        "reverse_pairs")] + \
-        [(n, ctypes.c_double) for n in ("apply_ms", "energy_ms", "reverse_ms")]
+        "reverse_pairs", "recompute_scanned", "recompute_rotations", "recompute_created", "forward_launches",
+        "reverse_launches")] + \
+        [(n, ctypes.c_double) for n in ("apply_ms", "energy_ms", "reverse_ms", "forward_kernel_ms",
+                                        "reverse_kernel_ms")]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}

@@ -51,8 +51,9 @@ class UCCContext:
         handle = ctypes.c_void_p()
         check(self.lib.ucc_create(ctypes.byref(ham), ctypes.byref(an), self.stream, ctypes.byref(handle)))
         self.handle = handle
-        if probe_width or max_entries:
-            self.set_options(probe_width=probe_width, max_entries=max_entries)
+        n_max, n_cut = int(getattr(prob, "n_max", 0)), int(getattr(prob, "n_cut", 0))
+        if probe_width or max_entries or n_max:
+            self.set_options(n_max=n_max, n_cut=n_cut, probe_width=probe_width, max_entries=max_entries)
 
     def close(self):
         if getattr(self, "handle", None):
@@ -62,8 +63,8 @@ class UCCContext:
     def __del__(self):
         self.close()
 
-    def set_options(self, n_max=0, n_cut=0, max_entries=0, probe_width=0):
-        o = Options(int(n_max), int(n_cut), int(max_entries), int(probe_width))
+    def set_options(self, n_max=0, n_cut=0, max_entries=0, probe_width=0, checkpoint_stride=0):
+        o = Options(int(n_max), int(n_cut), int(max_entries), int(probe_width), int(checkpoint_stride))
         check(self.lib.ucc_set_options(self.handle, ctypes.byref(o)))
 
     def set_theta(self, theta):

@@ -15,7 +15,7 @@
 // before the pair sweep.  Entries created by factor k (born[] == k) leave the
 // table when the sweep passes k.
 
-#include "ucc_device.cuh"
+#include "ucc_steps.cuh"
 
 namespace ucc {
 
@@ -50,79 +50,14 @@ template <int G>
 __global__ void __launch_bounds__(kThreads) k_reverse(Table t, const Factor* __restrict__ factors, int k,
                                                        unsigned int stamp, double* grad) {
   const Factor f = factors[k];
-  const unsigned long long m = f.occ | f.vir;
   const unsigned long long n = min(*((volatile unsigned long long*)&t.cnt->n_tail), t.cap_n);
   const unsigned int lane = threadIdx.x & 31u;
   const unsigned long long warp = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const unsigned long long nwarps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
-  const unsigned int kk = (unsigned int)k;
   double acc = 0.0;
   unsigned int pairs = 0;
   for (unsigned long long base = warp * 32ull; base < n; base += nwarps * 32ull) {
-    const unsigned long long i = base + lane;
-    bool act = i < n;
-    unsigned long long X = 0;
-    double cX = 0.0;
-    bool ex = false;
-    if (act) {
-      X = t.keys[i];
-      ex = ((X & f.occ) == f.occ) && ((X & f.vir) == 0ull);
-      const bool de = ((X & f.vir) == f.vir) && ((X & f.occ) == 0ull);
-      act = ex || de;
-      if (act) {
-        cX = t.amps[i];
-        act = !is_dead(cX);
-      }
-    }
-    const unsigned long long Y = X ^ m;
-    Lookup r = findG<G>(t, Y, act, stamp);
-    if (!act) continue;
-    const bool partner_live = (r.state == ALIVE);
-    if (!ex && (partner_live || r.state == DEAD_NOW)) continue;  // E's thread owns the pair
-    const unsigned long long E = ex ? X : Y;
-    const int parity = (__popcll(E & f.pmask) + f.pconst) & 1;
-    const double sg = parity ? -1.0 : 1.0;
-    const double ss = parity ? -f.s : f.s;
-    const double muX = t.lam[i];
-    ++pairs;
-    if (partner_live) {
-      // Both members stored: (e, d) = U^T (e', d'), (lamE, lamD) = U^T (muE, muD).
-      const double e1 = cX, d1 = r.amp;
-      const double muE = muX, muD = t.lam[r.idx];
-      const double e0 = __dadd_rn(__dmul_rn(f.c, e1), __dmul_rn(ss, d1));
-      const double d0 = __dsub_rn(__dmul_rn(f.c, d1), __dmul_rn(ss, e1));
-      const double lE = __dadd_rn(__dmul_rn(f.c, muE), __dmul_rn(ss, muD));
-      const double lD = __dsub_rn(__dmul_rn(f.c, muD), __dmul_rn(ss, muE));
-      acc += sg * (lD * e0 - lE * d0);
-      if (t.born[i] == kk) {
-        t.amps[i] = dead_value(stamp);
-      } else {
-        t.amps[i] = e0;
-        t.lam[i] = lE;
-      }
-      if (t.born[r.idx] == kk) {
-        t.amps[r.idx] = dead_value(stamp);
-      } else {
-        t.amps[r.idx] = d0;
-        t.lam[r.idx] = lD;
-      }
-    } else if (ex) {
-      // E alone: D was absent before the factor, c_E' = cos c_E.
-      const double e0 = __ddiv_rn(cX, f.c);
-      const double lE = __dmul_rn(f.c, muX);
-      const double lD = -__dmul_rn(ss, muX);
-      acc += sg * (lD * e0);
-      t.amps[i] = e0;
-      t.lam[i] = lE;
-    } else {
-      // D alone: E was absent before the factor, c_D' = cos c_D.
-      const double d0 = __ddiv_rn(cX, f.c);
-      const double lD = __dmul_rn(f.c, muX);
-      const double lE = __dmul_rn(ss, muX);
-      acc += sg * (-lE * d0);
-      t.amps[i] = d0;
-      t.lam[i] = lD;
-    }
+    reverse_entry<G>(t, f, k, stamp, base + lane, base + lane < n, acc, pairs);
   }
   {
     __shared__ unsigned long long s_pairs;

@@ -5,7 +5,7 @@
 // 16-byte slots {key, index} for partner lookups, and (gradient runs) born[]
 // (uint32, the factor that created each entry) plus an append-only kill tape.
 
-#include "ucc_device.cuh"
+#include "ucc_steps.cuh"
 
 namespace ucc {
 
@@ -38,18 +38,6 @@ __device__ __forceinline__ void block_add_counts(Counters* c, unsigned long long
   }
 }
 
-__device__ __forceinline__ void record_kill(const Table& t, const Tape& tape, unsigned long long key, double val,
-                                            unsigned int born) {
-  unsigned long long ti = aggregated_add(&t.cnt->tape_n);
-  if (ti < tape.cap) {
-    tape.key[ti] = key;
-    tape.val[ti] = val;
-    tape.born[ti] = born;
-  } else {
-    raise_error(t.cnt, ERR_TAPE_FULL);
-  }
-}
-
 // One factor U_k on every stored determinant.  Each linked pair (E, D = tau E)
 // is rotated exactly once: by the thread of E when E is stored and live at the
 // start of the step, otherwise by the thread of D.  Entries dropped during
@@ -62,94 +50,17 @@ __global__ void __launch_bounds__(kThreads) k_forward(Table t, const Factor* __r
   if (threadIdx.x == 0) s_skip = *((volatile int*)&t.cnt->stop_k) >= 0;
   __syncthreads();
   const bool skip = s_skip != 0;
-  unsigned long long rot = 0, cre = 0, dnew = 0, dold = 0;
-  long long dead_delta = 0;
+  StepCounts sc;
   if (!skip) {
     const Factor f = factors[k];
-    const unsigned long long m = f.occ | f.vir;
     const unsigned long long n = min(*((volatile unsigned long long*)&t.cnt->n_scan), t.cap_n);
     const unsigned int lane = threadIdx.x & 31u;
     const unsigned long long warp = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const unsigned long long nwarps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
-    for (unsigned long long base = warp * 32ull; base < n; base += nwarps * 32ull) {
-      const unsigned long long i = base + lane;
-      bool act = i < n;
-      unsigned long long X = 0;
-      double cX = 0.0;
-      bool ex = false;
-      if (act) {
-        X = t.keys[i];
-        ex = ((X & f.occ) == f.occ) && ((X & f.vir) == 0ull);
-        const bool de = ((X & f.vir) == f.vir) && ((X & f.occ) == 0ull);
-        act = ex || de;
-        if (act) {
-          cX = t.amps[i];
-          act = !is_dead(cX);
-        }
-      }
-      const unsigned long long Y = X ^ m;
-      Lookup r = findG<G>(t, Y, act, stamp);
-      if (!act) continue;
-      const bool partner_live = (r.state == ALIVE);
-      if (!ex && (partner_live || r.state == DEAD_NOW)) continue;  // E's thread owns the pair
-      if (ex && r.state == DEAD_NOW) {
-        raise_error(t.cnt, ERR_CONSISTENCY);
-        continue;
-      }
-      const unsigned long long E = ex ? X : Y;
-      const int parity = (__popcll(E & f.pmask) + f.pconst) & 1;
-      const double ss = parity ? -f.s : f.s;  // s * sin(theta), exact
-      const double cE = ex ? cX : 0.0;
-      const double cD = ex ? (partner_live ? r.amp : 0.0) : cX;
-      // c_E' = cos c_E - s sin c_D ;  c_D' = cos c_D + s sin c_E  (no contraction)
-      const double nE = __dsub_rn(__dmul_rn(f.c, cE), __dmul_rn(ss, cD));
-      const double nD = __dadd_rn(__dmul_rn(f.c, cD), __dmul_rn(ss, cE));
-      const double nX = ex ? nE : nD;
-      const double nY = ex ? nD : nE;
-      ++rot;
-      // The thread's own entry.
-      if (fabs(nX) < eps) {
-        if (RECORD) record_kill(t, tape, X, nX, t.born[i]);
-        t.amps[i] = dead_value(stamp);
-        ++dold;
-        ++dead_delta;
-      } else {
-        t.amps[i] = nX;
-      }
-      // The partner.
-      if (partner_live) {
-        if (fabs(nY) < eps) {
-          if (RECORD) record_kill(t, tape, Y, nY, t.born[r.idx]);
-          t.amps[r.idx] = dead_value(stamp);
-          ++dold;
-          ++dead_delta;
-        } else {
-          t.amps[r.idx] = nY;
-        }
-      } else if (fabs(nY) < eps) {
-        ++dnew;
-      } else if (r.state == DEAD_OLD) {
-        // Revive a dropped key as a fresh entry past the scan range and point
-        // its slot there.  (Reviving in place would let the old index's scan
-        // thread, if it runs later in this step, see a live entry that was
-        // not live when the step began and rotate the pair a second time.)
-        const unsigned long long idx = aggregated_add(&t.cnt->n_tail);
-        if (idx < t.cap_n) {
-          t.keys[idx] = Y;
-          t.amps[idx] = nY;
-          if (RECORD) t.born[idx] = (unsigned int)k;
-          t.slots[r.slot].idx = idx;
-        } else {
-          raise_error(t.cnt, ERR_CAPACITY);
-        }
-        ++cre;
-      } else {
-        insert_new(t, Y, nY, (unsigned int)k, r.slot, RECORD, false);
-        ++cre;
-      }
-    }
+    for (unsigned long long base = warp * 32ull; base < n; base += nwarps * 32ull)
+      forward_entry<G, RECORD>(t, f, k, eps, stamp, tape, base + lane, base + lane < n, sc);
   }
-  block_add_counts(t.cnt, rot, cre, dnew, dold, dead_delta);
+  block_add_counts(t.cnt, sc.rot, sc.cre, sc.dnew, sc.dold, sc.dead_delta);
   if (last_block_arrive(t.cnt) && threadIdx.x == 0) {
     Counters* c = t.cnt;
     c->done = 0u;
@@ -198,7 +109,7 @@ __global__ void __launch_bounds__(kThreads) k_rehash(Table t) {
   const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
   for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     const unsigned long long key = t.keys[i];
-    const unsigned long long s = claim_slot(t, key, mix64(key));
+    const unsigned long long s = claim_slot(t, key, home_slot(t, key));
     if (s != ~0ull) t.slots[s].idx = i;
   }
 }
@@ -237,9 +148,10 @@ __global__ void k_reset(Table t, unsigned long long hf) {
   t.keys[0] = hf;
   t.amps[0] = 1.0;
   if (t.born) t.born[0] = BORN_INITIAL;
-  const unsigned long long s = mix64(hf) & t.slot_mask;
+  const unsigned long long s = home_slot(t, hf);
   t.slots[s].key = hf;
   t.slots[s].idx = 0;
+  filter_add(t, hf);
   c->n_tail = 1;
   c->n_scan = 1;
   c->stop_k = -1;
@@ -296,6 +208,58 @@ cudaError_t launch_finish_rebuild(const Table& t, cudaStream_t st) {
 cudaError_t launch_export(const Table& t, unsigned long long cap, unsigned long long* keys, double* amps,
                           double* sigma, int grid, cudaStream_t st) {
   k_export<<<grid, kThreads, 0, st>>>(t, cap, keys, amps, sigma);
+  return cudaGetLastError();
+}
+
+}  // namespace ucc
+
+namespace ucc {
+
+namespace {
+
+// Load a snapshot (live keys and amplitudes, unordered) as entries [0, n).
+__global__ void __launch_bounds__(256) k_restore(Table t, const unsigned long long* keys, const double* amps,
+                                                  unsigned long long n) {
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n && i < t.cap_n;
+       i += stride) {
+    t.keys[i] = keys[i];
+    t.amps[i] = amps[i];
+    t.born[i] = BORN_INITIAL;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    Counters* c = t.cnt;
+    const unsigned long long m = n < t.cap_n ? n : t.cap_n;
+    c->n_tail = m;
+    c->n_scan = m;
+    c->new_n = m;
+    c->n_dead = 0;
+    c->stop_k = -1;
+  }
+}
+
+// Copy the adjoint vector of `src` onto the live entries of `dst` by key
+// (zero where src has no live entry).
+__global__ void __launch_bounds__(256) k_transfer_lambda(Table dst, Table src) {
+  const unsigned long long n = min(*((volatile unsigned long long*)&dst.cnt->n_tail), dst.cap_n);
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    if (is_dead(dst.amps[i])) continue;
+    Lookup r = find1(src, dst.keys[i], 0u);
+    dst.lam[i] = (r.state == ALIVE) ? src.lam[r.idx] : 0.0;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_restore(const Table& t, const unsigned long long* keys, const double* amps, unsigned long long n,
+                           int grid, cudaStream_t st) {
+  k_restore<<<grid, 256, 0, st>>>(t, keys, amps, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_transfer_lambda(const Table& dst, const Table& src, int grid, cudaStream_t st) {
+  k_transfer_lambda<<<grid, 256, 0, st>>>(dst, src);
   return cudaGetLastError();
 }
 

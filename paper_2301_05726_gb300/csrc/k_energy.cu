@@ -12,7 +12,7 @@
 // <pq||rs> = <pq|rs> - <pq|sr>.  sgn is the Jordan-Wigner sign of the
 // operator string on I.
 
-#include "ucc_device.cuh"
+#include "ucc_steps.cuh"
 
 namespace ucc {
 
@@ -20,66 +20,6 @@ namespace {
 
 constexpr int kWarps = 8;
 constexpr int kThreads = kWarps * 32;
-constexpr int kMaxSpin = 32;                          // spin-orbitals of one spin
-constexpr int kMaxPairs = kMaxSpin * (kMaxSpin - 1) / 2;  // same-spin empty pairs
-
-struct WarpLists {
-  unsigned char occ[2][kMaxSpin];
-  unsigned char emp[2][kMaxSpin];
-  int n_occ[2], n_emp[2];
-  unsigned short pairs[2][kMaxPairs];  // same-spin empty pairs (r | s << 8), r < s
-  int n_pairs[2];
-};
-
-__device__ __forceinline__ unsigned long long below(int p) { return (1ull << p) - 1ull; }
-
-// (ab|cd) in chemist notation over spatial orbitals.
-__device__ __forceinline__ double chem(const Integrals& in, int a, int b, int c, int d) {
-  const int n = in.n;
-  return __ldg(&in.g[((a * n + b) * n + c) * n + d]);
-}
-
-// <rs||pq> over spin-orbitals.
-__device__ __forceinline__ double anti(const Integrals& in, int r, int s, int p, int q) {
-  double v = 0.0;
-  if (((r ^ p) & 1) == 0 && ((s ^ q) & 1) == 0) v += chem(in, r >> 1, p >> 1, s >> 1, q >> 1);
-  if (((r ^ q) & 1) == 0 && ((s ^ p) & 1) == 0) v -= chem(in, r >> 1, q >> 1, s >> 1, p >> 1);
-  return v;
-}
-
-__device__ __forceinline__ double h_so(const Integrals& in, int p, int q) {
-  if ((p ^ q) & 1) return 0.0;
-  return __ldg(&in.h[(p >> 1) * in.n + (q >> 1)]);
-}
-
-// Sign of a+_r a+_s a_q a_p |I> (p, q occupied; r, s empty; all distinct).
-__device__ __forceinline__ int double_parity(unsigned long long I, int p, int q, int r, int s) {
-  const unsigned long long msk = below(p) ^ below(q) ^ below(r) ^ below(s);
-  return (__popcll(I & msk) + (p < q) + (p < s) + (q < s) + (p < r) + (q < r) + (s < r)) & 1;
-}
-
-// Sign of a+_r a_p |I>.
-__device__ __forceinline__ int single_parity(unsigned long long I, int p, int r) {
-  return (__popcll(I & (below(p) ^ below(r))) + (p < r)) & 1;
-}
-
-__device__ __forceinline__ bool lookup_live(const Table& t, unsigned long long key, double* amp) {
-  unsigned long long h = mix64(key) & t.slot_mask;
-  for (int step = 0; step < MAX_PROBE; ++step) {
-    const Slot s = t.slots[h];
-    if (s.key == key) {
-      const double a = t.amps[s.idx];
-      if (is_dead(a)) return false;
-      *amp = a;
-      return true;
-    }
-    if (s.key == 0ull) return false;
-    h = (h + 1) & t.slot_mask;
-  }
-  raise_error(t.cnt, ERR_PROBE_BOUND);
-  return false;
-}
-
 __global__ void __launch_bounds__(kThreads) k_sigma(Table t, Integrals in) {
   __shared__ WarpLists lists[kWarps];
   const int w = threadIdx.x >> 5;
@@ -94,111 +34,7 @@ __global__ void __launch_bounds__(kThreads) k_sigma(Table t, Integrals in) {
     const double cI = t.amps[e];
     if (is_dead(cI)) continue;  // warp-uniform
     const unsigned long long I = t.keys[e];
-    if (lane == 0) {
-      for (int sp = 0; sp < 2; ++sp) L.n_occ[sp] = L.n_emp[sp] = 0;
-      for (int p = 0; p < in.n_so; ++p) {
-        const int sp = p & 1;
-        if ((I >> p) & 1ull)
-          L.occ[sp][L.n_occ[sp]++] = (unsigned char)p;
-        else
-          L.emp[sp][L.n_emp[sp]++] = (unsigned char)p;
-      }
-    }
-    __syncwarp();
-    for (int sp = 0; sp < 2; ++sp) {
-      const int m = L.n_emp[sp];
-      const int np = m * (m - 1) / 2;
-      for (int u = lane; u < np; u += 32) {
-        // u -> (x, y), x < y, row-major over the strict upper triangle
-        int x = 0, rem = u;
-        while (rem >= m - 1 - x) {
-          rem -= m - 1 - x;
-          ++x;
-        }
-        const int y = x + 1 + rem;
-        L.pairs[sp][u] = (unsigned short)(L.emp[sp][x] | (L.emp[sp][y] << 8));
-      }
-      if (lane == 0) L.n_pairs[sp] = np;
-    }
-    __syncwarp();
-
-    double part = 0.0;
-    // Diagonal: lanes over the first index p.
-    {
-      double d = 0.0;
-      for (int sp = 0; sp < 2; ++sp)
-        for (int x = lane; x < L.n_occ[sp]; x += 32) {
-          const int p = L.occ[sp][x];
-          d += h_so(in, p, p);
-          for (int sq = 0; sq < 2; ++sq)
-            for (int y = 0; y < L.n_occ[sq]; ++y) {
-              const int q = L.occ[sq][y];
-              if (q != p) d += 0.5 * anti(in, p, q, p, q);
-            }
-        }
-      part += d * cI;
-    }
-    // Singles p -> r, same spin.
-    for (int sp = 0; sp < 2; ++sp) {
-      const int no = L.n_occ[sp], ne = L.n_emp[sp];
-      for (int u = lane; u < no * ne; u += 32) {
-        const int p = L.occ[sp][u / ne];
-        const int r = L.emp[sp][u % ne];
-        const unsigned long long J = I ^ ((1ull << p) | (1ull << r));
-        double cJ;
-        ++probes;
-        if (!lookup_live(t, J, &cJ)) continue;
-        ++hits;
-        double v = h_so(in, r, p);
-        for (int sk = 0; sk < 2; ++sk)
-          for (int y = 0; y < L.n_occ[sk]; ++y) {
-            const int kk = L.occ[sk][y];
-            if (kk != p) v += anti(in, r, kk, p, kk);
-          }
-        part += (single_parity(I, p, r) ? -v : v) * cJ;
-      }
-    }
-    // Doubles: same-spin (p < q from one spin, r < s from the same spin).
-    for (int sp = 0; sp < 2; ++sp) {
-      const int no = L.n_occ[sp];
-      const int np = L.n_pairs[sp];
-      for (int x = 0; x < no; ++x)
-        for (int y = x + 1; y < no; ++y) {
-          const int p = L.occ[sp][x], q = L.occ[sp][y];
-          const unsigned long long hole = (1ull << p) | (1ull << q);
-          for (int u = lane; u < np; u += 32) {
-            const unsigned short pr = L.pairs[sp][u];
-            const int r = pr & 0xFF, s = pr >> 8;
-            const unsigned long long J = I ^ (hole | (1ull << r) | (1ull << s));
-            double cJ;
-            ++probes;
-            if (!lookup_live(t, J, &cJ)) continue;
-            ++hits;
-            const double v = anti(in, r, s, p, q);
-            part += (double_parity(I, p, q, r, s) ? -v : v) * cJ;
-          }
-        }
-    }
-    // Doubles: opposite spin (p alpha, q beta -> r alpha, s beta).
-    {
-      const int noa = L.n_occ[0], nob = L.n_occ[1], nea = L.n_emp[0], neb = L.n_emp[1];
-      const int nE = nea * neb;
-      for (int x = 0; x < noa; ++x)
-        for (int y = 0; y < nob; ++y) {
-          const int p = L.occ[0][x], q = L.occ[1][y];
-          const unsigned long long hole = (1ull << p) | (1ull << q);
-          for (int u = lane; u < nE; u += 32) {
-            const int r = L.emp[0][u / neb], s = L.emp[1][u % neb];
-            const unsigned long long J = I ^ (hole | (1ull << r) | (1ull << s));
-            double cJ;
-            ++probes;
-            if (!lookup_live(t, J, &cJ)) continue;
-            ++hits;
-            const double v = anti(in, r, s, p, q);
-            part += (double_parity(I, p, q, r, s) ? -v : v) * cJ;
-          }
-        }
-    }
+    const double part = sigma_entry(t, in, L, I, cI, lane, probes, hits);
     const double sig = warp_sum(part);
     if (lane == 0) {
       t.sigma[e] = sig;

@@ -2,11 +2,12 @@
 // determinants are stored after a factor, keep the N_CUT of largest |c|
 // (ties: smaller key first) and drop the rest.
 //
-// Exact selection by radix passes over 8-bit digits, most significant first:
+// Exact selection by radix passes over 11-bit digits, most significant first:
 // |c| as its IEEE-754 bit pattern (monotone in |c| for non-negative values)
 // from the top bin down, then, only if several entries share the threshold
-// value, the determinant key from the bottom bin up.  Each pass is one
-// histogram kernel over the live entries and one single-warp pick kernel.
+// value, the determinant key from the bottom bin up.  Each pass is one kernel:
+// every block histograms its share of the live entries in shared memory, and
+// the last block to finish picks the bin that holds the target rank.
 
 #include "ucc_device.cuh"
 
@@ -15,23 +16,99 @@ namespace ucc {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kBins = 256;
+constexpr int kDigit = 11;
+constexpr int kBins = 1 << kDigit;            // 2048
+constexpr int kPasses = (64 + kDigit - 1) / kDigit;  // 6 (covers 64 bits)
+static_assert(kBins <= sizeof(SelectState::hist) / sizeof(unsigned long long), "histogram size");
 
 __device__ __forceinline__ unsigned long long mag_bits(double a) {
   return (unsigned long long)__double_as_longlong(a) & 0x7FFFFFFFFFFFFFFFull;
 }
 
-// Histogram of digit `d` of |c| (phase 0) or of the key among |c| == T
-// entries (phase 1), restricted to entries whose higher digits equal the
-// prefix chosen so far.
-__global__ void __launch_bounds__(kThreads) k_select_hist(Table t, SelectState* sel, int phase, int d) {
+__device__ __forceinline__ int digit_shift(int pass) { return 64 - kDigit * (pass + 1) < 0 ? 0 : 64 - kDigit * (pass + 1); }
+__device__ __forceinline__ unsigned long long digit_of(unsigned long long v, int pass) {
+  const int top = 64 - kDigit * pass;          // bits [shift, top) form this digit
+  const int shift = digit_shift(pass);
+  const int width = top - shift;
+  return (v >> shift) & ((1ull << width) - 1ull);
+}
+__device__ __forceinline__ unsigned long long high_mask(int pass) {
+  // bits above this pass's digit, i.e. the digits already fixed
+  const int top = 64 - kDigit * pass;
+  return top >= 64 ? 0ull : (~0ull << top);
+}
+
+// The last block turns the global histogram into the next digit of the
+// threshold: phase 0 walks bins from the top (largest |c| first), phase 1 from
+// the bottom (smallest key first).
+__device__ void pick_bin(SelectState* sel, int phase, int pass, int nbins) {
+  __shared__ unsigned long long s_scan[kThreads];
+  const int per = (nbins + kThreads - 1) / kThreads;
+  unsigned long long local = 0;
+  for (int j = 0; j < per; ++j) {
+    const int o = threadIdx.x * per + j;  // visiting order
+    if (o >= nbins) break;
+    const int b = phase == 0 ? nbins - 1 - o : o;
+    local += ld_cg(&sel->hist[b]);
+  }
+  s_scan[threadIdx.x] = local;
+  __syncthreads();
+  // inclusive scan (Hillis-Steele) over the 256 partial sums
+  for (int off = 1; off < kThreads; off <<= 1) {
+    unsigned long long v = threadIdx.x >= off ? s_scan[threadIdx.x - off] : 0ull;
+    __syncthreads();
+    s_scan[threadIdx.x] += v;
+    __syncthreads();
+  }
+  const unsigned long long incl = s_scan[threadIdx.x];
+  const unsigned long long before = incl - local;
+  const unsigned long long target = phase == 0 ? sel->target : sel->key_target;
+  if (before < target && target <= incl) {
+    unsigned long long cum = before;
+    for (int j = 0; j < per; ++j) {
+      const int o = threadIdx.x * per + j;
+      if (o >= nbins) break;
+      const int b = phase == 0 ? nbins - 1 - o : o;
+      const unsigned long long cnt = ld_cg(&sel->hist[b]);
+      if (cum + cnt >= target) {
+        const unsigned long long rest = target - cum;
+        const int shift = digit_shift(pass);
+        if (phase == 0) {
+          sel->prefix |= (unsigned long long)b << shift;
+          sel->target = rest;
+          if (pass == kPasses - 1) {
+            sel->count_eq = cnt;
+            sel->need_keys = cnt > rest ? 1 : 0;
+            sel->key_target = rest;
+          }
+        } else {
+          sel->key_prefix |= (unsigned long long)b << shift;
+          sel->key_target = rest;
+        }
+        break;
+      }
+      cum += cnt;
+    }
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < nbins; b += blockDim.x) sel->hist[b] = 0;
+}
+
+// One radix pass: histogram of the pass's digit of |c| (phase 0) or of the
+// key among |c| == threshold entries (phase 1), restricted to entries whose
+// already-fixed digits match, then the pick in the last block.
+__global__ void __launch_bounds__(kThreads) k_select_pass(Table t, SelectState* sel, int phase, int pass) {
   __shared__ unsigned int h[kBins];
-  if (phase == 1 && !sel->need_keys) return;
-  for (int b = threadIdx.x; b < kBins; b += blockDim.x) h[b] = 0;
+  __shared__ int s_skip;
+  if (threadIdx.x == 0) s_skip = (phase == 1 && !*((volatile int*)&sel->need_keys)) ? 1 : 0;
+  __syncthreads();
+  if (s_skip) return;  // uniform over the grid: no tie to break
+  const int top = 64 - kDigit * pass;
+  const int nbins = 1 << (top - digit_shift(pass));
+  for (int b = threadIdx.x; b < nbins; b += blockDim.x) h[b] = 0;
   __syncthreads();
   const unsigned long long n = min(*((volatile unsigned long long*)&t.cnt->n_tail), t.cap_n);
-  const int shift = 8 * d;
-  const unsigned long long hi_mask = (d == 7) ? 0ull : (~0ull << (shift + 8));
+  const unsigned long long hm = high_mask(pass);
   const unsigned long long T = sel->prefix;
   const unsigned long long kp = sel->key_prefix;
   const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
@@ -40,67 +117,22 @@ __global__ void __launch_bounds__(kThreads) k_select_hist(Table t, SelectState* 
     if (is_dead(a)) continue;
     const unsigned long long u = mag_bits(a);
     if (phase == 0) {
-      if ((u & hi_mask) != (T & hi_mask)) continue;
-      atomicAdd(&h[(u >> shift) & 0xFF], 1u);
+      if ((u & hm) != (T & hm)) continue;
+      atomicAdd(&h[digit_of(u, pass)], 1u);
     } else {
       if (u != T) continue;
       const unsigned long long key = t.keys[i];
-      if ((key & hi_mask) != (kp & hi_mask)) continue;
-      atomicAdd(&h[(key >> shift) & 0xFF], 1u);
+      if ((key & hm) != (kp & hm)) continue;
+      atomicAdd(&h[digit_of(key, pass)], 1u);
     }
   }
   __syncthreads();
-  for (int b = threadIdx.x; b < kBins; b += blockDim.x)
+  for (int b = threadIdx.x; b < nbins; b += blockDim.x)
     if (h[b]) atomicAdd(&sel->hist[b], (unsigned long long)h[b]);
-}
-
-// Pick the bin holding the target-th element.  phase 0 walks |c| bins from
-// the top (largest first); phase 1 walks key bins from the bottom.
-__global__ void k_select_pick(SelectState* sel, int phase, int d) {
-  if (phase == 1 && !sel->need_keys) return;
-  const int lane = threadIdx.x;  // one warp; lane owns 8 consecutive bins
-  unsigned long long c[8];
-  unsigned long long local = 0;
-  for (int j = 0; j < 8; ++j) {
-    // phase 0 visits bins 255..0, phase 1 visits 0..255
-    const int b = phase == 0 ? (kBins - 1 - (lane * 8 + j)) : (lane * 8 + j);
-    c[j] = sel->hist[b];
-    local += c[j];
+  if (last_block_arrive(t.cnt)) {
+    pick_bin(sel, phase, pass, nbins);
+    if (threadIdx.x == 0) t.cnt->done = 0u;
   }
-  // inclusive scan over lanes
-  unsigned long long incl = local;
-  for (int o = 1; o < 32; o <<= 1) {
-    unsigned long long v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-    if (lane >= o) incl += v;
-  }
-  const unsigned long long before = incl - local;
-  const unsigned long long target = phase == 0 ? sel->target : sel->key_target;
-  const bool mine = before < target && target <= incl;
-  if (mine) {
-    unsigned long long cum = before;
-    for (int j = 0; j < 8; ++j) {
-      if (cum + c[j] >= target) {
-        const int b = phase == 0 ? (kBins - 1 - (lane * 8 + j)) : (lane * 8 + j);
-        const unsigned long long rest = target - cum;  // rank inside the bin
-        if (phase == 0) {
-          sel->prefix |= (unsigned long long)b << (8 * d);
-          sel->target = rest;
-          if (d == 0) {
-            sel->count_eq = c[j];
-            sel->need_keys = c[j] > rest ? 1 : 0;
-            sel->key_target = rest;
-          }
-        } else {
-          sel->key_prefix |= (unsigned long long)b << (8 * d);
-          sel->key_target = rest;
-        }
-        break;
-      }
-      cum += c[j];
-    }
-  }
-  __syncwarp();
-  for (int j = 0; j < 8; ++j) sel->hist[lane * 8 + j] = 0;
 }
 
 // Drop every live entry outside the kept set; record drops on the tape.
@@ -149,26 +181,27 @@ __global__ void __launch_bounds__(kThreads) k_select_mark(Table t, SelectState* 
 }
 
 __global__ void k_select_init(SelectState* sel, unsigned long long n_cut) {
-  sel->prefix = 0;
-  sel->target = n_cut;
-  sel->key_prefix = 0;
-  sel->key_target = 0;
-  sel->need_keys = 0;
-  sel->count_eq = 0;
-  for (int b = 0; b < kBins; ++b) sel->hist[b] = 0;
+  if (threadIdx.x == 0) {
+    sel->prefix = 0;
+    sel->target = n_cut;
+    sel->key_prefix = 0;
+    sel->key_target = 0;
+    sel->need_keys = 0;
+    sel->count_eq = 0;
+  }
+  for (int b = threadIdx.x; b < kBins; b += blockDim.x) sel->hist[b] = 0;
 }
 
 }  // namespace
 
 cudaError_t launch_select_cut(const Table& t, SelectState* sel, unsigned long long n_cut, unsigned int stamp,
                               int record, const Tape& tape, int k, int grid, cudaStream_t st, long long* launches) {
-  k_select_init<<<1, 1, 0, st>>>(sel, n_cut);
+  k_select_init<<<1, kThreads, 0, st>>>(sel, n_cut);
   *launches += 1;
   for (int phase = 0; phase < 2; ++phase)
-    for (int d = 7; d >= 0; --d) {
-      k_select_hist<<<grid, kThreads, 0, st>>>(t, sel, phase, d);
-      k_select_pick<<<1, 32, 0, st>>>(sel, phase, d);
-      *launches += 2;
+    for (int pass = 0; pass < kPasses; ++pass) {
+      k_select_pass<<<grid, kThreads, 0, st>>>(t, sel, phase, pass);
+      *launches += 1;
     }
   if (record)
     k_select_mark<true><<<grid, kThreads, 0, st>>>(t, sel, stamp, tape, k);

@@ -78,7 +78,9 @@ struct Arrays {
   double* lam = nullptr;
   double* sigma = nullptr;
   Slot* slots = nullptr;
+  unsigned int* filt = nullptr;  // 8 bits per slot
   void release() {
+    dfree(filt);
     dfree(keys);
     dfree(amps);
     dfree(born);
@@ -95,9 +97,46 @@ struct Arrays {
     UCC_TRY(dalloc(&lam, cn));
     UCC_TRY(dalloc(&sigma, cn));
     UCC_TRY(dalloc(&slots, ns));
+    UCC_TRY(dalloc(&filt, ns / 4));
     cap_n = cn;
     n_slots = ns;
     return UCC_OK;
+  }
+};
+
+// A wavefunction table: entry arrays (current, and a spare for rebuilds) and
+// its device counters with a pinned host mirror.
+struct TableSet {
+  Arrays cur, spare;
+  Counters* d_cnt = nullptr;
+  Counters* h_cnt = nullptr;
+  void release() {
+    cur.release();
+    spare.release();
+    dfree(d_cnt);
+    if (h_cnt) cudaFreeHost(h_cnt);
+    h_cnt = nullptr;
+  }
+  ucc_status init() {
+    UCC_TRY(dalloc(&d_cnt, 1));
+    if (cudaMallocHost((void**)&h_cnt, sizeof(Counters)) != cudaSuccess) {
+      h_cnt = nullptr;
+      return fail(UCC_ENOMEM, "pinned host allocation failed");
+    }
+    std::memset(h_cnt, 0, sizeof(Counters));
+    return UCC_OK;
+  }
+};
+
+// psi (live keys and amplitudes) at the start of a gradient segment.
+struct Snapshot {
+  unsigned long long n = 0;
+  unsigned long long* keys = nullptr;
+  double* amps = nullptr;
+  void release() {
+    dfree(keys);
+    dfree(amps);
+    n = 0;
   }
 };
 
@@ -121,11 +160,11 @@ struct ucc_ctx {
   double* d_grad = nullptr;
   double* d_partials = nullptr;
   int partial_cap = 0;
-  Counters* d_cnt = nullptr;
-  Counters* h_cnt = nullptr;  // pinned mirror
   SelectState* d_sel = nullptr;
-  Arrays cur, spare;
-  // kill tape
+  TableSet ts[2];  // ts[main] holds psi; the other is the gradient's work table
+  int main = 0;
+  std::vector<Snapshot> snaps;
+  // kill tape of the segment being reversed
   unsigned long long* t_key = nullptr;
   double* t_val = nullptr;
   unsigned int* t_born = nullptr;
@@ -135,21 +174,26 @@ struct ucc_ctx {
   bool have_psi = false;
   bool have_sigma = false;
   cudaEvent_t ev[6] = {};
+  cudaEvent_t kev[2] = {};  // around each chunk of factor launches
   ucc_stats stats{};
   int probe_width = 1;
   long long launches = 0;
+  long long cut_total = 0;
 
-  Table table() const {
+  Table table(const TableSet& s) const {
     Table t;
-    t.keys = cur.keys;
-    t.amps = cur.amps;
-    t.born = cur.born;
-    t.lam = cur.lam;
-    t.sigma = cur.sigma;
-    t.slots = cur.slots;
-    t.slot_mask = cur.n_slots - 1;
-    t.cap_n = cur.cap_n;
-    t.cnt = d_cnt;
+    t.keys = s.cur.keys;
+    t.amps = s.cur.amps;
+    t.born = s.cur.born;
+    t.lam = s.cur.lam;
+    t.sigma = s.cur.sigma;
+    t.slots = s.cur.slots;
+    t.slot_mask = s.cur.n_slots - 1;
+    t.slot_shift = 64 - __builtin_ctzll(s.cur.n_slots);
+    t.filt = s.cur.filt;
+    t.filt_shift = 64 - (__builtin_ctzll(s.cur.n_slots) + 3);
+    t.cap_n = s.cur.cap_n;
+    t.cnt = s.d_cnt;
     t.partials = d_partials;
     return t;
   }
@@ -192,8 +236,8 @@ Factor make_factor(int i, int j, int a, int b, double th) {
   return f;
 }
 
-ucc_status check_device_error(ucc_ctx* c) {
-  int err = c->h_cnt->error;
+ucc_status check_device_error(const Counters& h) {
+  int err = h.error;
   if (!err) return UCC_OK;
   std::string msg = "device error word:";
   if (err & ERR_PROBE_BOUND) msg += " probe-bound";
@@ -203,10 +247,10 @@ ucc_status check_device_error(ucc_ctx* c) {
   return fail((err & (ERR_CAPACITY | ERR_TAPE_FULL)) ? UCC_ECAPACITY : UCC_ECUDA, msg);
 }
 
-ucc_status read_counters(ucc_ctx* c) {
-  CUDA_TRY(cudaMemcpyAsync(c->h_cnt, c->d_cnt, sizeof(Counters), cudaMemcpyDeviceToHost, c->stream));
+ucc_status read_counters(ucc_ctx* c, TableSet& s) {
+  CUDA_TRY(cudaMemcpyAsync(s.h_cnt, s.d_cnt, sizeof(Counters), cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(cudaStreamSynchronize(c->stream));
-  return check_device_error(c);
+  return check_device_error(*s.h_cnt);
 }
 
 ucc_status ensure_partials(ucc_ctx* c, int grid) {
@@ -224,36 +268,40 @@ unsigned long long slots_for(unsigned long long cap_n) {
 
 // Copy live entries into arrays of capacity new_cap (dropping dead entries) and
 // rebuild the hash.  Counters are updated on the device.
-ucc_status rebuild(ucc_ctx* c, unsigned long long new_cap) {
-  if (c->opt.max_entries > 0 && new_cap > 2ull * (unsigned long long)c->opt.max_entries)
-    new_cap = std::max<unsigned long long>(2ull * (unsigned long long)c->opt.max_entries, 64);
+ucc_status rebuild(ucc_ctx* c, TableSet& s, unsigned long long new_cap) {
   unsigned long long ns = slots_for(new_cap);
-  if (c->spare.cap_n != new_cap || c->spare.n_slots != ns) {
-    c->spare.release();
-    ucc_status s = c->spare.allocate(new_cap, ns);
-    if (s != UCC_OK) {
-      c->spare.release();
+  if (s.spare.cap_n != new_cap || s.spare.n_slots != ns) {
+    s.spare.release();
+    ucc_status st = s.spare.allocate(new_cap, ns);
+    if (st != UCC_OK) {
+      s.spare.release();
       return fail(UCC_ECAPACITY, "cannot allocate " + std::to_string(new_cap) + " entries: " + g_last_error);
     }
   }
-  Table from = c->table();
+  Table from = c->table(s);
   Table to = from;
-  to.keys = c->spare.keys;
-  to.amps = c->spare.amps;
-  to.born = c->spare.born;
-  to.lam = c->spare.lam;
-  to.sigma = c->spare.sigma;
-  to.slots = c->spare.slots;
+  to.keys = s.spare.keys;
+  to.amps = s.spare.amps;
+  to.born = s.spare.born;
+  to.lam = s.spare.lam;
+  to.sigma = s.spare.sigma;
+  to.slots = s.spare.slots;
   to.slot_mask = ns - 1;
+  to.slot_shift = 64 - __builtin_ctzll(ns);
+  to.filt = s.spare.filt;
+  to.filt_shift = 64 - (__builtin_ctzll(ns) + 3);
   to.cap_n = new_cap;
-  CUDA_TRY(cudaMemsetAsync(&c->d_cnt->new_n, 0, sizeof(unsigned long long), c->stream));
+  CUDA_TRY(cudaMemsetAsync(&s.d_cnt->new_n, 0, sizeof(unsigned long long), c->stream));
   CUDA_TRY(cudaMemsetAsync(to.slots, 0, ns * sizeof(Slot), c->stream));
+  CUDA_TRY(cudaMemsetAsync(to.filt, 0, ns / 4 * sizeof(unsigned int), c->stream));
   int grid = c->full_grid();
   CUDA_TRY(launch_compact(from, to, 1, grid, c->stream));
   CUDA_TRY(launch_rehash(to, grid, c->stream));
   CUDA_TRY(launch_finish_rebuild(to, c->stream));
   c->launches += 3;
-  std::swap(c->cur, c->spare);
+  std::swap(s.cur, s.spare);
+  // After growth the old, smaller arrays are not reused: free them now.
+  if (s.spare.cap_n != s.cur.cap_n) s.spare.release();
   c->stats.rebuilds++;
   return UCC_OK;
 }
@@ -284,21 +332,59 @@ ucc_status ensure_tape(ucc_ctx* c, unsigned long long need) {
   return UCC_OK;
 }
 
-ucc_status reset_state(ucc_ctx* c, bool record) {
-  if (c->cur.cap_n == 0) UCC_TRY(c->cur.allocate(1 << 12, slots_for(1 << 12)));
-  CUDA_TRY(cudaMemsetAsync(c->d_cnt, 0, sizeof(Counters), c->stream));
-  CUDA_TRY(cudaMemsetAsync(c->cur.slots, 0, c->cur.n_slots * sizeof(Slot), c->stream));
+unsigned long long reference_key(const ucc_ctx* c) {
   unsigned long long hf = 0;
   for (int s = 0; s < c->n_alpha; ++s) hf |= 1ull << (2 * s);
   for (int s = 0; s < c->n_beta; ++s) hf |= 1ull << (2 * s + 1);
-  CUDA_TRY(launch_reset(c->table(), hf, c->stream));
+  return hf;
+}
+
+// psi = {reference: 1.0} in table s.
+ucc_status reset_table(ucc_ctx* c, TableSet& s) {
+  if (s.cur.cap_n == 0) UCC_TRY(s.cur.allocate(1 << 12, slots_for(1 << 12)));
+  CUDA_TRY(cudaMemsetAsync(s.d_cnt, 0, sizeof(Counters), c->stream));
+  CUDA_TRY(cudaMemsetAsync(s.cur.slots, 0, s.cur.n_slots * sizeof(Slot), c->stream));
+  CUDA_TRY(cudaMemsetAsync(s.cur.filt, 0, s.cur.n_slots / 4 * sizeof(unsigned int), c->stream));
+  CUDA_TRY(launch_reset(c->table(s), reference_key(c), c->stream));
   c->launches++;
-  if (record) {
-    UCC_TRY(ensure_tape(c, 1 << 16));
-    CUDA_TRY(cudaMemsetAsync(c->t_off, 0, sizeof(unsigned long long), c->stream));
-  }
-  c->have_psi = false;
-  c->have_sigma = false;
+  return UCC_OK;
+}
+
+// Start the kill tape of a segment that begins at factor k0.
+ucc_status reset_tape(ucc_ctx* c, TableSet& s, int k0) {
+  UCC_TRY(ensure_tape(c, 1 << 16));
+  CUDA_TRY(cudaMemsetAsync(&s.d_cnt->tape_n, 0, sizeof(unsigned long long), c->stream));
+  CUDA_TRY(cudaMemsetAsync(c->t_off + k0, 0, sizeof(unsigned long long), c->stream));
+  return UCC_OK;
+}
+
+// Load a snapshot into table s (its previous contents are discarded).
+ucc_status load_snapshot(ucc_ctx* c, TableSet& s, const Snapshot& snap) {
+  const unsigned long long cap = std::max<unsigned long long>(4 * snap.n, 1 << 12);
+  if (s.cur.cap_n < cap) UCC_TRY(s.cur.allocate(cap, slots_for(cap)));
+  CUDA_TRY(cudaMemsetAsync(s.d_cnt, 0, sizeof(Counters), c->stream));
+  CUDA_TRY(cudaMemsetAsync(s.cur.slots, 0, s.cur.n_slots * sizeof(Slot), c->stream));
+  CUDA_TRY(cudaMemsetAsync(s.cur.filt, 0, s.cur.n_slots / 4 * sizeof(unsigned int), c->stream));
+  const int grid = c->full_grid();
+  CUDA_TRY(launch_restore(c->table(s), snap.keys, snap.amps, snap.n, grid, c->stream));
+  CUDA_TRY(launch_rehash(c->table(s), grid, c->stream));
+  c->launches += 2;
+  return read_counters(c, s);
+}
+
+// Copy the live entries of table s into a new snapshot.
+ucc_status take_snapshot(ucc_ctx* c, TableSet& s, Snapshot* out) {
+  UCC_TRY(read_counters(c, s));
+  const unsigned long long live = s.h_cnt->n_tail - s.h_cnt->n_dead;
+  out->release();
+  UCC_TRY(dalloc(&out->keys, live));
+  UCC_TRY(dalloc(&out->amps, live));
+  out->n = live;
+  CUDA_TRY(cudaMemsetAsync(&s.d_cnt->new_n, 0, sizeof(unsigned long long), c->stream));
+  CUDA_TRY(launch_export(c->table(s), live, out->keys, out->amps, nullptr, c->full_grid(), c->stream));
+  c->launches++;
+  UCC_TRY(read_counters(c, s));
+  if (s.h_cnt->new_n != live) return fail(UCC_ECUDA, "snapshot count mismatch");
   return UCC_OK;
 }
 
@@ -311,95 +397,138 @@ int pick_probe_width(ucc_ctx* c) {
 // Make room for the next factor: it may append one entry per stored entry
 // (and, in gradient runs, drop as many onto the tape).  Compacts when a
 // quarter of the stored entries are dropped ones.
-ucc_status ensure_room(ucc_ctx* c, bool record) {
-  UCC_TRY(read_counters(c));
-  const Counters h = *c->h_cnt;  // copy: later reads overwrite the mirror
+ucc_status ensure_room(ucc_ctx* c, TableSet& s, bool record) {
+  UCC_TRY(read_counters(c, s));
+  const Counters h = *s.h_cnt;  // copy: later reads overwrite the mirror
   const unsigned long long live = h.n_tail - h.n_dead;
   if (c->opt.max_entries > 0 && live > (unsigned long long)c->opt.max_entries)
     return fail(UCC_ECAPACITY, "wavefunction exceeds max_entries (" + std::to_string(live) + " live)");
-  const bool room = 2 * h.n_tail <= c->cur.cap_n && 8 * h.n_tail <= 3 * c->cur.n_slots;
+  const bool room = 2 * h.n_tail <= s.cur.cap_n && 8 * h.n_tail <= 3 * s.cur.n_slots;
   const bool sparse = h.n_dead > 4096 && h.n_dead * 4 > h.n_tail;
   if (record) UCC_TRY(ensure_tape(c, h.tape_n + 2 * live + (1 << 12)));
   if (!room || sparse) {
-    unsigned long long cap = c->cur.cap_n;
-    if (2 * live > cap || 8 * live > 3 * c->cur.n_slots) cap = std::max<unsigned long long>(4 * live, 1 << 12);
-    UCC_TRY(rebuild(c, cap));
-    UCC_TRY(read_counters(c));
+    unsigned long long cap = s.cur.cap_n;
+    if (2 * live > cap || 8 * live > 3 * s.cur.n_slots) cap = std::max<unsigned long long>(4 * live, 1 << 12);
+    UCC_TRY(rebuild(c, s, cap));
+    UCC_TRY(read_counters(c, s));
   }
   return UCC_OK;
 }
 
-// Factors [0, K) on the reference.  The last block of each factor flags a
-// stop when the next factor might not fit or when the Methods-section cut is
-// due; later launches in the chunk then skip, and the host cuts / grows and
-// resumes at the flagged factor.
-ucc_status run_forward(ucc_ctx* c, double eps, bool record) {
-  if (!(eps >= 0.0) || std::isinf(eps)) return fail(UCC_EINVAL, "eps must be finite and >= 0");
-  UCC_TRY(reset_state(c, record));
+// Factors [k0, k1) on table s.  The last block of each factor flags a stop
+// when the next factor might not fit or when the Methods-section cut is due;
+// later launches in the chunk then skip, and the host cuts / grows and
+// resumes at the flagged factor.  Chunks shrink when stops come often.
+ucc_status run_factors(ucc_ctx* c, TableSet& s, double eps, bool record, int k0, int k1) {
   const int pw = pick_probe_width(c);
-  const int chunk = 64;
   const unsigned long long n_max = c->opt.n_max > 0 ? (unsigned long long)c->opt.n_max : 0ull;
-  int k = 0;
-  unsigned long long n_known = 1;
-  long long cut_total = 0;
-  CUDA_TRY(cudaEventRecord(c->ev[0], c->stream));
-  while (k < c->K) {
-    int end = std::min(c->K, k + chunk);
+  UCC_TRY(read_counters(c, s));
+  unsigned long long n_known = s.h_cnt->n_tail;
+  int chunk = 64;
+  int k = k0;
+  while (k < k1) {
+    const int end = std::min(k1, k + chunk);
     // Grid sized from the last known count (grid-stride loops stay correct if
     // the table grew since).
-    unsigned long long est = std::min<unsigned long long>(n_known * 4, c->cur.cap_n);
+    const unsigned long long est = std::min<unsigned long long>(n_known * 4, s.cur.cap_n);
     int grid = (int)std::min<unsigned long long>((unsigned long long)c->full_grid(), (est + 255) / 256);
     grid = std::max(grid, std::min(c->full_grid(), 4));
     if (k < 0 || end > c->K) return fail(UCC_ECUDA, "factor index out of range");
+    CUDA_TRY(cudaEventRecord(c->kev[0], c->stream));
     for (int kk = k; kk < end; ++kk) {
-      CUDA_TRY(launch_forward(c->table(), c->d_factors, kk, eps, (unsigned int)(kk + 1), record ? 1 : 0, c->tape(),
+      CUDA_TRY(launch_forward(c->table(s), c->d_factors, kk, eps, (unsigned int)(kk + 1), record ? 1 : 0, c->tape(),
                               n_max, pw, grid, c->stream));
       c->launches++;
+      c->stats.forward_launches++;
     }
-    UCC_TRY(read_counters(c));
-    const Counters h = *c->h_cnt;  // copy: later reads overwrite the mirror
+    CUDA_TRY(cudaEventRecord(c->kev[1], c->stream));
+    UCC_TRY(read_counters(c, s));
+    {
+      float kms = 0.f;
+      CUDA_TRY(cudaEventElapsedTime(&kms, c->kev[0], c->kev[1]));
+      c->stats.forward_kernel_ms += kms;
+    }
+    const Counters h = *s.h_cnt;  // copy: later reads overwrite the mirror
     n_known = h.n_tail;
     c->stats.peak_entries = std::max<long long>(c->stats.peak_entries, (long long)h.n_tail);
     if (h.stop_k >= 0) {
       const int resume = h.stop_k;
       if (resume <= k || resume > end) return fail(UCC_ECUDA, "invalid resume factor");
+      // Stops every few factors: launch fewer factors per round trip.
+      chunk = std::max(2, std::min(64, 2 * (resume - k)));
       if (h.cut_pending) {
         const unsigned long long before = h.n_tail - h.n_dead;
-        CUDA_TRY(launch_select_cut(c->table(), c->d_sel, (unsigned long long)c->opt.n_cut, (unsigned int)resume,
+        CUDA_TRY(launch_select_cut(c->table(s), c->d_sel, (unsigned long long)c->opt.n_cut, (unsigned int)resume,
                                    record ? 1 : 0, c->tape(), resume - 1, c->full_grid(), c->stream, &c->launches));
-        UCC_TRY(read_counters(c));
-        const unsigned long long after = c->h_cnt->n_tail - c->h_cnt->n_dead;
+        UCC_TRY(read_counters(c, s));
+        const unsigned long long after = s.h_cnt->n_tail - s.h_cnt->n_dead;
         if (after != (unsigned long long)c->opt.n_cut)
           return fail(UCC_ECUDA, "truncation kept " + std::to_string(after) + " entries, expected " +
                                      std::to_string(c->opt.n_cut));
-        cut_total += (long long)(before - after);
+        c->cut_total += (long long)(before - after);
       }
-      UCC_TRY(ensure_room(c, record));
+      UCC_TRY(ensure_room(c, s, record));
       const int minus_one = -1, zero = 0;
-      CUDA_TRY(cudaMemcpyAsync(&c->d_cnt->stop_k, &minus_one, sizeof(int), cudaMemcpyHostToDevice, c->stream));
-      CUDA_TRY(cudaMemcpyAsync(&c->d_cnt->cut_pending, &zero, sizeof(int), cudaMemcpyHostToDevice, c->stream));
-      UCC_TRY(read_counters(c));
-      n_known = c->h_cnt->n_tail;
+      CUDA_TRY(cudaMemcpyAsync(&s.d_cnt->stop_k, &minus_one, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+      CUDA_TRY(cudaMemcpyAsync(&s.d_cnt->cut_pending, &zero, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+      UCC_TRY(read_counters(c, s));
+      n_known = s.h_cnt->n_tail;
       k = resume;
       continue;
     }
+    chunk = std::min(64, chunk * 2);
     // Compact when a quarter of the stored entries are dropped ones.
-    if (h.n_dead > 4096 && h.n_dead * 4 > h.n_tail) UCC_TRY(rebuild(c, c->cur.cap_n));
+    if (h.n_dead > 4096 && h.n_dead * 4 > h.n_tail) UCC_TRY(rebuild(c, s, s.cur.cap_n));
     k = end;
   }
-  CUDA_TRY(cudaEventRecord(c->ev[1], c->stream));
-  UCC_TRY(read_counters(c));
-  const Counters h = *c->h_cnt;  // copy: later reads overwrite the mirror
+  return UCC_OK;
+}
+
+void fill_forward_stats(ucc_ctx* c, const Counters& h) {
   c->stats.n_det = (long long)(h.n_tail - h.n_dead);
   c->stats.rotations = (long long)h.rotations;
   c->stats.created = (long long)h.created;
   c->stats.dropped_new = (long long)h.dropped_new;
   c->stats.dropped_old = (long long)h.dropped_old;
-  c->stats.cut = cut_total;
-  c->stats.tape_entries = (long long)h.tape_n;
+  c->stats.cut = c->cut_total;
   c->stats.scanned = (long long)h.scanned;
-  c->stats.capacity_entries = (long long)c->cur.cap_n;
-  c->stats.hash_slots = (long long)c->cur.n_slots;
+}
+
+// Factors per gradient segment.  With cuts, most of what the forward pass
+// drops is cut, not pruned, so the segments are ~sqrt(K) long: snapshots at
+// their starts, one recomputation each, and a tape that covers one segment.
+int segment_stride(const ucc_ctx* c) {
+  if (c->opt.checkpoint_stride > 0) return std::min(c->opt.checkpoint_stride, std::max(1, c->K));
+  if (c->opt.n_max > 0) return std::max(1, (int)std::ceil(std::sqrt((double)std::max(1, c->K))));
+  return std::max(1, c->K);
+}
+
+ucc_status run_forward(ucc_ctx* c, double eps, bool record) {
+  if (!(eps >= 0.0) || std::isinf(eps)) return fail(UCC_EINVAL, "eps must be finite and >= 0");
+  TableSet& s = c->ts[c->main];
+  c->cut_total = 0;
+  UCC_TRY(reset_table(c, s));
+  CUDA_TRY(cudaEventRecord(c->ev[0], c->stream));
+  if (!record) {
+    UCC_TRY(run_factors(c, s, eps, false, 0, c->K));
+  } else {
+    const int S = segment_stride(c);
+    const int nseg = c->K == 0 ? 0 : (c->K + S - 1) / S;
+    for (auto& sn : c->snaps) sn.release();
+    c->snaps.assign(std::max(0, nseg), Snapshot());
+    for (int j = 0; j < nseg; ++j) {
+      const int k0 = j * S, k1 = std::min(c->K, k0 + S);
+      if (j > 0) UCC_TRY(take_snapshot(c, s, &c->snaps[j]));
+      UCC_TRY(reset_tape(c, s, k0));
+      UCC_TRY(run_factors(c, s, eps, true, k0, k1));
+    }
+  }
+  CUDA_TRY(cudaEventRecord(c->ev[1], c->stream));
+  UCC_TRY(read_counters(c, s));
+  fill_forward_stats(c, *s.h_cnt);
+  c->stats.tape_entries = (long long)s.h_cnt->tape_n;
+  c->stats.capacity_entries = (long long)s.cur.cap_n;
+  c->stats.hash_slots = (long long)s.cur.n_slots;
   float ms = 0.f;
   CUDA_TRY(cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
   c->stats.apply_ms = ms;
@@ -408,88 +537,144 @@ ucc_status run_forward(ucc_ctx* c, double eps, bool record) {
 }
 
 ucc_status run_energy(ucc_ctx* c, double* E, double* norm2) {
+  TableSet& s = c->ts[c->main];
   Integrals in;
   in.h = c->d_h;
   in.g = c->d_g;
   in.n = c->n_spatial;
   in.n_so = c->n_so;
-  unsigned long long n = c->h_cnt->n_tail;
+  UCC_TRY(read_counters(c, s));
+  const unsigned long long n = s.h_cnt->n_tail;
   int grid = (int)std::min<unsigned long long>((unsigned long long)c->full_grid(), (n + 7) / 8);
   grid = std::max(grid, 1);
   UCC_TRY(ensure_partials(c, c->full_grid()));
-  CUDA_TRY(cudaMemsetAsync(&c->d_cnt->sig_probes, 0, 2 * sizeof(unsigned long long), c->stream));
+  CUDA_TRY(cudaMemsetAsync(&s.d_cnt->sig_probes, 0, 2 * sizeof(unsigned long long), c->stream));
   CUDA_TRY(cudaEventRecord(c->ev[2], c->stream));
-  CUDA_TRY(launch_sigma(c->table(), in, grid, c->stream));
+  CUDA_TRY(launch_sigma(c->table(s), in, grid, c->stream));
   c->launches++;
   CUDA_TRY(cudaEventRecord(c->ev[3], c->stream));
-  UCC_TRY(read_counters(c));
+  UCC_TRY(read_counters(c, s));
   float ms = 0.f;
   CUDA_TRY(cudaEventElapsedTime(&ms, c->ev[2], c->ev[3]));
   c->stats.energy_ms = ms;
-  c->stats.sigma_probes = (long long)c->h_cnt->sig_probes;
-  c->stats.sigma_hits = (long long)c->h_cnt->sig_hits;
-  const double n2 = c->h_cnt->norm2;
+  c->stats.sigma_probes = (long long)s.h_cnt->sig_probes;
+  c->stats.sigma_hits = (long long)s.h_cnt->sig_hits;
+  const double n2 = s.h_cnt->norm2;
   if (norm2) *norm2 = n2;
-  if (E) *E = c->h_cnt->e_num / n2 + c->e_nuc;
+  if (E) *E = s.h_cnt->e_num / n2 + c->e_nuc;
   c->have_sigma = true;
+  return UCC_OK;
+}
+
+// Room to re-insert every tape record of the segment into table s.
+ucc_status room_for_reverse(ucc_ctx* c, TableSet& s) {
+  UCC_TRY(read_counters(c, s));
+  const Counters h = *s.h_cnt;
+  const unsigned long long live = h.n_tail - h.n_dead;
+  const unsigned long long need = h.n_tail + h.tape_n;
+  if (need > s.cur.cap_n || 4ull * need > 3ull * s.cur.n_slots) {
+    UCC_TRY(rebuild(c, s, std::max<unsigned long long>(s.cur.cap_n, 2 * (live + h.tape_n) + 64)));
+    UCC_TRY(read_counters(c, s));
+  }
+  return UCC_OK;
+}
+
+// The reverse sweep over factors [k0, k1) on table s, which holds psi_{k1}
+// and mu_{k1} (in lam), with the tape recorded for this segment.
+ucc_status reverse_segment(ucc_ctx* c, TableSet& s, int k0, int k1) {
+  if (k1 <= k0) return UCC_OK;
+  std::vector<unsigned long long> off(k1 - k0 + 1);
+  CUDA_TRY(cudaMemcpyAsync(off.data(), c->t_off + k0, off.size() * sizeof(unsigned long long),
+                           cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  const int pw = pick_probe_width(c);
+  const int grid_full = c->full_grid();
+  const unsigned long long n_now = s.h_cnt->n_tail;
+  int grid = (int)std::min<unsigned long long>((unsigned long long)grid_full, (n_now * 2 + 255) / 256);
+  grid = std::max(grid, std::min(grid_full, 4));
+  CUDA_TRY(cudaEventRecord(c->kev[0], c->stream));
+  for (int k = k1 - 1; k >= k0; --k) {
+    const unsigned int stamp = 0x80000000u | (unsigned int)k;
+    const unsigned long long lo = off[k - k0], hi = off[k - k0 + 1];
+    if (hi > c->tape_cap || lo > hi) return fail(UCC_ECUDA, "tape offsets out of range");
+    if (hi > lo) {
+      const int g2 = (int)std::min<unsigned long long>((unsigned long long)grid_full, (hi - lo + 255) / 256);
+      CUDA_TRY(launch_tape_reinsert(c->table(s), c->tape(), k, std::max(g2, 1), c->stream));
+      c->launches++;
+    }
+    CUDA_TRY(launch_reverse(c->table(s), c->d_factors, k, stamp, c->d_grad, pw, grid, c->stream));
+    c->launches++;
+    c->stats.reverse_launches++;
+  }
+  CUDA_TRY(cudaEventRecord(c->kev[1], c->stream));
+  UCC_TRY(read_counters(c, s));
+  {
+    float kms = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&kms, c->kev[0], c->kev[1]));
+    c->stats.reverse_kernel_ms += kms;
+  }
+  c->stats.reverse_pairs += (long long)s.h_cnt->rev_pairs;
   return UCC_OK;
 }
 
 ucc_status run_gradient(ucc_ctx* c, double eps, double* E, double* grad_out, int on_device) {
   c->launches = 0;
   c->stats = ucc_stats{};
+  c->main = 0;
   UCC_TRY(run_forward(c, eps, true));
-  {
-    // The reverse sweep re-inserts up to tape_n entries: make room now, before
-    // sigma and lambda are laid out against the entry indices.
-    const Counters h = *c->h_cnt;  // copy: later reads overwrite the mirror
-    const unsigned long long live = h.n_tail - h.n_dead;
-    const unsigned long long need = h.n_tail + h.tape_n;
-    if (need > c->cur.cap_n || 4ull * need > 3ull * c->cur.n_slots) {
-      UCC_TRY(rebuild(c, std::max<unsigned long long>(c->cur.cap_n, 2 * (live + h.tape_n) + 64)));
-      UCC_TRY(read_counters(c));
-    }
-  }
+  TableSet& s0 = c->ts[c->main];
+  UCC_TRY(room_for_reverse(c, s0));
   double e = 0.0, n2 = 0.0;
   UCC_TRY(run_energy(c, &e, &n2));
   if (E) *E = e;
   const int grid_full = c->full_grid();
-  CUDA_TRY(cudaEventRecord(c->ev[4], c->stream));
-  CUDA_TRY(launch_lambda_init(c->table(), grid_full, c->stream));
-  c->launches++;
-  // Tape offsets of every factor.
-  std::vector<unsigned long long> off(c->K + 1);
-  CUDA_TRY(cudaMemcpyAsync(off.data(), c->t_off, (c->K + 1) * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
-                           c->stream));
-  CUDA_TRY(cudaStreamSynchronize(c->stream));
-  const int pw = pick_probe_width(c);
-  unsigned long long n_now = c->h_cnt->n_tail;
-  int grid = (int)std::min<unsigned long long>((unsigned long long)grid_full, (n_now * 2 + 255) / 256);
-  grid = std::max(grid, std::min(grid_full, 4));
   UCC_TRY(ensure_partials(c, grid_full));
-  for (int k = c->K - 1; k >= 0; --k) {
-    const unsigned int stamp = 0x80000000u | (unsigned int)k;
-    if (off[k + 1] > off[k]) {
-      int g2 = (int)std::min<unsigned long long>((unsigned long long)grid_full, (off[k + 1] - off[k] + 255) / 256);
-      CUDA_TRY(launch_tape_reinsert(c->table(), c->tape(), k, std::max(g2, 1), c->stream));
+  CUDA_TRY(cudaEventRecord(c->ev[4], c->stream));
+  CUDA_TRY(launch_lambda_init(c->table(s0), grid_full, c->stream));
+  c->launches++;
+  const int S = segment_stride(c);
+  const int nseg = c->K == 0 ? 0 : (c->K + S - 1) / S;
+  long long tape_peak = c->stats.tape_entries;
+  for (int j = nseg - 1; j >= 0; --j) {
+    const int k0 = j * S, k1 = std::min(c->K, k0 + S);
+    if (j < nseg - 1) {
+      // Recompute segment j forward from its snapshot on the other table,
+      // recording its tape; carry mu over by key; swap the tables' roles.
+      TableSet& from = c->ts[c->main];
+      TableSet& work = c->ts[1 - c->main];
+      if (j == 0) {
+        UCC_TRY(reset_table(c, work));
+      } else {
+        UCC_TRY(load_snapshot(c, work, c->snaps[j]));
+      }
+      UCC_TRY(reset_tape(c, work, k0));
+      UCC_TRY(run_factors(c, work, eps, true, k0, k1));
+      UCC_TRY(room_for_reverse(c, work));
+      c->stats.recompute_scanned += (long long)work.h_cnt->scanned;
+      c->stats.recompute_rotations += (long long)work.h_cnt->rotations;
+      c->stats.recompute_created += (long long)work.h_cnt->created;
+      tape_peak = std::max<long long>(tape_peak, (long long)work.h_cnt->tape_n);
+      CUDA_TRY(launch_transfer_lambda(c->table(work), c->table(from), grid_full, c->stream));
       c->launches++;
+      c->main = 1 - c->main;
     }
-    CUDA_TRY(launch_reverse(c->table(), c->d_factors, k, stamp, c->d_grad, pw, grid, c->stream));
-    c->launches++;
+    UCC_TRY(reverse_segment(c, c->ts[c->main], k0, k1));
   }
   CUDA_TRY(cudaEventRecord(c->ev[5], c->stream));
-  if (grad_out) {
+  if (grad_out && c->K) {
     CUDA_TRY(cudaMemcpyAsync(grad_out, c->d_grad, c->K * sizeof(double),
                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
   }
-  UCC_TRY(read_counters(c));
+  UCC_TRY(read_counters(c, c->ts[c->main]));
   float ms = 0.f;
   CUDA_TRY(cudaEventElapsedTime(&ms, c->ev[4], c->ev[5]));
   c->stats.reverse_ms = ms;
-  c->stats.reverse_pairs = (long long)c->h_cnt->rev_pairs;
+  c->stats.tape_entries = tape_peak;
   c->stats.kernel_launches = c->launches;
+  for (auto& sn : c->snaps) sn.release();
   c->have_psi = false;
   c->have_sigma = false;
+  c->main = 0;
   return UCC_OK;
 }
 
@@ -552,23 +737,179 @@ void destroy(ucc_ctx* c) {
   if (!c) return;
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
-  c->cur.release();
-  c->spare.release();
+  c->ts[0].release();
+  c->ts[1].release();
+  for (auto& sn : c->snaps) sn.release();
   dfree(c->d_factors);
   dfree(c->d_h);
   dfree(c->d_g);
   dfree(c->d_grad);
   dfree(c->d_partials);
-  dfree(c->d_cnt);
   dfree(c->d_sel);
   dfree(c->t_key);
   dfree(c->t_val);
   dfree(c->t_born);
   dfree(c->t_off);
-  if (c->h_cnt) cudaFreeHost(c->h_cnt);
   for (auto& e : c->ev)
     if (e) cudaEventDestroy(e);
+  for (auto& e : c->kev)
+    if (e) cudaEventDestroy(e);
   delete c;
+}
+
+// The batched path: every job advances one factor per launch.
+ucc_status batch_together(const std::vector<int>& idx, ucc_ctx* const* jobs, double eps, double* E,
+                          double* const* grads) {
+  const int n = (int)idx.size();
+  ucc_ctx* c0 = jobs[idx[0]];
+  cudaStream_t st = c0->stream;
+  bool record = false;
+  for (int x = 0; x < n; ++x) record |= grads && grads[idx[x]];
+  int maxK = 0;
+  for (int x = 0; x < n; ++x) {
+    ucc_ctx* c = jobs[idx[x]];
+    c->main = 0;
+    c->launches = 0;
+    c->stats = ucc_stats{};
+    c->cut_total = 0;
+    UCC_TRY(reset_table(c, c->ts[0]));
+    if (record) UCC_TRY(reset_tape(c, c->ts[0], 0));
+    maxK = std::max(maxK, c->K);
+  }
+  JobView* d_jobs = nullptr;
+  JobState* d_js = nullptr;
+  BatchHeader* d_bh = nullptr;
+  UCC_TRY(dalloc(&d_jobs, n));
+  UCC_TRY(dalloc(&d_js, n));
+  UCC_TRY(dalloc(&d_bh, 1));
+  std::vector<JobView> hv(n);
+  std::vector<JobState> hs(n);
+  auto release = [&]() {
+    dfree(d_jobs);
+    dfree(d_js);
+    dfree(d_bh);
+  };
+  auto view_of = [&](int x) {
+    ucc_ctx* c = jobs[idx[x]];
+    JobView v{};
+    v.t = c->table(c->ts[0]);
+    v.factors = c->d_factors;
+    v.tape = c->tape();
+    v.in.h = c->d_h;
+    v.in.g = c->d_g;
+    v.in.n = c->n_spatial;
+    v.in.n_so = c->n_so;
+    v.grad = c->d_grad;
+    v.eps = eps;
+    v.K = c->K;
+    return v;
+  };
+  auto upload = [&]() -> ucc_status {
+    for (int x = 0; x < n; ++x) hv[x] = view_of(x);
+    CUDA_TRY(cudaMemcpyAsync(d_jobs, hv.data(), n * sizeof(JobView), cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(d_js, hs.data(), n * sizeof(JobState), cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    return UCC_OK;
+  };
+  auto fetch = [&]() -> ucc_status {
+    CUDA_TRY(cudaMemcpyAsync(hs.data(), d_js, n * sizeof(JobState), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    return UCC_OK;
+  };
+  auto run = [&]() -> ucc_status {
+    const int grid = c0->full_grid();
+    for (int x = 0; x < n; ++x) {
+      hs[x] = JobState{};
+      hs[x].stop = -1;
+    }
+    UCC_TRY(upload());
+    CUDA_TRY(cudaMemsetAsync(d_bh, 0, sizeof(BatchHeader), st));
+    CUDA_TRY(launch_batch_layout(d_jobs, d_js, n, d_bh, 0, st));
+    // Forward: chunks of launches, then host action for jobs that need room.
+    CUDA_TRY(cudaEventRecord(c0->ev[0], st));
+    for (;;) {
+      for (int s = 0; s < 32; ++s) CUDA_TRY(launch_forward_batch(d_jobs, d_js, n, d_bh, record ? 1 : 0, grid, st));
+      for (int x = 0; x < n; ++x) jobs[idx[x]]->launches += 32;
+      UCC_TRY(fetch());
+      bool done = true, changed = false;
+      for (int x = 0; x < n; ++x) {
+        ucc_ctx* c = jobs[idx[x]];
+        if (hs[x].k < c->K) done = false;
+        const bool sparse = hs[x].n_dead > 4096 && hs[x].n_dead * 4 > hs[x].n_tail;
+        if (hs[x].stop >= 0 || (sparse && hs[x].k < c->K)) {
+          UCC_TRY(ensure_room(c, c->ts[0], record));
+          hs[x].stop = -1;
+          changed = true;
+        }
+      }
+      if (done) break;
+      if (changed) {
+        UCC_TRY(upload());
+        CUDA_TRY(launch_batch_layout(d_jobs, d_js, n, d_bh, 0, st));
+      }
+    }
+    CUDA_TRY(cudaEventRecord(c0->ev[1], st));
+    for (int x = 0; x < n; ++x) {
+      ucc_ctx* c = jobs[idx[x]];
+      UCC_TRY(read_counters(c, c->ts[0]));
+      if (record) UCC_TRY(room_for_reverse(c, c->ts[0]));
+      fill_forward_stats(c, *c->ts[0].h_cnt);
+      c->stats.tape_entries = (long long)c->ts[0].h_cnt->tape_n;
+    }
+    // Energy of every job in one launch.
+    for (int x = 0; x < n; ++x) hs[x].e_num = hs[x].norm2 = hs[x].gacc = 0.0;
+    UCC_TRY(upload());
+    for (int x = 0; x < n; ++x)
+      CUDA_TRY(cudaMemsetAsync(&jobs[idx[x]]->ts[0].d_cnt->sig_probes, 0, 2 * sizeof(unsigned long long), st));
+    CUDA_TRY(launch_batch_layout(d_jobs, d_js, n, d_bh, 1, st));
+    CUDA_TRY(cudaEventRecord(c0->ev[2], st));
+    CUDA_TRY(launch_sigma_batch(d_jobs, d_js, n, d_bh, grid, st));
+    CUDA_TRY(cudaEventRecord(c0->ev[3], st));
+    UCC_TRY(fetch());
+    for (int x = 0; x < n; ++x) {
+      ucc_ctx* c = jobs[idx[x]];
+      E[idx[x]] = hs[x].e_num / hs[x].norm2 + c->e_nuc;
+      c->launches += 2;
+    }
+    if (record) {
+      CUDA_TRY(launch_lambda_init_batch(d_jobs, d_js, n, d_bh, grid, st));
+      for (int x = 0; x < n; ++x) hs[x].k = jobs[idx[x]]->K - 1;
+      CUDA_TRY(cudaMemcpyAsync(d_js, hs.data(), n * sizeof(JobState), cudaMemcpyHostToDevice, st));
+      CUDA_TRY(cudaEventRecord(c0->ev[4], st));
+      for (int s = 0; s < maxK; ++s) CUDA_TRY(launch_reverse_batch(d_jobs, d_js, n, d_bh, grid, st));
+      CUDA_TRY(cudaEventRecord(c0->ev[5], st));
+      UCC_TRY(fetch());
+      for (int x = 0; x < n; ++x) {
+        ucc_ctx* c = jobs[idx[x]];
+        if (hs[x].k != -1) return fail(UCC_ECUDA, "batched reverse sweep did not finish");
+        if (c->K) CUDA_TRY(cudaMemcpyAsync(grads[idx[x]], c->d_grad, c->K * sizeof(double), cudaMemcpyDeviceToHost, st));
+        c->launches += 1 + 4LL * maxK;
+      }
+    }
+    float ms = 0.f;
+    for (int x = 0; x < n; ++x) {
+      ucc_ctx* c = jobs[idx[x]];
+      UCC_TRY(read_counters(c, c->ts[0]));
+      c->stats.sigma_probes = (long long)c->ts[0].h_cnt->sig_probes;
+      c->stats.sigma_hits = (long long)c->ts[0].h_cnt->sig_hits;
+      c->stats.reverse_pairs = (long long)c->ts[0].h_cnt->rev_pairs;
+      c->stats.kernel_launches = c->launches;
+      c->have_psi = !record;
+      c->have_sigma = !record;
+    }
+    CUDA_TRY(cudaEventElapsedTime(&ms, c0->ev[0], c0->ev[1]));
+    c0->stats.apply_ms = ms;
+    CUDA_TRY(cudaEventElapsedTime(&ms, c0->ev[2], c0->ev[3]));
+    c0->stats.energy_ms = ms;
+    if (record) {
+      CUDA_TRY(cudaEventElapsedTime(&ms, c0->ev[4], c0->ev[5]));
+      c0->stats.reverse_ms = ms;
+    }
+    return UCC_OK;
+  };
+  ucc_status s = run();
+  release();
+  return s;
 }
 
 }  // namespace
@@ -607,14 +948,14 @@ ucc_status ucc_create(const ucc_hamiltonian* ham, const ucc_ansatz* an, void* cu
   if ((s = dalloc(&c->d_h, n * n)) != UCC_OK) return bail(s);
   if ((s = dalloc(&c->d_g, n * n * n * n)) != UCC_OK) return bail(s);
   if ((s = dalloc(&c->d_grad, std::max(1, c->K))) != UCC_OK) return bail(s);
-  if ((s = dalloc(&c->d_cnt, 1)) != UCC_OK) return bail(s);
+  if ((s = c->ts[0].init()) != UCC_OK) return bail(s);
+  if ((s = c->ts[1].init()) != UCC_OK) return bail(s);
   if ((s = dalloc(&c->d_sel, 1)) != UCC_OK) return bail(s);
   if ((s = dalloc(&c->t_off, (size_t)c->K + 1)) != UCC_OK) return bail(s);
   if ((s = ensure_partials(c, c->full_grid())) != UCC_OK) return bail(s);
-  if (cudaMallocHost((void**)&c->h_cnt, sizeof(Counters)) != cudaSuccess)
-    return bail(fail(UCC_ENOMEM, "pinned host allocation failed"));
-  std::memset(c->h_cnt, 0, sizeof(Counters));
   for (auto& e : c->ev)
+    if (cudaEventCreate(&e) != cudaSuccess) return bail(fail(UCC_ECUDA, "event creation failed"));
+  for (auto& e : c->kev)
     if (cudaEventCreate(&e) != cudaSuccess) return bail(fail(UCC_ECUDA, "event creation failed"));
   if (cudaMemcpyAsync(c->d_h, ham->h, n * n * sizeof(double), cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
       cudaMemcpyAsync(c->d_g, ham->g, n * n * n * n * sizeof(double), cudaMemcpyHostToDevice, c->stream) !=
@@ -685,8 +1026,9 @@ ucc_status ucc_get_wavefunction(ucc_ctx* c, size_t cap, size_t* n, uint64_t* key
   if (!c->have_psi) return fail(UCC_ESTATE, "no wavefunction held: call ucc_apply first");
   if (sigma && !c->have_sigma) return fail(UCC_ESTATE, "no sigma held: call ucc_energy first");
   CUDA_TRY(cudaSetDevice(c->device));
-  UCC_TRY(read_counters(c));
-  const unsigned long long live = c->h_cnt->n_tail - c->h_cnt->n_dead;
+  TableSet& tab = c->ts[c->main];
+  UCC_TRY(read_counters(c, tab));
+  const unsigned long long live = tab.h_cnt->n_tail - tab.h_cnt->n_dead;
   *n = (size_t)live;
   if (cap < live) return fail(UCC_ECAPACITY, "buffer smaller than the wavefunction");
   if (live == 0) return UCC_OK;
@@ -696,28 +1038,28 @@ ucc_status ucc_get_wavefunction(ucc_ctx* c, size_t cap, size_t* n, uint64_t* key
   double* ds = sigma;
   unsigned long long* tk = nullptr;
   double* ta = nullptr;
-  double* ts = nullptr;
+  double* tsig = nullptr;
   if (!on_device) {
     UCC_TRY(dalloc(&tk, live));
     UCC_TRY(dalloc(&ta, live));
-    if (sigma) UCC_TRY(dalloc(&ts, live));
+    if (sigma) UCC_TRY(dalloc(&tsig, live));
     dk = tk;
     da = ta;
-    ds = ts;
+    ds = tsig;
   }
-  CUDA_TRY(cudaMemsetAsync(&c->d_cnt->new_n, 0, sizeof(unsigned long long), c->stream));
-  CUDA_TRY(launch_export(c->table(), live, dk, da, ds, c->full_grid(), c->stream));
+  CUDA_TRY(cudaMemsetAsync(&tab.d_cnt->new_n, 0, sizeof(unsigned long long), c->stream));
+  CUDA_TRY(launch_export(c->table(tab), live, dk, da, ds, c->full_grid(), c->stream));
   if (!on_device) {
     CUDA_TRY(cudaMemcpyAsync(keys, tk, live * sizeof(uint64_t), cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(cudaMemcpyAsync(amps, ta, live * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-    if (sigma) CUDA_TRY(cudaMemcpyAsync(sigma, ts, live * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if (sigma) CUDA_TRY(cudaMemcpyAsync(sigma, tsig, live * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   }
-  ucc_status s = read_counters(c);
+  ucc_status s = read_counters(c, tab);
   dfree(tk);
   dfree(ta);
-  dfree(ts);
+  dfree(tsig);
   UCC_TRY(s);
-  if (c->h_cnt->new_n != live) return fail(UCC_ECUDA, "export count mismatch");
+  if (tab.h_cnt->new_n != live) return fail(UCC_ECUDA, "export count mismatch");
   return UCC_OK;
 }
 
@@ -729,17 +1071,33 @@ ucc_status ucc_get_stats(const ucc_ctx* c, ucc_stats* out) {
 
 ucc_status ucc_batch_run(int n_jobs, ucc_ctx* const* jobs, double eps, double* E, double* const* grads) {
   if (n_jobs < 0 || (n_jobs > 0 && (!jobs || !E))) return fail(UCC_EINVAL, "bad batch arguments");
+  if (n_jobs == 0) return UCC_OK;
+  if (!(eps >= 0.0) || std::isinf(eps)) return fail(UCC_EINVAL, "eps must be finite and >= 0");
+  for (int j = 0; j < n_jobs; ++j) {
+    if (!jobs[j]) return fail(UCC_EINVAL, "null job");
+    if (jobs[j]->device != jobs[0]->device || jobs[j]->stream != jobs[0]->stream)
+      return fail(UCC_EINVAL, "batched jobs must share one device and one stream");
+  }
+  CUDA_TRY(cudaSetDevice(jobs[0]->device));
+  // Jobs with the N_MAX/N_CUT cut need segment checkpoints: they run one by one.
+  std::vector<int> together;
   for (int j = 0; j < n_jobs; ++j) {
     ucc_ctx* c = jobs[j];
-    if (!c) return fail(UCC_EINVAL, "null job");
-    if (grads && grads[j]) {
-      UCC_TRY(ucc_gradient(c, eps, &E[j], grads[j], 0));
+    if (c->opt.n_max > 0 || together.size() >= (size_t)kMaxBatchJobs) {
+      if (grads && grads[j]) {
+        UCC_TRY(run_gradient(c, eps, &E[j], grads[j], 0));
+      } else {
+        c->launches = 0;
+        c->stats = ucc_stats{};
+        UCC_TRY(run_forward(c, eps, false));
+        UCC_TRY(run_energy(c, &E[j], nullptr));
+      }
     } else {
-      UCC_TRY(ucc_apply(c, eps));
-      UCC_TRY(ucc_energy(c, &E[j], nullptr));
+      together.push_back(j);
     }
   }
-  return UCC_OK;
+  if (together.empty()) return UCC_OK;
+  return batch_together(together, jobs, eps, E, grads);
 }
 
 const char* ucc_last_error(void) { return g_last_error.c_str(); }

@@ -14,15 +14,34 @@ namespace cg = cooperative_groups;
 // steps; the bound only guarantees termination.
 constexpr int MAX_PROBE = 1 << 14;
 
-// 64-bit finalizer of SplitMix64 (Steele, Lea and Flood, "Fast splittable
-// pseudorandom number generators", 2014): a bijective mix of all key bits.
-__device__ __forceinline__ unsigned long long mix64(unsigned long long x) {
-  x ^= x >> 30;
-  x *= 0xbf58476d1ce4e5b9ULL;
-  x ^= x >> 27;
-  x *= 0x94d049bb133111ebULL;
-  x ^= x >> 31;
-  return x;
+// Home slot of a key: Fibonacci hashing (Knuth, TAOCP vol. 3, 6.4) -- the
+// top log2(slots) bits of key * 2^64/phi.  One 64-bit multiply; on the
+// workloads' determinant keys it gives the same linear-probing lengths as a
+// full 64-bit finalizer.
+constexpr unsigned long long kFibonacci = 0x9E3779B97F4A7C15ull;
+
+__device__ __forceinline__ unsigned long long home_slot(const Table& t, unsigned long long key) {
+  return (key * kFibonacci) >> t.slot_shift;
+}
+
+// Existence filter: one bit per key (8 filter bits per hash slot, so it is
+// 1/16 the size of the slot array and mostly stays in L2).  Every key that
+// occupies a slot has its bit set, so a clear bit proves the key absent and
+// saves the probe; a set bit (a stored key, or a collision) falls through to
+// the probe.  The bit index multiplies by a second odd constant (the
+// SplitMix64 finalizer's first multiplier) so it does not follow the slot.
+constexpr unsigned long long kFilterMul = 0xbf58476d1ce4e5b9ull;
+
+__device__ __forceinline__ bool filter_maybe(const Table& t, unsigned long long key) {
+  if (!t.filt) return true;
+  const unsigned long long b = (key * kFilterMul) >> t.filt_shift;
+  return (t.filt[b >> 5] >> (b & 31u)) & 1u;
+}
+
+__device__ __forceinline__ void filter_add(const Table& t, unsigned long long key) {
+  if (!t.filt) return;
+  const unsigned long long b = (key * kFilterMul) >> t.filt_shift;
+  atomicOr(&t.filt[b >> 5], 1u << (b & 31u));
 }
 
 // A dropped entry keeps its key and slot; its amplitude becomes a quiet NaN
@@ -69,7 +88,11 @@ __device__ __forceinline__ Lookup find1(const Table& t, unsigned long long key, 
   r.state = ABSENT;
   r.idx = 0;
   r.amp = 0.0;
-  unsigned long long h = mix64(key) & t.slot_mask;
+  unsigned long long h = home_slot(t, key);
+  if (!filter_maybe(t, key)) {
+    r.slot = h;  // absent: an insertion claims the first empty slot from home
+    return r;
+  }
   for (int step = 0; step < MAX_PROBE; ++step) {
     Slot s = t.slots[h];
     if (s.key == key) {
@@ -118,8 +141,12 @@ __device__ __forceinline__ Lookup findG(const Table& t, unsigned long long key, 
       // Group-uniform: every lane of the group sees the same qk / qa.
       unsigned long long res_slot = 0, res_idx = 0;
       int res_state = ABSENT;
+      unsigned long long h = home_slot(t, qk);
       bool decided = !qa;
-      unsigned long long h = mix64(qk) & t.slot_mask;
+      if (qa && !filter_maybe(t, qk)) {  // group-uniform: absent without a probe
+        decided = true;
+        res_slot = h;
+      }
       for (int step = 0; step < MAX_PROBE / G; ++step) {
         // All lanes of the warp run this loop in lock step (the trip count is
         // warp-uniform via the ballot below), so full-mask votes are safe.
@@ -170,7 +197,10 @@ __device__ __forceinline__ unsigned long long claim_slot(const Table& t, unsigne
   unsigned long long h = start & t.slot_mask;
   for (int step = 0; step < MAX_PROBE; ++step) {
     unsigned long long prev = atomicCAS(&t.slots[h].key, 0ull, key);
-    if (prev == 0ull) return h;
+    if (prev == 0ull) {
+      filter_add(t, key);
+      return h;
+    }
     if (prev == key) {
       raise_error(t.cnt, ERR_CONSISTENCY);
       return h;
@@ -209,6 +239,11 @@ __device__ __forceinline__ bool insert_new(const Table& t, unsigned long long ke
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
   return v;
 }

@@ -61,8 +61,11 @@ struct Table {
   unsigned int* born;        // [cap_n] factor that created the entry (gradient runs)
   double* lam;               // [cap_n] adjoint vector (gradient runs)
   double* sigma;             // [cap_n] P_S H psi (energy runs)
-  Slot* slots;               // [slot_mask + 1]
+  Slot* slots;               // [slot_mask + 1], a power of two
   unsigned long long slot_mask;
+  int slot_shift;            // 64 - log2(slot_mask + 1): home slot = (key * phi64) >> slot_shift
+  int filt_shift;            // 64 - log2(filter bits)
+  unsigned int* filt;        // existence filter, 8 bits per slot (nullptr: none)
   unsigned long long cap_n;
   Counters* cnt;
   double* partials;          // [grid] per-block partial sums
@@ -90,8 +93,38 @@ struct SelectState {
   unsigned long long key_prefix, key_target;  // key tie-break among |c| == threshold
   unsigned long long count_eq, cut_total;
   int need_keys, pad;
-  unsigned long long hist[256];
+  unsigned long long hist[2048];
 };
+
+// One job of a batch, as the batched kernels see it (uploaded by the host).
+struct JobView {
+  Table t;
+  const Factor* factors;
+  Tape tape;
+  Integrals in;
+  double* grad;  // [K] dE/dtheta of this job
+  double eps;
+  int K;
+  int pad;
+};
+
+// Per-job progress, written by the batched kernels and read back by the host.
+struct JobState {
+  int k;                      // forward: next factor; reverse: next factor to undo (-1 when done)
+  int stop;                   // forward: factor the job waits at for host action (-1: none)
+  unsigned long long base;    // this step's padded offset of the job in the batch index space
+  unsigned long long n;       // entries of the job this step covers
+  unsigned long long n_tail, n_dead, tape_n;  // mirror of the job's counters after the step
+  double e_num, norm2, gacc;  // energy sums; gradient accumulator of the current factor
+};
+
+struct BatchHeader {
+  unsigned long long total;   // size of the batch index space of the next step
+  unsigned int done;          // last-block arrival counter
+  int pad;
+};
+
+constexpr int kMaxBatchJobs = 1024;
 
 constexpr unsigned int BORN_INITIAL = 0xFFFFFFFFu;  // the reference determinant
 
@@ -112,7 +145,23 @@ cudaError_t launch_lambda_init(const Table& t, int grid, cudaStream_t st);
 cudaError_t launch_tape_reinsert(const Table& t, const Tape& tape, int k, int grid, cudaStream_t st);
 cudaError_t launch_reverse(const Table& t, const Factor* factors, int k, unsigned int stamp, double* grad,
                            int probe_width, int grid, cudaStream_t st);
+cudaError_t launch_restore(const Table& t, const unsigned long long* keys, const double* amps, unsigned long long n,
+                           int grid, cudaStream_t st);
+cudaError_t launch_transfer_lambda(const Table& dst, const Table& src, int grid, cudaStream_t st);
 int sigma_smem_bytes(int n_so);
+// Batched (many-job) launches; mode 0 lays out the forward index space
+// (n_scan of jobs still applying factors), 1 the energy space (n_tail of every
+// job), 2 the reverse space (n_tail of jobs still undoing factors).
+cudaError_t launch_batch_layout(const JobView* jobs, JobState* js, int n_jobs, BatchHeader* bh, int mode,
+                                cudaStream_t st);
+cudaError_t launch_forward_batch(const JobView* jobs, JobState* js, int n_jobs, BatchHeader* bh, int record,
+                                 int grid, cudaStream_t st);
+cudaError_t launch_sigma_batch(const JobView* jobs, JobState* js, int n_jobs, BatchHeader* bh, int grid,
+                               cudaStream_t st);
+cudaError_t launch_lambda_init_batch(const JobView* jobs, JobState* js, int n_jobs, BatchHeader* bh, int grid,
+                                     cudaStream_t st);
+cudaError_t launch_reverse_batch(const JobView* jobs, JobState* js, int n_jobs, BatchHeader* bh, int grid,
+                                 cudaStream_t st);
 // Message returned by ucc_last_error() on the calling thread.
 void set_last_error(const char* msg);
 

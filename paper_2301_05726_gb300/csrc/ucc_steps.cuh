@@ -1,0 +1,427 @@
+// Per-entry bodies of the factor steps, shared by the single-problem kernels
+// and the batched (many-job) kernels so both run the same arithmetic.
+#pragma once
+
+#include "ucc_device.cuh"
+
+namespace ucc {
+
+struct StepCounts {
+  unsigned long long rot = 0, cre = 0, dnew = 0, dold = 0;
+  long long dead_delta = 0;
+};
+
+__device__ __forceinline__ void record_kill(const Table& t, const Tape& tape, unsigned long long key, double val,
+                                            unsigned int born) {
+  unsigned long long ti = aggregated_add(&t.cnt->tape_n);
+  if (ti < tape.cap) {
+    tape.key[ti] = key;
+    tape.val[ti] = val;
+    tape.born[ti] = born;
+  } else {
+    raise_error(t.cnt, ERR_TAPE_FULL);
+  }
+}
+
+// One stored entry i of a factor step U_k (Eq. 3 with the eps rule).  Each
+// linked pair (E, D = tau E) is rotated exactly once: by the thread of E when
+// E is stored and live at the start of the step, otherwise by the thread of D.
+// Entries dropped during this step carry this step's stamp, so a D-thread can
+// tell "E was live when the step began" (live or DEAD_NOW) from "E absent"
+// (ABSENT or DEAD_OLD).  Every lane of the warp calls this (findG votes across
+// lanes); in_range is false for lanes past the end of the table.
+// The rotation, creation and eps rule for one linked entry i (key X, live
+// amplitude cX, ex = X is the excited member) whose partner lookup is r.
+template <bool RECORD>
+__device__ __forceinline__ void forward_resolve(const Table& t, const Factor& f, int k, double eps, unsigned int stamp,
+                                                const Tape& tape, unsigned long long i, unsigned long long X,
+                                                double cX, bool ex, const Lookup& r, StepCounts& sc) {
+  const unsigned long long Y = X ^ (f.occ | f.vir);
+  const bool partner_live = (r.state == ALIVE);
+  if (!ex && (partner_live || r.state == DEAD_NOW)) return;  // E's thread owns the pair
+  if (ex && r.state == DEAD_NOW) {
+    raise_error(t.cnt, ERR_CONSISTENCY);
+    return;
+  }
+  const unsigned long long E = ex ? X : Y;
+  const int parity = (__popcll(E & f.pmask) + f.pconst) & 1;
+  const double ss = parity ? -f.s : f.s;  // s * sin(theta), exact
+  const double cE = ex ? cX : 0.0;
+  const double cD = ex ? (partner_live ? r.amp : 0.0) : cX;
+  // c_E' = cos c_E - s sin c_D ;  c_D' = cos c_D + s sin c_E  (no contraction)
+  const double nE = __dsub_rn(__dmul_rn(f.c, cE), __dmul_rn(ss, cD));
+  const double nD = __dadd_rn(__dmul_rn(f.c, cD), __dmul_rn(ss, cE));
+  const double nX = ex ? nE : nD;
+  const double nY = ex ? nD : nE;
+  ++sc.rot;
+  // The thread's own entry.
+  if (fabs(nX) < eps) {
+    if (RECORD) record_kill(t, tape, X, nX, t.born[i]);
+    t.amps[i] = dead_value(stamp);
+    ++sc.dold;
+    ++sc.dead_delta;
+  } else {
+    t.amps[i] = nX;
+  }
+  // The partner.
+  if (partner_live) {
+    if (fabs(nY) < eps) {
+      if (RECORD) record_kill(t, tape, Y, nY, t.born[r.idx]);
+      t.amps[r.idx] = dead_value(stamp);
+      ++sc.dold;
+      ++sc.dead_delta;
+    } else {
+      t.amps[r.idx] = nY;
+    }
+  } else if (fabs(nY) < eps) {
+    ++sc.dnew;
+  } else if (r.state == DEAD_OLD) {
+    // Revive a dropped key as a fresh entry past the scan range and point
+    // its slot there.  (Reviving in place would let the old index's scan
+    // thread, if it runs later in this step, see a live entry that was
+    // not live when the step began and rotate the pair a second time.)
+    const unsigned long long idx = aggregated_add(&t.cnt->n_tail);
+    if (idx < t.cap_n) {
+      t.keys[idx] = Y;
+      t.amps[idx] = nY;
+      if (RECORD) t.born[idx] = (unsigned int)k;
+      t.slots[r.slot].idx = idx;
+    } else {
+      raise_error(t.cnt, ERR_CAPACITY);
+    }
+    ++sc.cre;
+  } else {
+    insert_new(t, Y, nY, (unsigned int)k, r.slot, RECORD, false);
+    ++sc.cre;
+  }
+}
+
+template <int G, bool RECORD>
+__device__ __forceinline__ void forward_entry(const Table& t, const Factor& f, int k, double eps, unsigned int stamp,
+                                              const Tape& tape, unsigned long long i, bool in_range,
+                                              StepCounts& sc) {
+  bool act = in_range;
+  unsigned long long X = 0;
+  double cX = 0.0;
+  bool ex = false;
+  if (act) {
+    X = t.keys[i];
+    ex = ((X & f.occ) == f.occ) && ((X & f.vir) == 0ull);
+    const bool de = ((X & f.vir) == f.vir) && ((X & f.occ) == 0ull);
+    act = ex || de;
+    if (act) {
+      cX = t.amps[i];
+      act = !is_dead(cX);
+    }
+  }
+  const unsigned long long Y = X ^ (f.occ | f.vir);
+  Lookup r = findG<G>(t, Y, act, stamp);
+  if (!act) return;
+  forward_resolve<RECORD>(t, f, k, eps, stamp, tape, i, X, cX, ex, r, sc);
+}
+
+// U entries per lane (i0, i0 + 32, ..., i0 + 32(U-1)), single-lane probes:
+// all key loads, then all amplitude loads, filter tests and first-slot loads
+// are issued before any result is used, so a lane keeps up to 3U independent
+// loads in flight instead of one dependent chain.
+template <int U, bool RECORD>
+__device__ __forceinline__ void forward_entries(const Table& t, const Factor& f, int k, double eps,
+                                                unsigned int stamp, const Tape& tape, unsigned long long i0,
+                                                unsigned long long n, StepCounts& sc) {
+  unsigned long long X[U];
+  double cX[U];
+  bool act[U], ex[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const unsigned long long i = i0 + 32ull * u;
+    act[u] = i < n;
+    X[u] = act[u] ? t.keys[i] : 0ull;
+  }
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    ex[u] = ((X[u] & f.occ) == f.occ) && ((X[u] & f.vir) == 0ull);
+    const bool de = ((X[u] & f.vir) == f.vir) && ((X[u] & f.occ) == 0ull);
+    act[u] = act[u] && (ex[u] || de);
+    cX[u] = act[u] ? t.amps[i0 + 32ull * u] : 0.0;
+  }
+  const unsigned long long m = f.occ | f.vir;
+  bool maybe[U];
+  Slot s0[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    act[u] = act[u] && !is_dead(cX[u]);
+    maybe[u] = act[u] && filter_maybe(t, X[u] ^ m);
+    s0[u].key = 1ull;
+    s0[u].idx = 0;
+    if (maybe[u]) s0[u] = t.slots[home_slot(t, X[u] ^ m)];
+  }
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    if (!act[u]) continue;
+    const unsigned long long Y = X[u] ^ m;
+    Lookup r;
+    r.state = ABSENT;
+    r.idx = 0;
+    r.amp = 0.0;
+    r.slot = home_slot(t, Y);
+    if (maybe[u]) {
+      if (s0[u].key == Y) {
+        classify(t, s0[u].idx, stamp, r);
+      } else if (s0[u].key != 0ull) {
+        r = find1(t, Y, stamp);  // collision: continue the probe from home
+      }
+    }
+    forward_resolve<RECORD>(t, f, k, eps, stamp, tape, i0 + 32ull * u, X[u], cX[u], ex[u], r, sc);
+  }
+}
+
+// One stored entry i of the reverse step for factor k: psi_k -> psi_{k-1} in
+// place (inverse rotation on a stored pair, cos(theta) divided out of a lone
+// member), lambda_{k-1} = U_k^T mu_k, and this pair's share of
+// dE/dtheta_k / 2 = sum_pairs s (lam_D psi_E - lam_E psi_D) added to acc.
+// Entries created by factor k (born == k) leave the table.  Every lane of the
+// warp calls this.
+template <int G>
+__device__ __forceinline__ void reverse_entry(const Table& t, const Factor& f, int k, unsigned int stamp,
+                                              unsigned long long i, bool in_range, double& acc, unsigned int& pairs) {
+  bool act = in_range;
+  unsigned long long X = 0;
+  double cX = 0.0;
+  bool ex = false;
+  if (act) {
+    X = t.keys[i];
+    ex = ((X & f.occ) == f.occ) && ((X & f.vir) == 0ull);
+    const bool de = ((X & f.vir) == f.vir) && ((X & f.occ) == 0ull);
+    act = ex || de;
+    if (act) {
+      cX = t.amps[i];
+      act = !is_dead(cX);
+    }
+  }
+  const unsigned long long Y = X ^ (f.occ | f.vir);
+  Lookup r = findG<G>(t, Y, act, stamp);
+  if (!act) return;
+  const bool partner_live = (r.state == ALIVE);
+  if (!ex && (partner_live || r.state == DEAD_NOW)) return;  // E's thread owns the pair
+  const unsigned long long E = ex ? X : Y;
+  const int parity = (__popcll(E & f.pmask) + f.pconst) & 1;
+  const double sg = parity ? -1.0 : 1.0;
+  const double ss = parity ? -f.s : f.s;
+  const double muX = t.lam[i];
+  ++pairs;
+  if (partner_live) {
+    // Both members stored: (e, d) = U^T (e', d'), (lamE, lamD) = U^T (muE, muD).
+    const double e1 = cX, d1 = r.amp;
+    const double muE = muX, muD = t.lam[r.idx];
+    const double e0 = __dadd_rn(__dmul_rn(f.c, e1), __dmul_rn(ss, d1));
+    const double d0 = __dsub_rn(__dmul_rn(f.c, d1), __dmul_rn(ss, e1));
+    const double lE = __dadd_rn(__dmul_rn(f.c, muE), __dmul_rn(ss, muD));
+    const double lD = __dsub_rn(__dmul_rn(f.c, muD), __dmul_rn(ss, muE));
+    acc += sg * (lD * e0 - lE * d0);
+    if (t.born[i] == (unsigned int)k) {
+      t.amps[i] = dead_value(stamp);
+    } else {
+      t.amps[i] = e0;
+      t.lam[i] = lE;
+    }
+    if (t.born[r.idx] == (unsigned int)k) {
+      t.amps[r.idx] = dead_value(stamp);
+    } else {
+      t.amps[r.idx] = d0;
+      t.lam[r.idx] = lD;
+    }
+  } else if (ex) {
+    // E alone: D was absent before the factor, c_E' = cos c_E.
+    const double e0 = __ddiv_rn(cX, f.c);
+    const double lE = __dmul_rn(f.c, muX);
+    const double lD = -__dmul_rn(ss, muX);
+    acc += sg * (lD * e0);
+    t.amps[i] = e0;
+    t.lam[i] = lE;
+  } else {
+    // D alone: E was absent before the factor, c_D' = cos c_D.
+    const double d0 = __ddiv_rn(cX, f.c);
+    const double lD = __dmul_rn(f.c, muX);
+    const double lE = __dmul_rn(ss, muX);
+    acc += sg * (-lE * d0);
+    t.amps[i] = d0;
+    t.lam[i] = lD;
+  }
+}
+
+constexpr int kMaxSpin = 32;                          // spin-orbitals of one spin
+constexpr int kMaxPairs = kMaxSpin * (kMaxSpin - 1) / 2;  // same-spin empty pairs
+
+struct WarpLists {
+  unsigned char occ[2][kMaxSpin];
+  unsigned char emp[2][kMaxSpin];
+  int n_occ[2], n_emp[2];
+  unsigned short pairs[2][kMaxPairs];  // same-spin empty pairs (r | s << 8), r < s
+  int n_pairs[2];
+};
+
+__device__ __forceinline__ unsigned long long below(int p) { return (1ull << p) - 1ull; }
+
+// (ab|cd) in chemist notation over spatial orbitals.
+__device__ __forceinline__ double chem(const Integrals& in, int a, int b, int c, int d) {
+  const int n = in.n;
+  return __ldg(&in.g[((a * n + b) * n + c) * n + d]);
+}
+
+// <rs||pq> over spin-orbitals.
+__device__ __forceinline__ double anti(const Integrals& in, int r, int s, int p, int q) {
+  double v = 0.0;
+  if (((r ^ p) & 1) == 0 && ((s ^ q) & 1) == 0) v += chem(in, r >> 1, p >> 1, s >> 1, q >> 1);
+  if (((r ^ q) & 1) == 0 && ((s ^ p) & 1) == 0) v -= chem(in, r >> 1, q >> 1, s >> 1, p >> 1);
+  return v;
+}
+
+__device__ __forceinline__ double h_so(const Integrals& in, int p, int q) {
+  if ((p ^ q) & 1) return 0.0;
+  return __ldg(&in.h[(p >> 1) * in.n + (q >> 1)]);
+}
+
+// Sign of a+_r a+_s a_q a_p |I> (p, q occupied; r, s empty; all distinct).
+__device__ __forceinline__ int double_parity(unsigned long long I, int p, int q, int r, int s) {
+  const unsigned long long msk = below(p) ^ below(q) ^ below(r) ^ below(s);
+  return (__popcll(I & msk) + (p < q) + (p < s) + (q < s) + (p < r) + (q < r) + (s < r)) & 1;
+}
+
+// Sign of a+_r a_p |I>.
+__device__ __forceinline__ int single_parity(unsigned long long I, int p, int r) {
+  return (__popcll(I & (below(p) ^ below(r))) + (p < r)) & 1;
+}
+
+__device__ __forceinline__ bool lookup_live(const Table& t, unsigned long long key, double* amp) {
+  if (!filter_maybe(t, key)) return false;
+  unsigned long long h = home_slot(t, key);
+  for (int step = 0; step < MAX_PROBE; ++step) {
+    const Slot s = t.slots[h];
+    if (s.key == key) {
+      const double a = t.amps[s.idx];
+      if (is_dead(a)) return false;
+      *amp = a;
+      return true;
+    }
+    if (s.key == 0ull) return false;
+    h = (h + 1) & t.slot_mask;
+  }
+  raise_error(t.cnt, ERR_PROBE_BOUND);
+  return false;
+}
+
+// The lane's share of sigma_I = sum_{J in S} <I|H|J> c_J for one stored
+// determinant I (the warp's lanes split I's connections; sum with warp_sum).
+// L is this warp's shared-memory scratch.  Every lane of the warp calls this.
+__device__ __forceinline__ double sigma_entry(const Table& t, const Integrals& in, WarpLists& L,
+                                              unsigned long long I, double cI, int lane, unsigned long long& probes,
+                                              unsigned long long& hits) {
+  if (lane == 0) {
+    for (int sp = 0; sp < 2; ++sp) L.n_occ[sp] = L.n_emp[sp] = 0;
+    for (int p = 0; p < in.n_so; ++p) {
+      const int sp = p & 1;
+      if ((I >> p) & 1ull)
+        L.occ[sp][L.n_occ[sp]++] = (unsigned char)p;
+      else
+        L.emp[sp][L.n_emp[sp]++] = (unsigned char)p;
+    }
+  }
+  __syncwarp();
+  for (int sp = 0; sp < 2; ++sp) {
+    const int m = L.n_emp[sp];
+    const int np = m * (m - 1) / 2;
+    for (int u = lane; u < np; u += 32) {
+      // u -> (x, y), x < y, row-major over the strict upper triangle
+      int x = 0, rem = u;
+      while (rem >= m - 1 - x) {
+        rem -= m - 1 - x;
+        ++x;
+      }
+      const int y = x + 1 + rem;
+      L.pairs[sp][u] = (unsigned short)(L.emp[sp][x] | (L.emp[sp][y] << 8));
+    }
+    if (lane == 0) L.n_pairs[sp] = np;
+  }
+  __syncwarp();
+
+  double part = 0.0;
+  // Diagonal: lanes over the first index p.
+  {
+    double d = 0.0;
+    for (int sp = 0; sp < 2; ++sp)
+      for (int x = lane; x < L.n_occ[sp]; x += 32) {
+        const int p = L.occ[sp][x];
+        d += h_so(in, p, p);
+        for (int sq = 0; sq < 2; ++sq)
+          for (int y = 0; y < L.n_occ[sq]; ++y) {
+            const int q = L.occ[sq][y];
+            if (q != p) d += 0.5 * anti(in, p, q, p, q);
+          }
+      }
+    part += d * cI;
+  }
+  // Singles p -> r, same spin.
+  for (int sp = 0; sp < 2; ++sp) {
+    const int no = L.n_occ[sp], ne = L.n_emp[sp];
+    for (int u = lane; u < no * ne; u += 32) {
+      const int p = L.occ[sp][u / ne];
+      const int r = L.emp[sp][u % ne];
+      const unsigned long long J = I ^ ((1ull << p) | (1ull << r));
+      double cJ;
+      ++probes;
+      if (!lookup_live(t, J, &cJ)) continue;
+      ++hits;
+      double v = h_so(in, r, p);
+      for (int sk = 0; sk < 2; ++sk)
+        for (int y = 0; y < L.n_occ[sk]; ++y) {
+          const int kk = L.occ[sk][y];
+          if (kk != p) v += anti(in, r, kk, p, kk);
+        }
+      part += (single_parity(I, p, r) ? -v : v) * cJ;
+    }
+  }
+  // Doubles: same-spin (p < q from one spin, r < s from the same spin).
+  for (int sp = 0; sp < 2; ++sp) {
+    const int no = L.n_occ[sp];
+    const int np = L.n_pairs[sp];
+    for (int x = 0; x < no; ++x)
+      for (int y = x + 1; y < no; ++y) {
+        const int p = L.occ[sp][x], q = L.occ[sp][y];
+        const unsigned long long hole = (1ull << p) | (1ull << q);
+        for (int u = lane; u < np; u += 32) {
+          const unsigned short pr = L.pairs[sp][u];
+          const int r = pr & 0xFF, s = pr >> 8;
+          const unsigned long long J = I ^ (hole | (1ull << r) | (1ull << s));
+          double cJ;
+          ++probes;
+          if (!lookup_live(t, J, &cJ)) continue;
+          ++hits;
+          const double v = anti(in, r, s, p, q);
+          part += (double_parity(I, p, q, r, s) ? -v : v) * cJ;
+        }
+      }
+  }
+  // Doubles: opposite spin (p alpha, q beta -> r alpha, s beta).
+  {
+    const int noa = L.n_occ[0], nob = L.n_occ[1], nea = L.n_emp[0], neb = L.n_emp[1];
+    const int nE = nea * neb;
+    for (int x = 0; x < noa; ++x)
+      for (int y = 0; y < nob; ++y) {
+        const int p = L.occ[0][x], q = L.occ[1][y];
+        const unsigned long long hole = (1ull << p) | (1ull << q);
+        for (int u = lane; u < nE; u += 32) {
+          const int r = L.emp[0][u / neb], s = L.emp[1][u % neb];
+          const unsigned long long J = I ^ (hole | (1ull << r) | (1ull << s));
+          double cJ;
+          ++probes;
+          if (!lookup_live(t, J, &cJ)) continue;
+          ++hits;
+          const double v = anti(in, r, s, p, q);
+          part += (double_parity(I, p, q, r, s) ? -v : v) * cJ;
+        }
+      }
+  }
+  return part;
+}
+
+}  // namespace ucc

@@ -284,3 +284,20 @@ def test_truncation_gradient(torch_cuda):
     assert abs(E - E_ref) <= E_TOL
     assert np.max(np.abs(g - g_ref)) <= G_TOL
     assert ctx.stats()["cut"] > 0
+
+
+@pytest.mark.parametrize("case,stride", [("pruned_small", 7), ("pruned_small", 1), ("cfg2", 38)])
+def test_gradient_segment_checkpoints(torch_cuda, case, stride):
+    # Snapshots every `stride` factors, each segment recomputed and swept
+    # backward: the same gradient as the oracle's checkpointed adjoint.
+    if case == "cfg2":
+        prob = synth.config_problem(2)
+        E_ref, g_ref = load_golden("cfg2_energy_gradient.txt")
+    else:
+        prob = small_pruned()
+        E_ref, g_ref = oracle_for(prob).gradient()
+    ctx = ctx_for(prob)
+    ctx.set_options(checkpoint_stride=stride)
+    E, g = ctx.gradient()
+    assert abs(E - E_ref) <= E_TOL
+    assert np.max(np.abs(g - g_ref)) <= G_TOL
