@@ -235,13 +235,12 @@ def run_ours(args, prob):
     torch.cuda.synchronize()
     clocks = sampler.stop()
     ms = sum(times) / len(times)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
     n_steps = len(times)
+    # Replicas: the slowest rank's step time, the work of all ranks.
+    from paper_2301_05726_gb300.replicas import combine_step
+    ms, rot_all = combine_step(ms, tot["rotations"] / n_steps, device=dev)
     rot_per_eval = tot["rotations"] / n_steps
-    value = rot_per_eval * world / (ms / 1e3)
+    value = rot_all / (ms / 1e3)
 
     # End to end through the public API with host buffers.
     e2e_times = []
@@ -303,7 +302,7 @@ def run_ours(args, prob):
         "vs_plain": {"plain": "per-theta central differences on the GPU, 2K+1 energy evaluations",
                      "energy_eval_s": energy_eval_s, "plain_gradient_s_extrapolated": plain_s,
                      "adjoint_gradient_s": ms / 1e3, "speedup": plain_s / (ms / 1e3)},
-        "e2e": {"value": rot_per_eval * world / (e2e_ms / 1e3), "unit": UNIT,
+        "e2e": {"value": rot_all / (e2e_ms / 1e3), "unit": UNIT,
                 "h2d_bytes_per_step": 48 * prob.n_exc, "d2h_bytes_per_step": 8 * prob.n_exc + 8},
         "gpu_launches": int(tot["kernel_launches"]),
         "roofline": roof,

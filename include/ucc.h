@@ -93,8 +93,11 @@ typedef struct {
   int64_t max_entries;  /* hard cap on stored determinants, 0 = device memory */
   int32_t probe_width;  /* lanes per hash probe: 1, 2, 4 or 8; 0 = autotuned */
   int32_t checkpoint_stride; /* gradient: factors between snapshots of psi; 0 =
-                                ceil(sqrt(K)) with a cut, else one segment */
-  int32_t reserved[4];
+                                one segment while the kill tape fits its
+                                budget, else ceil(sqrt(K)) */
+  int32_t tape_budget_mb;    /* kill-tape budget in MiB; 0 = 60% of free memory */
+  int32_t record_entropy;    /* ucc_apply records Eq. 6 after every factor */
+  int32_t reserved[2];
 } ucc_options;
 
 /* Counters of the last apply / gradient call. */
@@ -120,6 +123,7 @@ typedef struct {
   int64_t recompute_created;   /* gradient: entries created while recomputing segments */
   int64_t forward_launches;    /* forward factor launches (incl. recomputation) */
   int64_t reverse_launches;    /* reverse factor launches */
+  int64_t probe_width;         /* lanes per hash probe in use (fixed or autotuned) */
   double apply_ms;          /* device time of the last forward pass */
   double energy_ms;         /* device time of the last energy evaluation */
   double reverse_ms;        /* device time of the last reverse sweep */
@@ -166,6 +170,13 @@ ucc_status ucc_gradient(ucc_ctx* ctx, double eps, double* E, double* grad, int o
  * too small.  Synchronises. */
 ucc_status ucc_get_wavefunction(ucc_ctx* ctx, size_t cap, size_t* n, uint64_t* keys, double* amps, double* sigma,
                                 int on_device);
+
+/* The Eq. 6 entropy S_k = -sum_I |c_I|^2 ln|c_I|^2 of the stored state after
+ * each factor k of the last ucc_apply (after its eps rule and cut), the
+ * quantity the paper plots per factor index (Figs. 3b and 4).  Needs
+ * ucc_options.record_entropy; S is a host array of n = n_exc doubles.
+ * UCC_ESTATE if the last apply did not record it.  Synchronises. */
+ucc_status ucc_get_entropy(ucc_ctx* ctx, double* S, int32_t n);
 
 /* Counters of the last call.  Does not synchronise beyond what that call did. */
 ucc_status ucc_get_stats(const ucc_ctx* ctx, ucc_stats* out);

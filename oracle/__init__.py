@@ -55,7 +55,7 @@ def _load():
         lib.orc_problem_free.argtypes = [vp]
         lib.orc_apply.restype = vp
         lib.orc_apply.argtypes = [vp, dp, ctypes.c_int, ctypes.c_double, ctypes.c_longlong, ctypes.c_longlong,
-                                  ctypes.POINTER(_Counts)]
+                                  ctypes.POINTER(_Counts), dp]
         lib.orc_wf_from_arrays.restype = vp
         lib.orc_wf_from_arrays.argtypes = [ctypes.c_longlong, u64p, dp]
         lib.orc_wf_size.restype = ctypes.c_longlong
@@ -116,11 +116,25 @@ class Oracle:
         n_max, n_cut = self._cut(n_max, n_cut)
         nf = len(th) if n_factors is None else int(n_factors)
         cnt = _Counts()
-        wf = self.lib.orc_apply(self.handle, _dp(th), nf, float(eps), int(n_max), int(n_cut), ctypes.byref(cnt))
+        wf = self.lib.orc_apply(self.handle, _dp(th), nf, float(eps), int(n_max), int(n_cut), ctypes.byref(cnt),
+                                None)
         keys, amps = _export(self.lib, wf)
         self.lib.orc_wf_free(wf)
         counts = {f: getattr(cnt, f) for f, _ in _Counts._fields_}
         return keys, amps, counts
+
+    def entropy_per_factor(self, theta=None, eps=None, n_factors=None, n_max=None, n_cut=None):
+        """Eq. 6 after each factor (array of n_factors)."""
+        th = self._theta(theta)
+        eps = self.prob.eps if eps is None else eps
+        n_max, n_cut = self._cut(n_max, n_cut)
+        nf = len(th) if n_factors is None else int(n_factors)
+        out = np.zeros(nf)
+        cnt = _Counts()
+        wf = self.lib.orc_apply(self.handle, _dp(th), nf, float(eps), int(n_max), int(n_cut), ctypes.byref(cnt),
+                                _dp(out))
+        self.lib.orc_wf_free(wf)
+        return out
 
     def _wf(self, keys, amps):
         keys = np.ascontiguousarray(keys, dtype=np.uint64)

@@ -213,11 +213,29 @@ void truncate_top(Psi& psi, long long n_max, long long n_cut, Counts& cnt) {
   for (const auto& kv : all) psi[kv.first] = kv.second;
 }
 
+// Eq. 6: S = - sum_I |c_I|^2 ln |c_I|^2 over the map (0 ln 0 = 0).
+double entropy(const Psi& psi) {
+  double s = 0.0, comp = 0.0;  // Neumaier
+  for (const auto& kv : psi) {
+    const double p = kv.second * kv.second;
+    if (p == 0.0) continue;
+    const double x = -p * std::log(p);
+    const double t = s + x;
+    if (std::fabs(s) >= std::fabs(x))
+      comp += (s - t) + x;
+    else
+      comp += (x - t) + s;
+    s = t;
+  }
+  return s + comp;
+}
+
 Psi run_factors(const Problem& P, const double* theta, int k0, int k1, double eps, long long n_max,
-                long long n_cut, Psi psi, Counts& cnt) {
+                long long n_cut, Psi psi, Counts& cnt, double* entropy_out = nullptr) {
   for (int k = k0; k < k1; ++k) {
     psi = apply_factor(P.exc[k], std::cos(theta[k]), std::sin(theta[k]), eps, psi, cnt);
     truncate_top(psi, n_max, n_cut, cnt);
+    if (entropy_out) entropy_out[k] = entropy(psi);
   }
   return psi;
 }
@@ -481,13 +499,14 @@ void* orc_problem_new(int n_spatial, int n_alpha, int n_beta, const double* h, c
 void orc_problem_free(void* p) { delete static_cast<Problem*>(p); }
 
 // Apply factors [0, n_factors) to the reference; returns a wavefunction handle.
+// entropy_out (optional, n_factors doubles): Eq. 6 after each factor.
 void* orc_apply(const void* prob, const double* theta, int n_factors, double eps, long long n_max, long long n_cut,
-                orc_counts* counts) {
+                orc_counts* counts, double* entropy_out) {
   const Problem& P = *static_cast<const Problem*>(prob);
   Counts cnt;
   Psi psi;
   psi[P.reference()] = 1.0;
-  psi = run_factors(P, theta, 0, n_factors, eps, n_max, n_cut, psi, cnt);
+  psi = run_factors(P, theta, 0, n_factors, eps, n_max, n_cut, psi, cnt, entropy_out);
   if (counts) *counts = orc_counts{cnt.rotations, cnt.created, cnt.dropped_new, cnt.dropped_old, cnt.cut};
   return new WF(export_sorted(psi));
 }

@@ -18,7 +18,7 @@ STATUS_NAMES = {0: "UCC_OK", 1: "UCC_EINVAL", 2: "UCC_ENOMEM", 3: "UCC_ECAPACITY
 # Every symbol include/ucc.h declares.
 EXPORTS = ["ucc_create", "ucc_set_theta", "ucc_set_options", "ucc_apply", "ucc_energy", "ucc_gradient",
            "ucc_get_wavefunction", "ucc_get_stats", "ucc_batch_run", "ucc_last_error", "ucc_destroy",
-           "ucc_energy_static"]
+           "ucc_energy_static", "ucc_get_entropy"]
 
 
 class Hamiltonian(ctypes.Structure):
@@ -35,7 +35,8 @@ class Ansatz(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("n_max", ctypes.c_int64), ("n_cut", ctypes.c_int64), ("max_entries", ctypes.c_int64),
                 ("probe_width", ctypes.c_int32), ("checkpoint_stride", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("tape_budget_mb", ctypes.c_int32), ("record_entropy", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class Stats(ctypes.Structure):
@@ -43,7 +44,7 @@ class Stats(ctypes.Structure):
         "n_det", "rotations", "created", "dropped_new", "dropped_old", "cut", "peak_entries", "capacity_entries",
         "hash_slots", "rebuilds", "tape_entries", "kernel_launches", "scanned", "sigma_probes", "sigma_hits",
         "reverse_pairs", "recompute_scanned", "recompute_rotations", "recompute_created", "forward_launches",
-        "reverse_launches")] + \
+        "reverse_launches", "probe_width")] + \
         [(n, ctypes.c_double) for n in ("apply_ms", "energy_ms", "reverse_ms", "forward_kernel_ms",
                                         "reverse_kernel_ms")]
 
@@ -85,6 +86,8 @@ def load(path: str = LIB_PATH):
     lib.ucc_get_wavefunction.restype = st
     lib.ucc_get_wavefunction.argtypes = [vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t), vp, vp, vp,
                                          ctypes.c_int]
+    lib.ucc_get_entropy.restype = st
+    lib.ucc_get_entropy.argtypes = [vp, dp, ctypes.c_int32]
     lib.ucc_get_stats.restype = st
     lib.ucc_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
     lib.ucc_batch_run.restype = st

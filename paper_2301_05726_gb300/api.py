@@ -51,9 +51,10 @@ class UCCContext:
         handle = ctypes.c_void_p()
         check(self.lib.ucc_create(ctypes.byref(ham), ctypes.byref(an), self.stream, ctypes.byref(handle)))
         self.handle = handle
-        n_max, n_cut = int(getattr(prob, "n_max", 0)), int(getattr(prob, "n_cut", 0))
-        if probe_width or max_entries or n_max:
-            self.set_options(n_max=n_max, n_cut=n_cut, probe_width=probe_width, max_entries=max_entries)
+        self._opt = dict(n_max=int(getattr(prob, "n_max", 0)), n_cut=int(getattr(prob, "n_cut", 0)),
+                         max_entries=int(max_entries), probe_width=int(probe_width), checkpoint_stride=0,
+                         tape_budget_mb=0, record_entropy=0)
+        self.set_options()
 
     def close(self):
         if getattr(self, "handle", None):
@@ -63,8 +64,17 @@ class UCCContext:
     def __del__(self):
         self.close()
 
-    def set_options(self, n_max=0, n_cut=0, max_entries=0, probe_width=0, checkpoint_stride=0):
-        o = Options(int(n_max), int(n_cut), int(max_entries), int(probe_width), int(checkpoint_stride))
+    def set_options(self, **changes):
+        """Update run options (the rest keep their values): n_max, n_cut,
+        max_entries, probe_width, checkpoint_stride, tape_budget_mb,
+        record_entropy.  The problem's own cut is the starting point."""
+        unknown = set(changes) - set(self._opt)
+        if unknown:
+            raise TypeError(f"unknown options {sorted(unknown)}")
+        self._opt.update({k: int(v) for k, v in changes.items()})
+        o = self._opt
+        o = Options(o["n_max"], o["n_cut"], o["max_entries"], o["probe_width"], o["checkpoint_stride"],
+                    o["tape_budget_mb"], o["record_entropy"])
         check(self.lib.ucc_set_options(self.handle, ctypes.byref(o)))
 
     def set_theta(self, theta):
@@ -117,6 +127,12 @@ class UCCContext:
         if with_sigma:
             return keys[order], amps[order], sig[order]
         return keys[order], amps[order]
+
+    def entropy(self):
+        """Eq. 6 entropy after each factor of the last apply (needs record_entropy)."""
+        S = np.zeros(self.K)
+        check(self.lib.ucc_get_entropy(self.handle, _dp(S), self.K))
+        return S
 
     def stats(self):
         s = Stats()

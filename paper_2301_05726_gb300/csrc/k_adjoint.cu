@@ -30,9 +30,10 @@ __global__ void __launch_bounds__(kThreads) k_tape_reinsert(Table t, Tape tape, 
   const unsigned long long lo = min(tape.off[k], hi);
   const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
   for (unsigned long long x = lo + (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; x < hi; x += stride) {
-    const unsigned long long key = tape.key[x];
-    const double val = tape.val[x];
-    const unsigned int born = tape.born[x];
+    const TapeRec rec = tape_at(tape, x);
+    const unsigned long long key = rec.key;
+    const double val = rec.val;
+    const unsigned int born = rec.born;
     Lookup r = find1(t, key, 0u);
     if (r.state == ALIVE) {
       raise_error(t.cnt, ERR_CONSISTENCY);
@@ -56,9 +57,8 @@ __global__ void __launch_bounds__(kThreads) k_reverse(Table t, const Factor* __r
   const unsigned long long nwarps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
   double acc = 0.0;
   unsigned int pairs = 0;
-  for (unsigned long long base = warp * 32ull; base < n; base += nwarps * 32ull) {
+  for (unsigned long long base = warp * 32ull; base < n; base += nwarps * 32ull)
     reverse_entry<G>(t, f, k, stamp, base + lane, base + lane < n, acc, pairs);
-  }
   {
     __shared__ unsigned long long s_pairs;
     if (threadIdx.x == 0) s_pairs = 0;

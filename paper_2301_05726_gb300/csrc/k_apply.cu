@@ -13,28 +13,29 @@ namespace {
 
 constexpr int kThreads = 256;
 
+// Block totals of the step counters: a warp reduction, then one shared
+// atomic per warp and one global atomic per block and counter.
 __device__ __forceinline__ void block_add_counts(Counters* c, unsigned long long rot, unsigned long long cre,
                                                  unsigned long long dnew, unsigned long long dold,
                                                  long long dead_delta) {
-  __shared__ unsigned long long s_rot, s_cre, s_dnew, s_dold;
-  __shared__ long long s_dead;
-  if (threadIdx.x == 0) {
-    s_rot = s_cre = s_dnew = s_dold = 0;
-    s_dead = 0;
+  __shared__ unsigned long long s_v[5];
+  if (threadIdx.x < 5) s_v[threadIdx.x] = 0;
+  __syncthreads();
+  unsigned long long v[5] = {rot, cre, dnew, dold, (unsigned long long)dead_delta};
+#pragma unroll
+  for (int x = 0; x < 5; ++x) v[x] = warp_sum_u64(v[x]);
+  if ((threadIdx.x & 31u) == 0) {
+#pragma unroll
+    for (int x = 0; x < 5; ++x)
+      if (v[x]) atomicAdd(&s_v[x], v[x]);
   }
   __syncthreads();
-  if (rot) atomicAdd(&s_rot, rot);
-  if (cre) atomicAdd(&s_cre, cre);
-  if (dnew) atomicAdd(&s_dnew, dnew);
-  if (dold) atomicAdd(&s_dold, dold);
-  if (dead_delta) atomicAdd((unsigned long long*)&s_dead, (unsigned long long)dead_delta);
-  __syncthreads();
   if (threadIdx.x == 0) {
-    if (s_rot) atomicAdd(&c->rotations, s_rot);
-    if (s_cre) atomicAdd(&c->created, s_cre);
-    if (s_dnew) atomicAdd(&c->dropped_new, s_dnew);
-    if (s_dold) atomicAdd(&c->dropped_old, s_dold);
-    if (s_dead) atomicAdd(&c->n_dead, (unsigned long long)s_dead);
+    if (s_v[0]) atomicAdd(&c->rotations, s_v[0]);
+    if (s_v[1]) atomicAdd(&c->created, s_v[1]);
+    if (s_v[2]) atomicAdd(&c->dropped_new, s_v[2]);
+    if (s_v[3]) atomicAdd(&c->dropped_old, s_v[3]);
+    if (s_v[4]) atomicAdd(&c->n_dead, s_v[4]);
   }
 }
 
@@ -61,7 +62,22 @@ __global__ void __launch_bounds__(kThreads) k_forward(Table t, const Factor* __r
       forward_entry<G, RECORD>(t, f, k, eps, stamp, tape, base + lane, base + lane < n, sc);
   }
   block_add_counts(t.cnt, sc.rot, sc.cre, sc.dnew, sc.dold, sc.dead_delta);
-  if (last_block_arrive(t.cnt) && threadIdx.x == 0) {
+  if (t.entropy) {
+    const double b = block_sum(sc.dS);
+    if (threadIdx.x == 0) t.partials[blockIdx.x] = b;
+  }
+  const bool last = last_block_arrive(t.cnt);
+  if (last && t.entropy && !skip) {
+    // Fixed-order sum of the block changes, added once to the running total.
+    double s = 0.0;
+    for (unsigned int x = threadIdx.x; x < gridDim.x; x += blockDim.x) s += ld_cg(&t.partials[x]);
+    s = block_sum(s);
+    if (threadIdx.x == 0) {
+      t.cnt->entropy += s;
+      t.entropy[k] = t.cnt->entropy;
+    }
+  }
+  if (last && threadIdx.x == 0) {
     Counters* c = t.cnt;
     c->done = 0u;
     if (!skip) {
@@ -86,6 +102,7 @@ __global__ void __launch_bounds__(kThreads) k_forward(Table t, const Factor* __r
 }
 
 // Copy the live entries of `from` into `to` (unordered), counting in new_n.
+// with_born: 0 keys and amplitudes, 1 also born, 2 also born and lam.
 __global__ void __launch_bounds__(kThreads) k_compact(Table from, Table to, int with_born) {
   const unsigned long long n = min(*((volatile unsigned long long*)&from.cnt->n_tail), from.cap_n);
   const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
@@ -100,6 +117,7 @@ __global__ void __launch_bounds__(kThreads) k_compact(Table from, Table to, int 
     to.keys[j] = from.keys[i];
     to.amps[j] = a;
     if (with_born) to.born[j] = from.born[i];
+    if (with_born > 1) to.lam[j] = from.lam[i];  // mid reverse sweep: keep the adjoint
   }
 }
 
@@ -260,6 +278,60 @@ cudaError_t launch_restore(const Table& t, const unsigned long long* keys, const
 
 cudaError_t launch_transfer_lambda(const Table& dst, const Table& src, int grid, cudaStream_t st) {
   k_transfer_lambda<<<grid, 256, 0, st>>>(dst, src);
+  return cudaGetLastError();
+}
+
+}  // namespace ucc
+
+namespace ucc {
+
+namespace {
+
+// Read-only replay of factor f's partner lookups on the live table with
+// G-lane probes (the autotuner times it); the result only feeds a checksum.
+template <int G>
+__global__ void __launch_bounds__(256) k_probe_bench(Table t, Factor f, unsigned long long* sink) {
+  const unsigned long long n = min(*((volatile unsigned long long*)&t.cnt->n_tail), t.cap_n);
+  const unsigned int lane = threadIdx.x & 31u;
+  const unsigned long long warp = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const unsigned long long nwarps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
+  const unsigned long long m = f.occ | f.vir;
+  unsigned long long acc = 0;
+  for (unsigned long long base = warp * 32ull; base < n; base += nwarps * 32ull) {
+    const unsigned long long i = base + lane;
+    bool act = i < n;
+    unsigned long long X = 0;
+    if (act) {
+      X = t.keys[i];
+      const bool ex = ((X & f.occ) == f.occ) && ((X & f.vir) == 0ull);
+      const bool de = ((X & f.vir) == f.vir) && ((X & f.occ) == 0ull);
+      act = ex || de;
+    }
+    Lookup r = findG<G>(t, X ^ m, act, 0u);
+    if (act) acc += r.idx + (unsigned long long)r.state;
+  }
+  acc = warp_sum_u64(acc);
+  if (lane == 0 && acc) atomicAdd(sink, acc);
+}
+
+}  // namespace
+
+cudaError_t launch_probe_bench(const Table& t, const Factor& f, int probe_width, unsigned long long* sink, int grid,
+                               cudaStream_t st) {
+  switch (probe_width) {
+    case 2:
+      k_probe_bench<2><<<grid, 256, 0, st>>>(t, f, sink);
+      break;
+    case 4:
+      k_probe_bench<4><<<grid, 256, 0, st>>>(t, f, sink);
+      break;
+    case 8:
+      k_probe_bench<8><<<grid, 256, 0, st>>>(t, f, sink);
+      break;
+    default:
+      k_probe_bench<1><<<grid, 256, 0, st>>>(t, f, sink);
+      break;
+  }
   return cudaGetLastError();
 }
 

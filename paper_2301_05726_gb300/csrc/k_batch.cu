@@ -232,16 +232,17 @@ __global__ void __launch_bounds__(kThreads) k_tape_reinsert_batch(const JobView*
     const JobView& jv = jobs[j];
     const int k = js[j].k;
     const unsigned long long x = min(jv.tape.off[k], jv.tape.cap) + (g - s_base[j]);
-    const unsigned long long key = jv.tape.key[x];
+    const TapeRec rec = tape_at(jv.tape, x);
+    const unsigned long long key = rec.key;
     Lookup r = find1(jv.t, key, 0u);
     if (r.state == ALIVE) {
       raise_error(jv.t.cnt, ERR_CONSISTENCY);
     } else if (r.state == DEAD_OLD || r.state == DEAD_NOW) {
-      jv.t.amps[r.idx] = jv.tape.val[x];
+      jv.t.amps[r.idx] = rec.val;
       jv.t.lam[r.idx] = 0.0;
-      jv.t.born[r.idx] = jv.tape.born[x];
+      jv.t.born[r.idx] = rec.born;
     } else {
-      insert_new(jv.t, key, jv.tape.val[x], jv.tape.born[x], r.slot, true, true);
+      insert_new(jv.t, key, rec.val, rec.born, r.slot, true, true);
     }
   }
 }

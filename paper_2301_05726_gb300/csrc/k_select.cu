@@ -9,7 +9,7 @@
 // every block histograms its share of the live entries in shared memory, and
 // the last block to finish picks the bin that holds the target rank.
 
-#include "ucc_device.cuh"
+#include "ucc_steps.cuh"
 
 namespace ucc {
 
@@ -145,6 +145,7 @@ __global__ void __launch_bounds__(kThreads) k_select_mark(Table t, SelectState* 
   const unsigned long long Kt = sel->key_prefix;
   const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
   unsigned long long dropped = 0;
+  double dS = 0.0;
   for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     const double a = t.amps[i];
     if (is_dead(a)) continue;
@@ -152,12 +153,14 @@ __global__ void __launch_bounds__(kThreads) k_select_mark(Table t, SelectState* 
     bool keep = u > T;
     if (u == T) keep = !keys || t.keys[i] <= Kt;
     if (keep) continue;
+    if (t.entropy) dS -= entropy_term(a);
     if (RECORD) {
       const unsigned long long ti = aggregated_add(&t.cnt->tape_n);
       if (ti < tape.cap) {
-        tape.key[ti] = t.keys[i];
-        tape.val[ti] = a;
-        tape.born[ti] = t.born[i];
+        TapeRec& rec = tape_at(tape, ti);
+        rec.key = t.keys[i];
+        rec.val = a;
+        rec.born = t.born[i];
       } else {
         raise_error(t.cnt, ERR_TAPE_FULL);
       }
@@ -174,7 +177,21 @@ __global__ void __launch_bounds__(kThreads) k_select_mark(Table t, SelectState* 
     atomicAdd(&t.cnt->n_dead, s_d);
     atomicAdd(&sel->cut_total, s_d);
   }
-  if (last_block_arrive(t.cnt) && threadIdx.x == 0) {
+  if (t.entropy) {
+    const double b = block_sum(dS);
+    if (threadIdx.x == 0) t.partials[blockIdx.x] = b;
+  }
+  const bool last = last_block_arrive(t.cnt);
+  if (last && t.entropy) {
+    double s = 0.0;
+    for (unsigned int x = threadIdx.x; x < gridDim.x; x += blockDim.x) s += ld_cg(&t.partials[x]);
+    s = block_sum(s);
+    if (threadIdx.x == 0) {
+      t.cnt->entropy += s;
+      t.entropy[k] = t.cnt->entropy;
+    }
+  }
+  if (last && threadIdx.x == 0) {
     t.cnt->done = 0u;
     if (RECORD) tape.off[k + 1] = ld_cg(&t.cnt->tape_n);
   }

@@ -7,7 +7,10 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/ucc.h"
@@ -161,15 +164,20 @@ struct ucc_ctx {
   double* d_partials = nullptr;
   int partial_cap = 0;
   SelectState* d_sel = nullptr;
+  double* d_entropy = nullptr;  // [K] Eq. 6 after each factor of the last apply
+  bool entropy_on = false;
+  bool have_entropy = false;
   TableSet ts[2];  // ts[main] holds psi; the other is the gradient's work table
   int main = 0;
   std::vector<Snapshot> snaps;
-  // kill tape of the segment being reversed
-  unsigned long long* t_key = nullptr;
-  double* t_val = nullptr;
-  unsigned int* t_born = nullptr;
+  // kill tape (paged) of the segment being reversed
+  std::vector<TapeRec*> t_pages;
+  TapeRec** d_pages = nullptr;          // [kTapeMaxPages]
   unsigned long long* t_off = nullptr;  // K + 1
   unsigned long long tape_cap = 0;
+  unsigned long long tape_budget = 0;   // bytes the tape may take in this call
+  bool tape_over_budget = false;
+  bool force_segments = false;
 
   bool have_psi = false;
   bool have_sigma = false;
@@ -195,13 +203,12 @@ struct ucc_ctx {
     t.cap_n = s.cur.cap_n;
     t.cnt = s.d_cnt;
     t.partials = d_partials;
+    t.entropy = entropy_on ? d_entropy : nullptr;
     return t;
   }
   Tape tape() const {
     Tape tp;
-    tp.key = t_key;
-    tp.val = t_val;
-    tp.born = t_born;
+    tp.pages = d_pages;
     tp.off = t_off;
     tp.cap = tape_cap;
     return tp;
@@ -233,6 +240,7 @@ Factor make_factor(int i, int j, int a, int b, double th) {
   }
   f.c = std::cos(th);
   f.s = std::sin(th);
+  f.ic = 1.0 / f.c;
   return f;
 }
 
@@ -268,7 +276,7 @@ unsigned long long slots_for(unsigned long long cap_n) {
 
 // Copy live entries into arrays of capacity new_cap (dropping dead entries) and
 // rebuild the hash.  Counters are updated on the device.
-ucc_status rebuild(ucc_ctx* c, TableSet& s, unsigned long long new_cap) {
+ucc_status rebuild(ucc_ctx* c, TableSet& s, unsigned long long new_cap, bool with_lam = false) {
   unsigned long long ns = slots_for(new_cap);
   if (s.spare.cap_n != new_cap || s.spare.n_slots != ns) {
     s.spare.release();
@@ -295,7 +303,7 @@ ucc_status rebuild(ucc_ctx* c, TableSet& s, unsigned long long new_cap) {
   CUDA_TRY(cudaMemsetAsync(to.slots, 0, ns * sizeof(Slot), c->stream));
   CUDA_TRY(cudaMemsetAsync(to.filt, 0, ns / 4 * sizeof(unsigned int), c->stream));
   int grid = c->full_grid();
-  CUDA_TRY(launch_compact(from, to, 1, grid, c->stream));
+  CUDA_TRY(launch_compact(from, to, with_lam ? 2 : 1, grid, c->stream));
   CUDA_TRY(launch_rehash(to, grid, c->stream));
   CUDA_TRY(launch_finish_rebuild(to, c->stream));
   c->launches += 3;
@@ -306,30 +314,32 @@ ucc_status rebuild(ucc_ctx* c, TableSet& s, unsigned long long new_cap) {
   return UCC_OK;
 }
 
+// Grow the paged tape to hold `need` records (pages are added, never moved).
+// Past the call's budget it stops with tape_over_budget set; the gradient
+// then falls back to segment checkpoints.
 ucc_status ensure_tape(ucc_ctx* c, unsigned long long need) {
-  if (need <= c->tape_cap) return UCC_OK;
-  unsigned long long cap = std::max<unsigned long long>(need, 2 * c->tape_cap);
-  cap = std::max<unsigned long long>(cap, 1 << 16);
-  unsigned long long* nk = nullptr;
-  double* nv = nullptr;
-  unsigned int* nb = nullptr;
-  UCC_TRY(dalloc(&nk, cap));
-  UCC_TRY(dalloc(&nv, cap));
-  UCC_TRY(dalloc(&nb, cap));
-  if (c->tape_cap) {
-    CUDA_TRY(cudaMemcpyAsync(nk, c->t_key, c->tape_cap * sizeof(*nk), cudaMemcpyDeviceToDevice, c->stream));
-    CUDA_TRY(cudaMemcpyAsync(nv, c->t_val, c->tape_cap * sizeof(*nv), cudaMemcpyDeviceToDevice, c->stream));
-    CUDA_TRY(cudaMemcpyAsync(nb, c->t_born, c->tape_cap * sizeof(*nb), cudaMemcpyDeviceToDevice, c->stream));
+  while (c->tape_cap < need) {
+    if ((int)c->t_pages.size() >= kTapeMaxPages) return fail(UCC_ECAPACITY, "kill tape page table full");
+    const unsigned long long bytes = (c->tape_cap + kTapePageRecs) * sizeof(TapeRec);
+    if (c->tape_budget && bytes > c->tape_budget) {
+      c->tape_over_budget = true;
+      return fail(UCC_ECAPACITY, "kill tape over its memory budget");
+    }
+    TapeRec* page = nullptr;
+    UCC_TRY(dalloc(&page, kTapePageRecs));
+    CUDA_TRY(cudaMemcpyAsync(c->d_pages + c->t_pages.size(), &page, sizeof(TapeRec*), cudaMemcpyHostToDevice,
+                             c->stream));
     CUDA_TRY(cudaStreamSynchronize(c->stream));
+    c->t_pages.push_back(page);
+    c->tape_cap += kTapePageRecs;
   }
-  dfree(c->t_key);
-  dfree(c->t_val);
-  dfree(c->t_born);
-  c->t_key = nk;
-  c->t_val = nv;
-  c->t_born = nb;
-  c->tape_cap = cap;
   return UCC_OK;
+}
+
+void release_tape(ucc_ctx* c) {
+  for (auto& p : c->t_pages) dfree(p);
+  c->t_pages.clear();
+  c->tape_cap = 0;
 }
 
 unsigned long long reference_key(const ucc_ctx* c) {
@@ -352,7 +362,7 @@ ucc_status reset_table(ucc_ctx* c, TableSet& s) {
 
 // Start the kill tape of a segment that begins at factor k0.
 ucc_status reset_tape(ucc_ctx* c, TableSet& s, int k0) {
-  UCC_TRY(ensure_tape(c, 1 << 16));
+  UCC_TRY(ensure_tape(c, 1));
   CUDA_TRY(cudaMemsetAsync(&s.d_cnt->tape_n, 0, sizeof(unsigned long long), c->stream));
   CUDA_TRY(cudaMemsetAsync(c->t_off + k0, 0, sizeof(unsigned long long), c->stream));
   return UCC_OK;
@@ -394,6 +404,56 @@ int pick_probe_width(ucc_ctx* c) {
   return c->probe_width;
 }
 
+// Probe-width autotuner: per (spin-orbitals, floor(log2 stored entries)) the
+// fastest of 1, 2, 4 and 8 lanes per lookup, timed on the live table by a
+// read-only replay of the next factor's partner lookups.  Results are kept
+// for the life of the process.
+std::mutex g_tune_mutex;
+std::map<std::pair<int, int>, int> g_tuned;
+
+ucc_status autotune(ucc_ctx* c, TableSet& s, int k, unsigned long long n) {
+  if (c->opt.probe_width != 0 || n < (1ull << 16) || k >= c->K) return UCC_OK;
+  int bucket = 0;
+  while ((2ull << bucket) <= n) ++bucket;
+  const std::pair<int, int> key(c->n_so, bucket);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    auto it = g_tuned.find(key);
+    if (it != g_tuned.end()) {
+      c->probe_width = it->second;
+      return UCC_OK;
+    }
+  }
+  unsigned long long* sink = nullptr;
+  UCC_TRY(dalloc(&sink, 1));
+  const int widths[4] = {1, 2, 4, 8};
+  float best_ms = 0.f;
+  int best = 1;
+  ucc_status st = UCC_OK;
+  for (int rep = 0; rep < 2 && st == UCC_OK; ++rep)
+    for (int w : widths) {
+      if (cudaEventRecord(c->kev[0], c->stream) != cudaSuccess ||
+          launch_probe_bench(c->table(s), c->factors[k], w, sink, c->full_grid(), c->stream) != cudaSuccess ||
+          cudaEventRecord(c->kev[1], c->stream) != cudaSuccess || cudaEventSynchronize(c->kev[1]) != cudaSuccess) {
+        st = fail(UCC_ECUDA, "probe-width autotuning failed");
+        break;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, c->kev[0], c->kev[1]);
+      if (rep == 1 && (w == 1 || ms < best_ms)) {
+        best_ms = ms;
+        best = w;
+      }
+      c->launches++;
+    }
+  dfree(sink);
+  UCC_TRY(st);
+  c->probe_width = best;
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  g_tuned[key] = best;
+  return UCC_OK;
+}
+
 // Make room for the next factor: it may append one entry per stored entry
 // (and, in gradient runs, drop as many onto the tape).  Compacts when a
 // quarter of the stored entries are dropped ones.
@@ -420,7 +480,6 @@ ucc_status ensure_room(ucc_ctx* c, TableSet& s, bool record) {
 // later launches in the chunk then skip, and the host cuts / grows and
 // resumes at the flagged factor.  Chunks shrink when stops come often.
 ucc_status run_factors(ucc_ctx* c, TableSet& s, double eps, bool record, int k0, int k1) {
-  const int pw = pick_probe_width(c);
   const unsigned long long n_max = c->opt.n_max > 0 ? (unsigned long long)c->opt.n_max : 0ull;
   UCC_TRY(read_counters(c, s));
   unsigned long long n_known = s.h_cnt->n_tail;
@@ -434,6 +493,7 @@ ucc_status run_factors(ucc_ctx* c, TableSet& s, double eps, bool record, int k0,
     int grid = (int)std::min<unsigned long long>((unsigned long long)c->full_grid(), (est + 255) / 256);
     grid = std::max(grid, std::min(c->full_grid(), 4));
     if (k < 0 || end > c->K) return fail(UCC_ECUDA, "factor index out of range");
+    const int pw = pick_probe_width(c);
     CUDA_TRY(cudaEventRecord(c->kev[0], c->stream));
     for (int kk = k; kk < end; ++kk) {
       CUDA_TRY(launch_forward(c->table(s), c->d_factors, kk, eps, (unsigned int)(kk + 1), record ? 1 : 0, c->tape(),
@@ -477,6 +537,7 @@ ucc_status run_factors(ucc_ctx* c, TableSet& s, double eps, bool record, int k0,
       continue;
     }
     chunk = std::min(64, chunk * 2);
+    UCC_TRY(autotune(c, s, end, h.n_tail));
     // Compact when a quarter of the stored entries are dropped ones.
     if (h.n_dead > 4096 && h.n_dead * 4 > h.n_tail) UCC_TRY(rebuild(c, s, s.cur.cap_n));
     k = end;
@@ -492,14 +553,16 @@ void fill_forward_stats(ucc_ctx* c, const Counters& h) {
   c->stats.dropped_old = (long long)h.dropped_old;
   c->stats.cut = c->cut_total;
   c->stats.scanned = (long long)h.scanned;
+  c->stats.probe_width = pick_probe_width(c);
 }
 
-// Factors per gradient segment.  With cuts, most of what the forward pass
-// drops is cut, not pruned, so the segments are ~sqrt(K) long: snapshots at
-// their starts, one recomputation each, and a tape that covers one segment.
+// Factors per gradient segment.  One segment (the whole run on one tape) when
+// the tape fits its memory budget; otherwise ~sqrt(K)-long segments:
+// snapshots at their starts, one recomputation each, and a tape that covers
+// one segment.
 int segment_stride(const ucc_ctx* c) {
   if (c->opt.checkpoint_stride > 0) return std::min(c->opt.checkpoint_stride, std::max(1, c->K));
-  if (c->opt.n_max > 0) return std::max(1, (int)std::ceil(std::sqrt((double)std::max(1, c->K))));
+  if (c->force_segments) return std::max(1, (int)std::ceil(std::sqrt((double)std::max(1, c->K))));
   return std::max(1, c->K);
 }
 
@@ -507,10 +570,14 @@ ucc_status run_forward(ucc_ctx* c, double eps, bool record) {
   if (!(eps >= 0.0) || std::isinf(eps)) return fail(UCC_EINVAL, "eps must be finite and >= 0");
   TableSet& s = c->ts[c->main];
   c->cut_total = 0;
+  c->entropy_on = !record && c->opt.record_entropy != 0;
+  c->have_entropy = false;
   UCC_TRY(reset_table(c, s));
   CUDA_TRY(cudaEventRecord(c->ev[0], c->stream));
   if (!record) {
     UCC_TRY(run_factors(c, s, eps, false, 0, c->K));
+    c->have_entropy = c->entropy_on;
+    c->entropy_on = false;
   } else {
     const int S = segment_stride(c);
     const int nseg = c->K == 0 ? 0 : (c->K + S - 1) / S;
@@ -566,64 +633,95 @@ ucc_status run_energy(ucc_ctx* c, double* E, double* norm2) {
   return UCC_OK;
 }
 
-// Room to re-insert every tape record of the segment into table s.
-ucc_status room_for_reverse(ucc_ctx* c, TableSet& s) {
-  UCC_TRY(read_counters(c, s));
-  const Counters h = *s.h_cnt;
-  const unsigned long long live = h.n_tail - h.n_dead;
-  const unsigned long long need = h.n_tail + h.tape_n;
-  if (need > s.cur.cap_n || 4ull * need > 3ull * s.cur.n_slots) {
-    UCC_TRY(rebuild(c, s, std::max<unsigned long long>(s.cur.cap_n, 2 * (live + h.tape_n) + 64)));
-    UCC_TRY(read_counters(c, s));
-  }
-  return UCC_OK;
-}
-
 // The reverse sweep over factors [k0, k1) on table s, which holds psi_{k1}
-// and mu_{k1} (in lam), with the tape recorded for this segment.
+// and mu_{k1} (in lam), with the tape recorded for this segment.  Step k
+// appends at most its own tape records; the host keeps an upper bound of the
+// stored count and compacts (keeping lam) or grows before a step could pass
+// the table's room.
 ucc_status reverse_segment(ucc_ctx* c, TableSet& s, int k0, int k1) {
   if (k1 <= k0) return UCC_OK;
   std::vector<unsigned long long> off(k1 - k0 + 1);
   CUDA_TRY(cudaMemcpyAsync(off.data(), c->t_off + k0, off.size() * sizeof(unsigned long long),
                            cudaMemcpyDeviceToHost, c->stream));
-  CUDA_TRY(cudaStreamSynchronize(c->stream));
-  const int pw = pick_probe_width(c);
+  UCC_TRY(read_counters(c, s));
   const int grid_full = c->full_grid();
-  const unsigned long long n_now = s.h_cnt->n_tail;
-  int grid = (int)std::min<unsigned long long>((unsigned long long)grid_full, (n_now * 2 + 255) / 256);
+  unsigned long long bound = s.h_cnt->n_tail;
+  int grid = (int)std::min<unsigned long long>((unsigned long long)grid_full, (bound * 2 + 255) / 256);
   grid = std::max(grid, std::min(grid_full, 4));
   CUDA_TRY(cudaEventRecord(c->kev[0], c->stream));
+  float kernel_ms = 0.f;
   for (int k = k1 - 1; k >= k0; --k) {
     const unsigned int stamp = 0x80000000u | (unsigned int)k;
     const unsigned long long lo = off[k - k0], hi = off[k - k0 + 1];
     if (hi > c->tape_cap || lo > hi) return fail(UCC_ECUDA, "tape offsets out of range");
-    if (hi > lo) {
-      const int g2 = (int)std::min<unsigned long long>((unsigned long long)grid_full, (hi - lo + 255) / 256);
+    const unsigned long long rec = hi - lo;
+    if (bound + rec > s.cur.cap_n || 4ull * (bound + rec) > 3ull * s.cur.n_slots) {
+      CUDA_TRY(cudaEventRecord(c->kev[1], c->stream));
+      UCC_TRY(read_counters(c, s));
+      float ms = 0.f;
+      CUDA_TRY(cudaEventElapsedTime(&ms, c->kev[0], c->kev[1]));
+      kernel_ms += ms;
+      // Live entries now: stored minus those the sweep or the forward dropped.
+      UCC_TRY(rebuild(c, s, s.cur.cap_n, true));
+      UCC_TRY(read_counters(c, s));
+      bound = s.h_cnt->n_tail;
+      if (bound + rec > s.cur.cap_n || 4ull * (bound + rec) > 3ull * s.cur.n_slots) {
+        UCC_TRY(rebuild(c, s, std::max<unsigned long long>(2 * s.cur.cap_n, 2 * (bound + rec) + 64), true));
+        UCC_TRY(read_counters(c, s));
+        bound = s.h_cnt->n_tail;
+      }
+      grid = (int)std::min<unsigned long long>((unsigned long long)grid_full, (bound * 2 + 255) / 256);
+      grid = std::max(grid, std::min(grid_full, 4));
+      CUDA_TRY(cudaEventRecord(c->kev[0], c->stream));
+    }
+    if (rec) {
+      const int g2 = (int)std::min<unsigned long long>((unsigned long long)grid_full, (rec + 255) / 256);
       CUDA_TRY(launch_tape_reinsert(c->table(s), c->tape(), k, std::max(g2, 1), c->stream));
       c->launches++;
     }
-    CUDA_TRY(launch_reverse(c->table(s), c->d_factors, k, stamp, c->d_grad, pw, grid, c->stream));
+    CUDA_TRY(launch_reverse(c->table(s), c->d_factors, k, stamp, c->d_grad, pick_probe_width(c), grid, c->stream));
     c->launches++;
     c->stats.reverse_launches++;
+    bound += rec;
   }
   CUDA_TRY(cudaEventRecord(c->kev[1], c->stream));
   UCC_TRY(read_counters(c, s));
-  {
-    float kms = 0.f;
-    CUDA_TRY(cudaEventElapsedTime(&kms, c->kev[0], c->kev[1]));
-    c->stats.reverse_kernel_ms += kms;
-  }
+  float ms = 0.f;
+  CUDA_TRY(cudaEventElapsedTime(&ms, c->kev[0], c->kev[1]));
+  c->stats.reverse_kernel_ms += kernel_ms + ms;
   c->stats.reverse_pairs += (long long)s.h_cnt->rev_pairs;
   return UCC_OK;
 }
 
+ucc_status run_gradient_once(ucc_ctx* c, double eps, double* E, double* grad_out, int on_device);
+
+// dE/dtheta: first on one tape; if the tape would pass its budget, again with
+// segment checkpoints.
 ucc_status run_gradient(ucc_ctx* c, double eps, double* E, double* grad_out, int on_device) {
+  size_t free_b = 0, total_b = 0;
+  CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+  const unsigned long long held = (unsigned long long)c->tape_cap * sizeof(TapeRec);
+  c->tape_budget = c->opt.tape_budget_mb > 0 ? (unsigned long long)c->opt.tape_budget_mb << 20
+                                             : (unsigned long long)(0.6 * (double)(free_b + held));
+  c->force_segments = false;
+  c->tape_over_budget = false;
+  ucc_status s = run_gradient_once(c, eps, E, grad_out, on_device);
+  if (s == UCC_ECAPACITY && c->tape_over_budget && c->opt.checkpoint_stride <= 0) {
+    release_tape(c);
+    c->force_segments = true;
+    c->tape_over_budget = false;
+    c->tape_budget = 0;
+    s = run_gradient_once(c, eps, E, grad_out, on_device);
+  }
+  return s;
+}
+
+ucc_status run_gradient_once(ucc_ctx* c, double eps, double* E, double* grad_out, int on_device) {
   c->launches = 0;
   c->stats = ucc_stats{};
   c->main = 0;
   UCC_TRY(run_forward(c, eps, true));
   TableSet& s0 = c->ts[c->main];
-  UCC_TRY(room_for_reverse(c, s0));
   double e = 0.0, n2 = 0.0;
   UCC_TRY(run_energy(c, &e, &n2));
   if (E) *E = e;
@@ -649,7 +747,7 @@ ucc_status run_gradient(ucc_ctx* c, double eps, double* E, double* grad_out, int
       }
       UCC_TRY(reset_tape(c, work, k0));
       UCC_TRY(run_factors(c, work, eps, true, k0, k1));
-      UCC_TRY(room_for_reverse(c, work));
+      UCC_TRY(read_counters(c, work));
       c->stats.recompute_scanned += (long long)work.h_cnt->scanned;
       c->stats.recompute_rotations += (long long)work.h_cnt->rotations;
       c->stats.recompute_created += (long long)work.h_cnt->created;
@@ -746,9 +844,9 @@ void destroy(ucc_ctx* c) {
   dfree(c->d_grad);
   dfree(c->d_partials);
   dfree(c->d_sel);
-  dfree(c->t_key);
-  dfree(c->t_val);
-  dfree(c->t_born);
+  release_tape(c);
+  dfree(c->d_entropy);
+  dfree(c->d_pages);
   dfree(c->t_off);
   for (auto& e : c->ev)
     if (e) cudaEventDestroy(e);
@@ -772,6 +870,7 @@ ucc_status batch_together(const std::vector<int>& idx, ucc_ctx* const* jobs, dou
     c->launches = 0;
     c->stats = ucc_stats{};
     c->cut_total = 0;
+    c->tape_budget = 0;  // batched jobs run without the cut: their tapes stay small
     UCC_TRY(reset_table(c, c->ts[0]));
     if (record) UCC_TRY(reset_tape(c, c->ts[0], 0));
     maxK = std::max(maxK, c->K);
@@ -852,7 +951,17 @@ ucc_status batch_together(const std::vector<int>& idx, ucc_ctx* const* jobs, dou
     for (int x = 0; x < n; ++x) {
       ucc_ctx* c = jobs[idx[x]];
       UCC_TRY(read_counters(c, c->ts[0]));
-      if (record) UCC_TRY(room_for_reverse(c, c->ts[0]));
+      if (record) {
+        // The batched reverse re-inserts tapes without host checks: make room
+        // for the whole (small) tape now, before sigma and lambda exist.
+        const Counters h = *c->ts[0].h_cnt;
+        const unsigned long long need = h.n_tail + h.tape_n;
+        if (need > c->ts[0].cur.cap_n || 4ull * need > 3ull * c->ts[0].cur.n_slots) {
+          UCC_TRY(rebuild(c, c->ts[0], std::max<unsigned long long>(c->ts[0].cur.cap_n,
+                                                                    2 * (h.n_tail - h.n_dead + h.tape_n) + 64)));
+          UCC_TRY(read_counters(c, c->ts[0]));
+        }
+      }
       fill_forward_stats(c, *c->ts[0].h_cnt);
       c->stats.tape_entries = (long long)c->ts[0].h_cnt->tape_n;
     }
@@ -952,6 +1061,8 @@ ucc_status ucc_create(const ucc_hamiltonian* ham, const ucc_ansatz* an, void* cu
   if ((s = c->ts[1].init()) != UCC_OK) return bail(s);
   if ((s = dalloc(&c->d_sel, 1)) != UCC_OK) return bail(s);
   if ((s = dalloc(&c->t_off, (size_t)c->K + 1)) != UCC_OK) return bail(s);
+  if ((s = dalloc(&c->d_pages, kTapeMaxPages)) != UCC_OK) return bail(s);
+  if ((s = dalloc(&c->d_entropy, std::max(1, c->K))) != UCC_OK) return bail(s);
   if ((s = ensure_partials(c, c->full_grid())) != UCC_OK) return bail(s);
   for (auto& e : c->ev)
     if (cudaEventCreate(&e) != cudaSuccess) return bail(fail(UCC_ECUDA, "event creation failed"));
@@ -1060,6 +1171,17 @@ ucc_status ucc_get_wavefunction(ucc_ctx* c, size_t cap, size_t* n, uint64_t* key
   dfree(tsig);
   UCC_TRY(s);
   if (tab.h_cnt->new_n != live) return fail(UCC_ECUDA, "export count mismatch");
+  return UCC_OK;
+}
+
+ucc_status ucc_get_entropy(ucc_ctx* c, double* S, int32_t n) {
+  if (!c || (!S && n > 0)) return fail(UCC_EINVAL, "null argument");
+  if (n != c->K) return fail(UCC_EINVAL, "n must equal the number of factors");
+  if (!c->have_entropy) return fail(UCC_ESTATE, "no entropy recorded: set record_entropy and call ucc_apply");
+  if (n == 0) return UCC_OK;
+  CUDA_TRY(cudaSetDevice(c->device));
+  CUDA_TRY(cudaMemcpyAsync(S, c->d_entropy, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
   return UCC_OK;
 }
 

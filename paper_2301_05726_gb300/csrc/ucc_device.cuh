@@ -279,6 +279,10 @@ __device__ __forceinline__ bool last_block_arrive(Counters* c) {
   return last;
 }
 
+__device__ __forceinline__ TapeRec& tape_at(const Tape& tp, unsigned long long x) {
+  return tp.pages[x >> kTapePageBits][x & (kTapePageRecs - 1ull)];
+}
+
 // Loads that bypass L1 (values other blocks wrote in this kernel).
 __device__ __forceinline__ unsigned long long ld_cg(const unsigned long long* p) { return __ldcg(p); }
 __device__ __forceinline__ double ld_cg(const double* p) { return __ldcg(p); }

@@ -15,13 +15,14 @@ namespace ucc {
 //                   occupied modes below their index; the counts differ from
 //                   popc(E & below(x)) only by index comparisons, folded into
 //                   pconst);
-//   c, s : cos(theta_k), sin(theta_k) from the host's libm.
+//   c, s : cos(theta_k), sin(theta_k) from the host's libm;
+//   ic   : 1/cos(theta_k), used by the reverse sweep to undo a lone member.
 struct Factor {
   unsigned long long occ, vir, pmask;
-  double c, s;
+  double c, s, ic;
   int pconst, is_double;
 };
-static_assert(sizeof(Factor) == 48, "Factor layout");
+static_assert(sizeof(Factor) == 56, "Factor layout");
 
 // Open-addressing hash slot: key 0 = empty (no valid determinant has zero
 // electrons); idx = position of the entry in the compacted arrays.
@@ -45,6 +46,7 @@ struct Counters {
   int error;                  // device error word (bit flags below)
   int cut_pending;            // more than n_max live entries after factor stop_k - 1
   double e_num, norm2;        // <psi|H|psi>, <psi|psi> of the last energy pass
+  double entropy;             // running Eq. 6 entropy of the stored state (when recorded)
 };
 
 enum DeviceError : int {
@@ -69,14 +71,28 @@ struct Table {
   unsigned long long cap_n;
   Counters* cnt;
   double* partials;          // [grid] per-block partial sums
+  double* entropy;           // [K] Eq. 6 after each factor (nullptr: not recorded)
 };
 
+// Kill-tape record: a stored entry that fell below eps or was cut, with its
+// value just before the drop and the factor that created it.
+struct TapeRec {
+  unsigned long long key;
+  double val;
+  unsigned int born;
+  unsigned int pad;
+};
+
+// The tape is paged so it can grow to tens of GB without copying: record x
+// lives in pages[x >> kTapePageBits][x & (kTapePageRecs - 1)].
+constexpr int kTapePageBits = 20;
+constexpr unsigned long long kTapePageRecs = 1ull << kTapePageBits;  // 1M records, 24 MB
+constexpr int kTapeMaxPages = 65536;                                 // up to 1.6 TB
+
 struct Tape {
-  unsigned long long* key;
-  double* val;
-  unsigned int* born;
-  unsigned long long* off;  // [K + 1] tape_n at the start of factor k
-  unsigned long long cap;
+  TapeRec* const* pages;     // [kTapeMaxPages] device array of page pointers
+  unsigned long long* off;   // [K + 1] tape_n at the start of factor k
+  unsigned long long cap;    // records in the allocated pages
 };
 
 // Spatial integrals for the energy kernel.
@@ -148,6 +164,8 @@ cudaError_t launch_reverse(const Table& t, const Factor* factors, int k, unsigne
 cudaError_t launch_restore(const Table& t, const unsigned long long* keys, const double* amps, unsigned long long n,
                            int grid, cudaStream_t st);
 cudaError_t launch_transfer_lambda(const Table& dst, const Table& src, int grid, cudaStream_t st);
+cudaError_t launch_probe_bench(const Table& t, const Factor& f, int probe_width, unsigned long long* sink, int grid,
+                               cudaStream_t st);
 int sigma_smem_bytes(int n_so);
 // Batched (many-job) launches; mode 0 lays out the forward index space
 // (n_scan of jobs still applying factors), 1 the energy space (n_tail of every

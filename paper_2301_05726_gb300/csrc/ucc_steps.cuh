@@ -6,18 +6,33 @@
 
 namespace ucc {
 
+// |v| < eps for finite v and eps >= 0, decided on the IEEE bit patterns
+// (non-negative doubles order like their bits), off the scarce FP64 pipe.
+__device__ __forceinline__ bool below_eps(double v, double eps) {
+  return ((unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull) <
+         (unsigned long long)__double_as_longlong(eps);
+}
+
 struct StepCounts {
   unsigned long long rot = 0, cre = 0, dnew = 0, dold = 0;
   long long dead_delta = 0;
+  double dS = 0.0;  // change of the Eq. 6 entropy (when recorded)
 };
+
+// The Eq. 6 summand -|c|^2 ln|c|^2 (zero at c = 0).
+__device__ __forceinline__ double entropy_term(double c) {
+  const double p = c * c;
+  return p > 0.0 ? -p * log(p) : 0.0;
+}
 
 __device__ __forceinline__ void record_kill(const Table& t, const Tape& tape, unsigned long long key, double val,
                                             unsigned int born) {
   unsigned long long ti = aggregated_add(&t.cnt->tape_n);
   if (ti < tape.cap) {
-    tape.key[ti] = key;
-    tape.val[ti] = val;
-    tape.born[ti] = born;
+    TapeRec& rec = tape_at(tape, ti);
+    rec.key = key;
+    rec.val = val;
+    rec.born = born;
   } else {
     raise_error(t.cnt, ERR_TAPE_FULL);
   }
@@ -49,13 +64,34 @@ __device__ __forceinline__ void forward_resolve(const Table& t, const Factor& f,
   const double cE = ex ? cX : 0.0;
   const double cD = ex ? (partner_live ? r.amp : 0.0) : cX;
   // c_E' = cos c_E - s sin c_D ;  c_D' = cos c_D + s sin c_E  (no contraction)
-  const double nE = __dsub_rn(__dmul_rn(f.c, cE), __dmul_rn(ss, cD));
-  const double nD = __dadd_rn(__dmul_rn(f.c, cD), __dmul_rn(ss, cE));
+  double nE, nD;
+  if (!partner_live) {
+    // One member is +0.0: its two products are zeros, and adding or
+    // subtracting a zero leaves a nonzero product unchanged, so two products
+    // give the same bits as the full formula whenever both are nonzero.
+    const double pa = __dmul_rn(f.c, cX), pb = __dmul_rn(ss, cX);
+    if (pa != 0.0 && pb != 0.0) {
+      nE = ex ? pa : -pb;
+      nD = ex ? pb : pa;
+    } else {
+      nE = __dsub_rn(__dmul_rn(f.c, cE), __dmul_rn(ss, cD));
+      nD = __dadd_rn(__dmul_rn(f.c, cD), __dmul_rn(ss, cE));
+    }
+  } else {
+    nE = __dsub_rn(__dmul_rn(f.c, cE), __dmul_rn(ss, cD));
+    nD = __dadd_rn(__dmul_rn(f.c, cD), __dmul_rn(ss, cE));
+  }
   const double nX = ex ? nE : nD;
   const double nY = ex ? nD : nE;
   ++sc.rot;
+  if (t.entropy) {
+    // Eq. 6 changes only on the pair: new terms (zero if dropped) minus old.
+    const double kX = below_eps(nX, eps) ? 0.0 : nX;
+    const double kY = below_eps(nY, eps) ? 0.0 : nY;
+    sc.dS += entropy_term(kX) + entropy_term(kY) - entropy_term(cX) - (partner_live ? entropy_term(r.amp) : 0.0);
+  }
   // The thread's own entry.
-  if (fabs(nX) < eps) {
+  if (below_eps(nX, eps)) {
     if (RECORD) record_kill(t, tape, X, nX, t.born[i]);
     t.amps[i] = dead_value(stamp);
     ++sc.dold;
@@ -65,7 +101,7 @@ __device__ __forceinline__ void forward_resolve(const Table& t, const Factor& f,
   }
   // The partner.
   if (partner_live) {
-    if (fabs(nY) < eps) {
+    if (below_eps(nY, eps)) {
       if (RECORD) record_kill(t, tape, Y, nY, t.born[r.idx]);
       t.amps[r.idx] = dead_value(stamp);
       ++sc.dold;
@@ -73,7 +109,7 @@ __device__ __forceinline__ void forward_resolve(const Table& t, const Factor& f,
     } else {
       t.amps[r.idx] = nY;
     }
-  } else if (fabs(nY) < eps) {
+  } else if (below_eps(nY, eps)) {
     ++sc.dnew;
   } else if (r.state == DEAD_OLD) {
     // Revive a dropped key as a fresh entry past the scan range and point
@@ -120,87 +156,18 @@ __device__ __forceinline__ void forward_entry(const Table& t, const Factor& f, i
   forward_resolve<RECORD>(t, f, k, eps, stamp, tape, i, X, cX, ex, r, sc);
 }
 
-// U entries per lane (i0, i0 + 32, ..., i0 + 32(U-1)), single-lane probes:
-// all key loads, then all amplitude loads, filter tests and first-slot loads
-// are issued before any result is used, so a lane keeps up to 3U independent
-// loads in flight instead of one dependent chain.
-template <int U, bool RECORD>
-__device__ __forceinline__ void forward_entries(const Table& t, const Factor& f, int k, double eps,
-                                                unsigned int stamp, const Tape& tape, unsigned long long i0,
-                                                unsigned long long n, StepCounts& sc) {
-  unsigned long long X[U];
-  double cX[U];
-  bool act[U], ex[U];
-#pragma unroll
-  for (int u = 0; u < U; ++u) {
-    const unsigned long long i = i0 + 32ull * u;
-    act[u] = i < n;
-    X[u] = act[u] ? t.keys[i] : 0ull;
-  }
-#pragma unroll
-  for (int u = 0; u < U; ++u) {
-    ex[u] = ((X[u] & f.occ) == f.occ) && ((X[u] & f.vir) == 0ull);
-    const bool de = ((X[u] & f.vir) == f.vir) && ((X[u] & f.occ) == 0ull);
-    act[u] = act[u] && (ex[u] || de);
-    cX[u] = act[u] ? t.amps[i0 + 32ull * u] : 0.0;
-  }
-  const unsigned long long m = f.occ | f.vir;
-  bool maybe[U];
-  Slot s0[U];
-#pragma unroll
-  for (int u = 0; u < U; ++u) {
-    act[u] = act[u] && !is_dead(cX[u]);
-    maybe[u] = act[u] && filter_maybe(t, X[u] ^ m);
-    s0[u].key = 1ull;
-    s0[u].idx = 0;
-    if (maybe[u]) s0[u] = t.slots[home_slot(t, X[u] ^ m)];
-  }
-#pragma unroll
-  for (int u = 0; u < U; ++u) {
-    if (!act[u]) continue;
-    const unsigned long long Y = X[u] ^ m;
-    Lookup r;
-    r.state = ABSENT;
-    r.idx = 0;
-    r.amp = 0.0;
-    r.slot = home_slot(t, Y);
-    if (maybe[u]) {
-      if (s0[u].key == Y) {
-        classify(t, s0[u].idx, stamp, r);
-      } else if (s0[u].key != 0ull) {
-        r = find1(t, Y, stamp);  // collision: continue the probe from home
-      }
-    }
-    forward_resolve<RECORD>(t, f, k, eps, stamp, tape, i0 + 32ull * u, X[u], cX[u], ex[u], r, sc);
-  }
-}
-
 // One stored entry i of the reverse step for factor k: psi_k -> psi_{k-1} in
 // place (inverse rotation on a stored pair, cos(theta) divided out of a lone
 // member), lambda_{k-1} = U_k^T mu_k, and this pair's share of
 // dE/dtheta_k / 2 = sum_pairs s (lam_D psi_E - lam_E psi_D) added to acc.
 // Entries created by factor k (born == k) leave the table.  Every lane of the
 // warp calls this.
-template <int G>
-__device__ __forceinline__ void reverse_entry(const Table& t, const Factor& f, int k, unsigned int stamp,
-                                              unsigned long long i, bool in_range, double& acc, unsigned int& pairs) {
-  bool act = in_range;
-  unsigned long long X = 0;
-  double cX = 0.0;
-  bool ex = false;
-  if (act) {
-    X = t.keys[i];
-    ex = ((X & f.occ) == f.occ) && ((X & f.vir) == 0ull);
-    const bool de = ((X & f.vir) == f.vir) && ((X & f.occ) == 0ull);
-    act = ex || de;
-    if (act) {
-      cX = t.amps[i];
-      act = !is_dead(cX);
-    }
-  }
+// The reverse step for one linked entry i (key X, live amplitude cX, ex = X
+// is the excited member) whose partner lookup is r.
+__device__ __forceinline__ void reverse_resolve(const Table& t, const Factor& f, int k, unsigned int stamp,
+                                                unsigned long long i, unsigned long long X, double cX, bool ex,
+                                                const Lookup& r, double& acc, unsigned int& pairs) {
   const unsigned long long Y = X ^ (f.occ | f.vir);
-  Lookup r = findG<G>(t, Y, act, stamp);
-  if (!act) return;
   const bool partner_live = (r.state == ALIVE);
   if (!ex && (partner_live || r.state == DEAD_NOW)) return;  // E's thread owns the pair
   const unsigned long long E = ex ? X : Y;
@@ -232,7 +199,7 @@ __device__ __forceinline__ void reverse_entry(const Table& t, const Factor& f, i
     }
   } else if (ex) {
     // E alone: D was absent before the factor, c_E' = cos c_E.
-    const double e0 = __ddiv_rn(cX, f.c);
+    const double e0 = __dmul_rn(cX, f.ic);
     const double lE = __dmul_rn(f.c, muX);
     const double lD = -__dmul_rn(ss, muX);
     acc += sg * (lD * e0);
@@ -240,13 +207,36 @@ __device__ __forceinline__ void reverse_entry(const Table& t, const Factor& f, i
     t.lam[i] = lE;
   } else {
     // D alone: E was absent before the factor, c_D' = cos c_D.
-    const double d0 = __ddiv_rn(cX, f.c);
+    const double d0 = __dmul_rn(cX, f.ic);
     const double lD = __dmul_rn(f.c, muX);
     const double lE = __dmul_rn(ss, muX);
     acc += sg * (-lE * d0);
     t.amps[i] = d0;
     t.lam[i] = lD;
   }
+}
+
+template <int G>
+__device__ __forceinline__ void reverse_entry(const Table& t, const Factor& f, int k, unsigned int stamp,
+                                              unsigned long long i, bool in_range, double& acc, unsigned int& pairs) {
+  bool act = in_range;
+  unsigned long long X = 0;
+  double cX = 0.0;
+  bool ex = false;
+  if (act) {
+    X = t.keys[i];
+    ex = ((X & f.occ) == f.occ) && ((X & f.vir) == 0ull);
+    const bool de = ((X & f.vir) == f.vir) && ((X & f.occ) == 0ull);
+    act = ex || de;
+    if (act) {
+      cX = t.amps[i];
+      act = !is_dead(cX);
+    }
+  }
+  const unsigned long long Y = X ^ (f.occ | f.vir);
+  Lookup r = findG<G>(t, Y, act, stamp);
+  if (!act) return;
+  reverse_resolve(t, f, k, stamp, i, X, cX, ex, r, acc, pairs);
 }
 
 constexpr int kMaxSpin = 32;                          // spin-orbitals of one spin
@@ -310,6 +300,68 @@ __device__ __forceinline__ bool lookup_live(const Table& t, unsigned long long k
   return false;
 }
 
+// The slot probe of lookup_live, for a key the filter did not exclude.
+__device__ __forceinline__ bool probe_live(const Table& t, unsigned long long key, double* amp) {
+  unsigned long long h = home_slot(t, key);
+  for (int step = 0; step < MAX_PROBE; ++step) {
+    const Slot s = t.slots[h];
+    if (s.key == key) {
+      const double a = t.amps[s.idx];
+      if (is_dead(a)) return false;
+      *amp = a;
+      return true;
+    }
+    if (s.key == 0ull) return false;
+    h = (h + 1) & t.slot_mask;
+  }
+  raise_error(t.cnt, ERR_PROBE_BOUND);
+  return false;
+}
+
+// Lanes walk connections u = lane, lane + 32, ... < count, kV at a time: the
+// kV connection keys and their filter words are all requested before any is
+// tested, so each lane keeps kV independent loads in flight.  key_of(u) gives
+// the connected determinant, elem(u) its matrix element; hits add elem * c_J.
+constexpr int kV = 4;
+
+template <class KeyOf, class Elem>
+__device__ __forceinline__ void probe_connections(const Table& t, int count, int lane, KeyOf key_of, Elem elem,
+                                                  double& part, unsigned long long& probes,
+                                                  unsigned long long& hits) {
+  for (int u0 = lane; u0 < count; u0 += 32 * kV) {
+    unsigned long long J[kV];
+    unsigned int w[kV];
+#pragma unroll
+    for (int v = 0; v < kV; ++v) {
+      const int u = u0 + 32 * v;
+      J[v] = u < count ? key_of(u) : 0ull;
+    }
+#pragma unroll
+    for (int v = 0; v < kV; ++v) {
+      const int u = u0 + 32 * v;
+      w[v] = 0u;
+      if (u < count) {
+        if (t.filt) {
+          const unsigned long long b = (J[v] * kFilterMul) >> t.filt_shift;
+          w[v] = (t.filt[b >> 5] >> (b & 31u)) & 1u;
+        } else {
+          w[v] = 1u;
+        }
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < kV; ++v) {
+      const int u = u0 + 32 * v;
+      if (u >= count) continue;
+      ++probes;
+      double cJ;
+      if (!w[v] || !probe_live(t, J[v], &cJ)) continue;
+      ++hits;
+      part += elem(u, J[v]) * cJ;
+    }
+  }
+}
+
 // The lane's share of sigma_I = sum_{J in S} <I|H|J> c_J for one stored
 // determinant I (the warp's lanes split I's connections; sum with warp_sum).
 // L is this warp's shared-memory scratch.  Every lane of the warp calls this.
@@ -363,22 +415,20 @@ __device__ __forceinline__ double sigma_entry(const Table& t, const Integrals& i
   // Singles p -> r, same spin.
   for (int sp = 0; sp < 2; ++sp) {
     const int no = L.n_occ[sp], ne = L.n_emp[sp];
-    for (int u = lane; u < no * ne; u += 32) {
-      const int p = L.occ[sp][u / ne];
-      const int r = L.emp[sp][u % ne];
-      const unsigned long long J = I ^ ((1ull << p) | (1ull << r));
-      double cJ;
-      ++probes;
-      if (!lookup_live(t, J, &cJ)) continue;
-      ++hits;
-      double v = h_so(in, r, p);
-      for (int sk = 0; sk < 2; ++sk)
-        for (int y = 0; y < L.n_occ[sk]; ++y) {
-          const int kk = L.occ[sk][y];
-          if (kk != p) v += anti(in, r, kk, p, kk);
-        }
-      part += (single_parity(I, p, r) ? -v : v) * cJ;
-    }
+    probe_connections(
+        t, no * ne, lane,
+        [&](int u) { return I ^ ((1ull << L.occ[sp][u / ne]) | (1ull << L.emp[sp][u % ne])); },
+        [&](int u, unsigned long long) {
+          const int p = L.occ[sp][u / ne], r = L.emp[sp][u % ne];
+          double v = h_so(in, r, p);
+          for (int sk = 0; sk < 2; ++sk)
+            for (int y = 0; y < L.n_occ[sk]; ++y) {
+              const int kk = L.occ[sk][y];
+              if (kk != p) v += anti(in, r, kk, p, kk);
+            }
+          return single_parity(I, p, r) ? -v : v;
+        },
+        part, probes, hits);
   }
   // Doubles: same-spin (p < q from one spin, r < s from the same spin).
   for (int sp = 0; sp < 2; ++sp) {
@@ -388,17 +438,19 @@ __device__ __forceinline__ double sigma_entry(const Table& t, const Integrals& i
       for (int y = x + 1; y < no; ++y) {
         const int p = L.occ[sp][x], q = L.occ[sp][y];
         const unsigned long long hole = (1ull << p) | (1ull << q);
-        for (int u = lane; u < np; u += 32) {
-          const unsigned short pr = L.pairs[sp][u];
-          const int r = pr & 0xFF, s = pr >> 8;
-          const unsigned long long J = I ^ (hole | (1ull << r) | (1ull << s));
-          double cJ;
-          ++probes;
-          if (!lookup_live(t, J, &cJ)) continue;
-          ++hits;
-          const double v = anti(in, r, s, p, q);
-          part += (double_parity(I, p, q, r, s) ? -v : v) * cJ;
-        }
+        probe_connections(
+            t, np, lane,
+            [&](int u) {
+              const unsigned short pr = L.pairs[sp][u];
+              return I ^ (hole | (1ull << (pr & 0xFF)) | (1ull << (pr >> 8)));
+            },
+            [&](int u, unsigned long long) {
+              const unsigned short pr = L.pairs[sp][u];
+              const int r = pr & 0xFF, s = pr >> 8;
+              const double v = anti(in, r, s, p, q);
+              return double_parity(I, p, q, r, s) ? -v : v;
+            },
+            part, probes, hits);
       }
   }
   // Doubles: opposite spin (p alpha, q beta -> r alpha, s beta).
@@ -409,16 +461,15 @@ __device__ __forceinline__ double sigma_entry(const Table& t, const Integrals& i
       for (int y = 0; y < nob; ++y) {
         const int p = L.occ[0][x], q = L.occ[1][y];
         const unsigned long long hole = (1ull << p) | (1ull << q);
-        for (int u = lane; u < nE; u += 32) {
-          const int r = L.emp[0][u / neb], s = L.emp[1][u % neb];
-          const unsigned long long J = I ^ (hole | (1ull << r) | (1ull << s));
-          double cJ;
-          ++probes;
-          if (!lookup_live(t, J, &cJ)) continue;
-          ++hits;
-          const double v = anti(in, r, s, p, q);
-          part += (double_parity(I, p, q, r, s) ? -v : v) * cJ;
-        }
+        probe_connections(
+            t, nE, lane,
+            [&](int u) { return I ^ (hole | (1ull << L.emp[0][u / neb]) | (1ull << L.emp[1][u % neb])); },
+            [&](int u, unsigned long long) {
+              const int r = L.emp[0][u / neb], s = L.emp[1][u % neb];
+              const double v = anti(in, r, s, p, q);
+              return double_parity(I, p, q, r, s) ? -v : v;
+            },
+            part, probes, hits);
       }
   }
   return part;

@@ -85,6 +85,7 @@ def test_state_bit_exact(torch_cuda, case):
     assert st["dropped_new"] == oc["dropped_new"]
     assert st["dropped_old"] == oc["dropped_old"]
     assert st["n_det"] == len(ok)
+    assert st["probe_width"] in (1, 2, 4, 8)  # autotuned once the table passes 2^16 entries
 
 
 @pytest.mark.parametrize("pw", [1, 2, 4, 8])
@@ -301,3 +302,44 @@ def test_gradient_segment_checkpoints(torch_cuda, case, stride):
     E, g = ctx.gradient()
     assert abs(E - E_ref) <= E_TOL
     assert np.max(np.abs(g - g_ref)) <= G_TOL
+
+
+def test_gradient_tape_budget_falls_back_to_segments(torch_cuda):
+    # A 1 MiB tape budget cannot hold even one 24 MB tape page: the gradient
+    # falls back to segment checkpoints (with recomputation) and still matches
+    # the oracle's adjoint.
+    prob = small_pruned()
+    E_ref, g_ref = oracle_for(prob).gradient(n_max=3000, n_cut=1875)
+    ctx = ctx_for(prob)
+    ctx.set_options(n_max=3000, n_cut=1875, tape_budget_mb=1)
+    E, g = ctx.gradient()
+    assert abs(E - E_ref) <= E_TOL
+    assert np.max(np.abs(g - g_ref)) <= G_TOL
+    assert ctx.stats()["recompute_rotations"] > 0
+    # With room for the tape, one segment and no recomputation.
+    ctx.set_options(n_max=3000, n_cut=1875, tape_budget_mb=0)
+    E2, g2 = ctx.gradient()
+    assert ctx.stats()["recompute_rotations"] == 0
+    assert np.max(np.abs(g2 - g_ref)) <= G_TOL
+
+
+@pytest.mark.parametrize("case", ["cfg2", "cfg3_prefix150", "pruned_cut"])
+def test_entropy_per_factor(torch_cuda, case):
+    # Eq. 6 after every factor, accumulated on the device from the changes of
+    # the touched pairs (and the cut), vs the oracle's direct sum.
+    if case == "cfg2":
+        prob = synth.config_problem(2)
+        cut = {}
+    elif case == "cfg3_prefix150":
+        prob = synth.config_problem(3).prefix(150)
+        cut = {}
+    else:
+        prob = small_pruned()
+        cut = dict(n_max=3000, n_cut=1875)
+    S_ref = oracle_for(prob).entropy_per_factor(**cut)
+    ctx = ctx_for(prob)
+    ctx.set_options(record_entropy=True, **cut)
+    ctx.apply()
+    S = ctx.entropy()
+    assert np.max(np.abs(S - S_ref)) <= 1e-10
+    assert S_ref[-1] > 0.0

@@ -340,3 +340,22 @@ def test_gradient_at_theta_zero(cfg1):
         nonzero += s != 0
     assert nonzero > 10
     assert E == pytest.approx(hf_energy_spatial(cfg1), abs=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# Eq. 6 entropy after each factor
+# ---------------------------------------------------------------------------
+def test_entropy_per_factor_vs_dense_and_closed_form(cfg1):
+    o, d = Oracle(cfg1), Dense(cfg1)
+    S = o.entropy_per_factor()
+    assert S.shape == (cfg1.n_exc,)
+    for nf in (1, 10, 50, 92):
+        v = d.state(n_factors=nf)
+        p = v * v
+        p = p[p > 0]
+        assert S[nf - 1] == pytest.approx(float(-(p * np.log(p)).sum()), abs=1e-12)
+    # one factor on the reference: S = -cos^2 ln cos^2 - sin^2 ln sin^2
+    t = cfg1.theta[0]
+    c2, s2 = math.cos(t) ** 2, math.sin(t) ** 2
+    assert S[0] == pytest.approx(-c2 * math.log(c2) - s2 * math.log(s2), abs=1e-14)
+    assert np.all(o.entropy_per_factor(np.zeros(cfg1.n_exc)) == 0.0)
