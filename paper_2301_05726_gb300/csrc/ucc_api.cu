@@ -856,8 +856,8 @@ void destroy(ucc_ctx* c) {
 }
 
 // The batched path: every job advances one factor per launch.
-ucc_status batch_together(const std::vector<int>& idx, ucc_ctx* const* jobs, double eps, double* E,
-                          double* const* grads) {
+ucc_status batch_on_stream(const std::vector<int>& idx, ucc_ctx* const* jobs, double eps, double* E,
+                           double* const* grads) {
   const int n = (int)idx.size();
   ucc_ctx* c0 = jobs[idx[0]];
   cudaStream_t st = c0->stream;
@@ -883,7 +883,10 @@ ucc_status batch_together(const std::vector<int>& idx, ucc_ctx* const* jobs, dou
   UCC_TRY(dalloc(&d_bh, 1));
   std::vector<JobView> hv(n);
   std::vector<JobState> hs(n);
+  cudaGraphExec_t g_fwd = nullptr, g_rev = nullptr;
   auto release = [&]() {
+    if (g_fwd) cudaGraphExecDestroy(g_fwd);
+    if (g_rev) cudaGraphExecDestroy(g_rev);
     dfree(d_jobs);
     dfree(d_js);
     dfree(d_bh);
@@ -924,10 +927,34 @@ ucc_status batch_together(const std::vector<int>& idx, ucc_ctx* const* jobs, dou
     UCC_TRY(upload());
     CUDA_TRY(cudaMemsetAsync(d_bh, 0, sizeof(BatchHeader), st));
     CUDA_TRY(launch_batch_layout(d_jobs, d_js, n, d_bh, 0, st));
+    // A chunk of steps reads all of its state from device memory, so one
+    // captured graph of it serves every chunk (forward: 32 steps; reverse:
+    // 32 steps of 4 launches; steps past a job's end are no-ops).
+    if (maxK >= 64) {
+      cudaGraph_t g = nullptr;
+      CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+      for (int s = 0; s < 32; ++s) launch_forward_batch(d_jobs, d_js, n, d_bh, record ? 1 : 0, grid, st);
+      CUDA_TRY(cudaStreamEndCapture(st, &g));
+      cudaError_t e = cudaGraphInstantiate(&g_fwd, g, 0);
+      cudaGraphDestroy(g);
+      CUDA_TRY(e);
+      if (record) {
+        CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        for (int s = 0; s < 32; ++s) launch_reverse_batch(d_jobs, d_js, n, d_bh, grid, st);
+        CUDA_TRY(cudaStreamEndCapture(st, &g));
+        e = cudaGraphInstantiate(&g_rev, g, 0);
+        cudaGraphDestroy(g);
+        CUDA_TRY(e);
+      }
+    }
     // Forward: chunks of launches, then host action for jobs that need room.
     CUDA_TRY(cudaEventRecord(c0->ev[0], st));
     for (;;) {
-      for (int s = 0; s < 32; ++s) CUDA_TRY(launch_forward_batch(d_jobs, d_js, n, d_bh, record ? 1 : 0, grid, st));
+      if (g_fwd) {
+        CUDA_TRY(cudaGraphLaunch(g_fwd, st));
+      } else {
+        for (int s = 0; s < 32; ++s) CUDA_TRY(launch_forward_batch(d_jobs, d_js, n, d_bh, record ? 1 : 0, grid, st));
+      }
       for (int x = 0; x < n; ++x) jobs[idx[x]]->launches += 32;
       UCC_TRY(fetch());
       bool done = true, changed = false;
@@ -985,7 +1012,11 @@ ucc_status batch_together(const std::vector<int>& idx, ucc_ctx* const* jobs, dou
       for (int x = 0; x < n; ++x) hs[x].k = jobs[idx[x]]->K - 1;
       CUDA_TRY(cudaMemcpyAsync(d_js, hs.data(), n * sizeof(JobState), cudaMemcpyHostToDevice, st));
       CUDA_TRY(cudaEventRecord(c0->ev[4], st));
-      for (int s = 0; s < maxK; ++s) CUDA_TRY(launch_reverse_batch(d_jobs, d_js, n, d_bh, grid, st));
+      if (g_rev) {
+        for (int s = 0; s < maxK; s += 32) CUDA_TRY(cudaGraphLaunch(g_rev, st));
+      } else {
+        for (int s = 0; s < maxK; ++s) CUDA_TRY(launch_reverse_batch(d_jobs, d_js, n, d_bh, grid, st));
+      }
       CUDA_TRY(cudaEventRecord(c0->ev[5], st));
       UCC_TRY(fetch());
       for (int x = 0; x < n; ++x) {
@@ -1018,6 +1049,33 @@ ucc_status batch_together(const std::vector<int>& idx, ucc_ctx* const* jobs, dou
   };
   ucc_status s = run();
   release();
+  return s;
+}
+
+// The batch runs on a private stream (graph capture needs one that is not
+// the legacy default stream), ordered after and before the caller's stream.
+ucc_status batch_together(const std::vector<int>& idx, ucc_ctx* const* jobs, double eps, double* E,
+                          double* const* grads) {
+  cudaStream_t caller = jobs[idx[0]]->stream;
+  cudaStream_t bs = nullptr;
+  cudaEvent_t e_in = nullptr, e_out = nullptr;
+  CUDA_TRY(cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking));
+  if (cudaEventCreateWithFlags(&e_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&e_out, cudaEventDisableTiming) != cudaSuccess) {
+    cudaStreamDestroy(bs);
+    return fail(UCC_ECUDA, "event creation failed");
+  }
+  cudaEventRecord(e_in, caller);
+  cudaStreamWaitEvent(bs, e_in, 0);
+  for (int j : idx) jobs[j]->stream = bs;
+  ucc_status s = batch_on_stream(idx, jobs, eps, E, grads);
+  for (int j : idx) jobs[j]->stream = caller;
+  cudaEventRecord(e_out, bs);
+  cudaStreamWaitEvent(caller, e_out, 0);
+  cudaStreamSynchronize(bs);
+  cudaEventDestroy(e_in);
+  cudaEventDestroy(e_out);
+  cudaStreamDestroy(bs);
   return s;
 }
 
