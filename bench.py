@@ -270,7 +270,9 @@ def run_ours(args, prob):
     hbm, peak_kind = peaks()
     fwd_bytes = 8.0 * (tot["scanned"] + tot["recompute_scanned"]) + \
         48.0 * (tot["rotations"] + tot["recompute_rotations"]) + 32.0 * (tot["created"] + tot["recompute_created"])
-    sig_bytes = 24.0 * tot["n_det"] + 16.0 * tot["sigma_probes"] + 8.0 * tot["sigma_hits"]
+    # per stored determinant: key + amplitude read, sigma written; per connected stored pair (visited once):
+    # the partner amplitude read and one sigma update
+    sig_bytes = 24.0 * tot["n_det"] + 16.0 * tot["sigma_hits"]
     rev_bytes = 80.0 * tot["reverse_pairs"]
     kernels = {
         "k_forward": _roofline("k_forward", fwd_bytes, tot["forward_kernel_ms"], tot["forward_launches"], hbm,

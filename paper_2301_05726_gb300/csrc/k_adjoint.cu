@@ -50,15 +50,16 @@ __global__ void __launch_bounds__(kThreads) k_tape_reinsert(Table t, Tape tape, 
 template <int G>
 __global__ void __launch_bounds__(kThreads) k_reverse(Table t, const Factor* __restrict__ factors, int k,
                                                        unsigned int stamp, double* grad) {
+  __shared__ LinkQueue s_q[kThreads / 32];
   const Factor f = factors[k];
   const unsigned long long n = min(*((volatile unsigned long long*)&t.cnt->n_tail), t.cap_n);
-  const unsigned int lane = threadIdx.x & 31u;
-  const unsigned long long warp = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const unsigned long long nwarps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
   double acc = 0.0;
   unsigned int pairs = 0;
-  for (unsigned long long base = warp * 32ull; base < n; base += nwarps * 32ull)
-    reverse_entry<G>(t, f, k, stamp, base + lane, base + lane < n, acc, pairs);
+  for_each_linked(t, f, n, s_q[threadIdx.x >> 5],
+                  [&](unsigned long long i, unsigned long long X, double cX, bool ex, bool act) {
+                    Lookup r = findG<G>(t, X ^ (f.occ | f.vir), act, stamp);
+                    if (act) reverse_resolve(t, f, k, stamp, i, X, cX, ex, r, acc, pairs);
+                  });
   {
     __shared__ unsigned long long s_pairs;
     if (threadIdx.x == 0) s_pairs = 0;
@@ -91,16 +92,16 @@ cudaError_t launch_reverse(const Table& t, const Factor* factors, int k, unsigne
                            int probe_width, int grid, cudaStream_t st) {
   switch (probe_width) {
     case 2:
-      k_reverse<2><<<grid, kThreads, 0, st>>>(t, factors, k, stamp, grad);
+      k_reverse<2><<<one_wave<k_reverse<2>, kThreads>(grid), kThreads, 0, st>>>(t, factors, k, stamp, grad);
       break;
     case 4:
-      k_reverse<4><<<grid, kThreads, 0, st>>>(t, factors, k, stamp, grad);
+      k_reverse<4><<<one_wave<k_reverse<4>, kThreads>(grid), kThreads, 0, st>>>(t, factors, k, stamp, grad);
       break;
     case 8:
-      k_reverse<8><<<grid, kThreads, 0, st>>>(t, factors, k, stamp, grad);
+      k_reverse<8><<<one_wave<k_reverse<8>, kThreads>(grid), kThreads, 0, st>>>(t, factors, k, stamp, grad);
       break;
     default:
-      k_reverse<1><<<grid, kThreads, 0, st>>>(t, factors, k, stamp, grad);
+      k_reverse<1><<<one_wave<k_reverse<1>, kThreads>(grid), kThreads, 0, st>>>(t, factors, k, stamp, grad);
       break;
   }
   return cudaGetLastError();

@@ -45,9 +45,10 @@ __device__ __forceinline__ void block_add_counts(Counters* c, unsigned long long
 // this step carry this step's stamp, so a D-thread can tell "E was live when
 // the step began" (live or DEAD_NOW) from "E absent" (ABSENT or DEAD_OLD).
 template <int G, bool RECORD>
-__global__ void __launch_bounds__(kThreads) k_forward(Table t, const Factor* __restrict__ factors, int k, double eps,
+__global__ void __launch_bounds__(kThreads, 4) k_forward(Table t, const Factor* __restrict__ factors, int k, double eps,
                                                        unsigned int stamp, Tape tape, unsigned long long n_max) {
   __shared__ int s_skip;
+  __shared__ LinkQueue s_q[kThreads / 32];
   if (threadIdx.x == 0) s_skip = *((volatile int*)&t.cnt->stop_k) >= 0;
   __syncthreads();
   const bool skip = s_skip != 0;
@@ -55,11 +56,11 @@ __global__ void __launch_bounds__(kThreads) k_forward(Table t, const Factor* __r
   if (!skip) {
     const Factor f = factors[k];
     const unsigned long long n = min(*((volatile unsigned long long*)&t.cnt->n_scan), t.cap_n);
-    const unsigned int lane = threadIdx.x & 31u;
-    const unsigned long long warp = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const unsigned long long nwarps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
-    for (unsigned long long base = warp * 32ull; base < n; base += nwarps * 32ull)
-      forward_entry<G, RECORD>(t, f, k, eps, stamp, tape, base + lane, base + lane < n, sc);
+    for_each_linked(t, f, n, s_q[threadIdx.x >> 5],
+                    [&](unsigned long long i, unsigned long long X, double cX, bool ex, bool act) {
+                      Lookup r = findG<G>(t, X ^ (f.occ | f.vir), act, stamp);
+                      if (act) forward_resolve<RECORD>(t, f, k, eps, stamp, tape, i, X, cX, ex, r, sc);
+                    });
   }
   block_add_counts(t.cnt, sc.rot, sc.cre, sc.dnew, sc.dold, sc.dead_delta);
   if (t.entropy) {
@@ -187,16 +188,20 @@ static cudaError_t forward_g(const Table& t, const Factor* factors, int k, doubl
                              const Tape& tape, unsigned long long n_max, int pw, int grid, cudaStream_t st) {
   switch (pw) {
     case 2:
-      k_forward<2, RECORD><<<grid, kThreads, 0, st>>>(t, factors, k, eps, stamp, tape, n_max);
+      k_forward<2, RECORD><<<one_wave<k_forward<2, RECORD>, kThreads>(grid), kThreads, 0, st>>>(
+          t, factors, k, eps, stamp, tape, n_max);
       break;
     case 4:
-      k_forward<4, RECORD><<<grid, kThreads, 0, st>>>(t, factors, k, eps, stamp, tape, n_max);
+      k_forward<4, RECORD><<<one_wave<k_forward<4, RECORD>, kThreads>(grid), kThreads, 0, st>>>(
+          t, factors, k, eps, stamp, tape, n_max);
       break;
     case 8:
-      k_forward<8, RECORD><<<grid, kThreads, 0, st>>>(t, factors, k, eps, stamp, tape, n_max);
+      k_forward<8, RECORD><<<one_wave<k_forward<8, RECORD>, kThreads>(grid), kThreads, 0, st>>>(
+          t, factors, k, eps, stamp, tape, n_max);
       break;
     default:
-      k_forward<1, RECORD><<<grid, kThreads, 0, st>>>(t, factors, k, eps, stamp, tape, n_max);
+      k_forward<1, RECORD><<<one_wave<k_forward<1, RECORD>, kThreads>(grid), kThreads, 0, st>>>(
+          t, factors, k, eps, stamp, tape, n_max);
       break;
   }
   return cudaGetLastError();
@@ -291,27 +296,17 @@ namespace {
 // G-lane probes (the autotuner times it); the result only feeds a checksum.
 template <int G>
 __global__ void __launch_bounds__(256) k_probe_bench(Table t, Factor f, unsigned long long* sink) {
+  __shared__ LinkQueue s_q[256 / 32];
   const unsigned long long n = min(*((volatile unsigned long long*)&t.cnt->n_tail), t.cap_n);
-  const unsigned int lane = threadIdx.x & 31u;
-  const unsigned long long warp = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const unsigned long long nwarps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
   const unsigned long long m = f.occ | f.vir;
   unsigned long long acc = 0;
-  for (unsigned long long base = warp * 32ull; base < n; base += nwarps * 32ull) {
-    const unsigned long long i = base + lane;
-    bool act = i < n;
-    unsigned long long X = 0;
-    if (act) {
-      X = t.keys[i];
-      const bool ex = ((X & f.occ) == f.occ) && ((X & f.vir) == 0ull);
-      const bool de = ((X & f.vir) == f.vir) && ((X & f.occ) == 0ull);
-      act = ex || de;
-    }
-    Lookup r = findG<G>(t, X ^ m, act, 0u);
-    if (act) acc += r.idx + (unsigned long long)r.state;
-  }
+  for_each_linked(t, f, n, s_q[threadIdx.x >> 5],
+                  [&](unsigned long long, unsigned long long X, double, bool, bool act) {
+                    Lookup r = findG<G>(t, X ^ m, act, 0u);
+                    if (act) acc += r.idx + (unsigned long long)r.state;
+                  });
   acc = warp_sum_u64(acc);
-  if (lane == 0 && acc) atomicAdd(sink, acc);
+  if ((threadIdx.x & 31u) == 0 && acc) atomicAdd(sink, acc);
 }
 
 }  // namespace

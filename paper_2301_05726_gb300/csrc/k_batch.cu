@@ -155,15 +155,30 @@ __global__ void __launch_bounds__(kThreads) k_forward_batch(const JobView* jobs,
   if (threadIdx.x == 0) bh->done = 0u;
 }
 
-// sigma and the energy sums of every job; one warp per stored entry.
+// sigma[0, n) = 0 in every job before the lower-triangle pass.
+__global__ void __launch_bounds__(kThreads) k_sigma_zero_batch(const JobView* jobs, JobState* js, int n_jobs,
+                                                                BatchHeader* bh) {
+  __shared__ unsigned long long s_base[kMaxBatchJobs + 1];
+  load_bases(js, n_jobs, bh, s_base);
+  const unsigned long long total = s_base[n_jobs];
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long g = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += stride) {
+    const int j = job_of(s_base, n_jobs, g);
+    jobs[j].t.sigma[g - s_base[j]] = 0.0;
+  }
+}
+
+// sigma and the energy sums of every job; one warp per stored entry, each
+// connected stored pair of a job visited once from its larger key (the
+// single-problem energy kernel's lower-triangle pass).
 __global__ void __launch_bounds__(kThreads) k_sigma_batch(const JobView* jobs, JobState* js, int n_jobs,
                                                            BatchHeader* bh) {
   __shared__ unsigned long long s_base[kMaxBatchJobs + 1];
-  __shared__ WarpLists lists[kWarps];
+  __shared__ LowerLists lists[kWarps];
   load_bases(js, n_jobs, bh, s_base);
   const unsigned long long total = s_base[n_jobs];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  WarpLists& L = lists[w];
+  LowerLists& L = lists[w];
   const unsigned long long gw = (unsigned long long)blockIdx.x * kWarps + w;
   const unsigned long long nw = (unsigned long long)gridDim.x * kWarps;
   int cur = -1;
@@ -190,11 +205,14 @@ __global__ void __launch_bounds__(kThreads) k_sigma_batch(const JobView* jobs, J
     const unsigned long long e = g - s_base[j];
     const double cI = jv.t.amps[e];
     if (is_dead(cI)) continue;
-    const double part = sigma_entry(jv.t, jv.in, L, jv.t.keys[e], cI, lane, probes, hits);
-    const double sig = warp_sum(part);
+    double d;
+    double part = sigma_lower(jv.t, jv.in, L, jv.t.keys[e], cI, lane, d, probes, hits);
+    d = warp_sum(d);
+    part = warp_sum(part);
     if (lane == 0) {
-      jv.t.sigma[e] = sig;
-      se += cI * sig;
+      const double dc = d * cI;
+      atomicAdd(&jv.t.sigma[e], dc + part);
+      se += cI * (dc + 2.0 * part);
       sn += cI * cI;
     }
     __syncwarp();
@@ -320,6 +338,7 @@ cudaError_t launch_forward_batch(const JobView* jobs, JobState* js, int n_jobs, 
 
 cudaError_t launch_sigma_batch(const JobView* jobs, JobState* js, int n_jobs, BatchHeader* bh, int grid,
                                cudaStream_t st) {
+  k_sigma_zero_batch<<<grid, kThreads, 0, st>>>(jobs, js, n_jobs, bh);
   k_sigma_batch<<<grid, kThreads, 0, st>>>(jobs, js, n_jobs, bh);
   return cudaGetLastError();
 }

@@ -2,15 +2,18 @@
 // UCCSD energy; the Hamiltonian of the Methods section's integrals).
 //
 // One warp per stored determinant I.  The warp builds I's occupied and empty
-// spin-orbital lists by spin in shared memory, then its lanes walk every
-// spin-conserving single and double J = tau I, look J up in the hash table
-// and, on a hit, add <I|H|J> c_J by the Slater-Condon rules:
+// spin-orbital lists by spin in shared memory, then its lanes walk the
+// spin-conserving singles and doubles J = tau I with J < I, look J up in the
+// hash table and, on a hit, add <I|H|J> c_J to sigma_I and <J|H|I> c_I to
+// sigma_J (H is real symmetric, so each connected stored pair is visited once,
+// from its larger key), by the Slater-Condon rules:
 //   <I|H|I>   = sum_{p in I} h_pp + 1/2 sum_{p,q in I} <pq||pq>
 //   <J|H|I>   = sgn (h_rp + sum_{k in I, k != p} <rk||pk>)     J = a+_r a_p I
 //   <J|H|I>   = sgn <rs||pq>                                  J = a+_r a+_s a_q a_p I
 // with <pq|rs> = (pr|qs) delta(spin p, spin r) delta(spin q, spin s) and
 // <pq||rs> = <pq|rs> - <pq|sr>.  sgn is the Jordan-Wigner sign of the
-// operator string on I.
+// operator string on I.  <psi|H|psi> = sum_I c_I^2 <I|H|I> + 2 sum_{J<I} c_I
+// <I|H|J> c_J is summed alongside.
 
 #include "ucc_steps.cuh"
 
@@ -20,11 +23,19 @@ namespace {
 
 constexpr int kWarps = 8;
 constexpr int kThreads = kWarps * 32;
+// sigma[0, n_tail) = 0 before the lower-triangle pass accumulates into it.
+__global__ void __launch_bounds__(256) k_sigma_zero(Table t) {
+  const unsigned long long n = min(*((volatile unsigned long long*)&t.cnt->n_tail), t.cap_n);
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    t.sigma[i] = 0.0;
+}
+
 __global__ void __launch_bounds__(kThreads) k_sigma(Table t, Integrals in) {
-  __shared__ WarpLists lists[kWarps];
+  __shared__ LowerLists lists[kWarps];
   const int w = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
-  WarpLists& L = lists[w];
+  LowerLists& L = lists[w];
   const unsigned long long n = min(*((volatile unsigned long long*)&t.cnt->n_tail), t.cap_n);
   const unsigned long long gw = (unsigned long long)blockIdx.x * kWarps + w;
   const unsigned long long nw = (unsigned long long)gridDim.x * kWarps;
@@ -34,11 +45,14 @@ __global__ void __launch_bounds__(kThreads) k_sigma(Table t, Integrals in) {
     const double cI = t.amps[e];
     if (is_dead(cI)) continue;  // warp-uniform
     const unsigned long long I = t.keys[e];
-    const double part = sigma_entry(t, in, L, I, cI, lane, probes, hits);
-    const double sig = warp_sum(part);
+    double d;
+    double part = sigma_lower(t, in, L, I, cI, lane, d, probes, hits);
+    d = warp_sum(d);
+    part = warp_sum(part);
     if (lane == 0) {
-      t.sigma[e] = sig;
-      acc_e += cI * sig;
+      const double dc = d * cI;
+      atomicAdd(&t.sigma[e], dc + part);
+      acc_e += cI * (dc + 2.0 * part);
       acc_n += cI * cI;
     }
     __syncwarp();
@@ -92,9 +106,10 @@ __global__ void __launch_bounds__(256) k_lambda_init(Table t) {
 
 }  // namespace
 
-int sigma_smem_bytes(int) { return (int)sizeof(WarpLists) * kWarps; }
+int sigma_smem_bytes(int) { return (int)sizeof(LowerLists) * kWarps; }
 
 cudaError_t launch_sigma(const Table& t, const Integrals& in, int grid, cudaStream_t st) {
+  k_sigma_zero<<<grid, 256, 0, st>>>(t);
   k_sigma<<<grid, kThreads, 0, st>>>(t, in);
   return cudaGetLastError();
 }

@@ -618,7 +618,7 @@ ucc_status run_energy(ucc_ctx* c, double* E, double* norm2) {
   CUDA_TRY(cudaMemsetAsync(&s.d_cnt->sig_probes, 0, 2 * sizeof(unsigned long long), c->stream));
   CUDA_TRY(cudaEventRecord(c->ev[2], c->stream));
   CUDA_TRY(launch_sigma(c->table(s), in, grid, c->stream));
-  c->launches++;
+  c->launches += 2;
   CUDA_TRY(cudaEventRecord(c->ev[3], c->stream));
   UCC_TRY(read_counters(c, s));
   float ms = 0.f;
@@ -1005,7 +1005,7 @@ ucc_status batch_on_stream(const std::vector<int>& idx, ucc_ctx* const* jobs, do
     for (int x = 0; x < n; ++x) {
       ucc_ctx* c = jobs[idx[x]];
       E[idx[x]] = hs[x].e_num / hs[x].norm2 + c->e_nuc;
-      c->launches += 2;
+      c->launches += 3;
     }
     if (record) {
       CUDA_TRY(launch_lambda_init_batch(d_jobs, d_js, n, d_bh, grid, st));

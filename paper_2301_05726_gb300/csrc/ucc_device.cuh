@@ -283,6 +283,22 @@ __device__ __forceinline__ TapeRec& tape_at(const Tape& tp, unsigned long long x
   return tp.pages[x >> kTapePageBits][x & (kTapePageRecs - 1ull)];
 }
 
+// Blocks of a kernel that are resident on the current device at once (one
+// full wave), capped at grid: grid-strided kernels launched with this run in
+// a single wave instead of a full wave plus a second one behind it.
+template <auto Kernel, int Threads>
+inline int one_wave(int grid) {
+  static const int resident = [] {
+    int dev = 0, sms = 0, occ = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, Kernel, Threads, 0) != cudaSuccess)
+      return 0;
+    return sms * occ;
+  }();
+  return resident > 0 && resident < grid ? resident : grid;
+}
+
 // Loads that bypass L1 (values other blocks wrote in this kernel).
 __device__ __forceinline__ unsigned long long ld_cg(const unsigned long long* p) { return __ldcg(p); }
 __device__ __forceinline__ double ld_cg(const double* p) { return __ldcg(p); }

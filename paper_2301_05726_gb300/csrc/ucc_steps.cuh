@@ -13,6 +13,16 @@ __device__ __forceinline__ bool below_eps(double v, double eps) {
          (unsigned long long)__double_as_longlong(eps);
 }
 
+// -v when flip is 1, else v: IEEE negation is a flip of the sign bit, done
+// here on the integer pipe (the same bits as a multiply by -1.0).
+__device__ __forceinline__ double neg_if(double v, int flip) {
+  return __longlong_as_double(
+      (long long)((unsigned long long)__double_as_longlong(v) ^ ((unsigned long long)(flip & 1) << 63)));
+}
+
+// v != 0.0 (either zero) on the bit pattern.
+__device__ __forceinline__ bool nonzero(double v) { return ((unsigned long long)__double_as_longlong(v) << 1) != 0ull; }
+
 struct StepCounts {
   unsigned long long rot = 0, cre = 0, dnew = 0, dold = 0;
   long long dead_delta = 0;
@@ -60,7 +70,7 @@ __device__ __forceinline__ void forward_resolve(const Table& t, const Factor& f,
   }
   const unsigned long long E = ex ? X : Y;
   const int parity = (__popcll(E & f.pmask) + f.pconst) & 1;
-  const double ss = parity ? -f.s : f.s;  // s * sin(theta), exact
+  const double ss = neg_if(f.s, parity);  // s * sin(theta), exact
   const double cE = ex ? cX : 0.0;
   const double cD = ex ? (partner_live ? r.amp : 0.0) : cX;
   // c_E' = cos c_E - s sin c_D ;  c_D' = cos c_D + s sin c_E  (no contraction)
@@ -70,8 +80,8 @@ __device__ __forceinline__ void forward_resolve(const Table& t, const Factor& f,
     // subtracting a zero leaves a nonzero product unchanged, so two products
     // give the same bits as the full formula whenever both are nonzero.
     const double pa = __dmul_rn(f.c, cX), pb = __dmul_rn(ss, cX);
-    if (pa != 0.0 && pb != 0.0) {
-      nE = ex ? pa : -pb;
+    if (nonzero(pa) && nonzero(pb)) {
+      nE = ex ? pa : neg_if(pb, 1);
       nD = ex ? pb : pa;
     } else {
       nE = __dsub_rn(__dmul_rn(f.c, cE), __dmul_rn(ss, cD));
@@ -132,26 +142,32 @@ __device__ __forceinline__ void forward_resolve(const Table& t, const Factor& f,
   }
 }
 
+// Scan half of a factor step: whether stored entry i (in_range false past the
+// end of the table) is a live member of one of the factor's linked pairs.  X
+// is its key, cX its amplitude, ex whether it is the excited member E.
+__device__ __forceinline__ bool linked_entry(const Table& t, const Factor& f, unsigned long long i, bool in_range,
+                                             unsigned long long& X, double& cX, bool& ex) {
+  X = 0ull;
+  cX = 0.0;
+  ex = false;
+  if (!in_range) return false;
+  X = t.keys[i];
+  ex = ((X & f.occ) == f.occ) && ((X & f.vir) == 0ull);
+  const bool de = ((X & f.vir) == f.vir) && ((X & f.occ) == 0ull);
+  if (!(ex || de)) return false;
+  cX = t.amps[i];
+  return !is_dead(cX);
+}
+
 template <int G, bool RECORD>
 __device__ __forceinline__ void forward_entry(const Table& t, const Factor& f, int k, double eps, unsigned int stamp,
                                               const Tape& tape, unsigned long long i, bool in_range,
                                               StepCounts& sc) {
-  bool act = in_range;
-  unsigned long long X = 0;
-  double cX = 0.0;
-  bool ex = false;
-  if (act) {
-    X = t.keys[i];
-    ex = ((X & f.occ) == f.occ) && ((X & f.vir) == 0ull);
-    const bool de = ((X & f.vir) == f.vir) && ((X & f.occ) == 0ull);
-    act = ex || de;
-    if (act) {
-      cX = t.amps[i];
-      act = !is_dead(cX);
-    }
-  }
-  const unsigned long long Y = X ^ (f.occ | f.vir);
-  Lookup r = findG<G>(t, Y, act, stamp);
+  unsigned long long X;
+  double cX;
+  bool ex;
+  const bool act = linked_entry(t, f, i, in_range, X, cX, ex);
+  Lookup r = findG<G>(t, X ^ (f.occ | f.vir), act, stamp);
   if (!act) return;
   forward_resolve<RECORD>(t, f, k, eps, stamp, tape, i, X, cX, ex, r, sc);
 }
@@ -172,8 +188,7 @@ __device__ __forceinline__ void reverse_resolve(const Table& t, const Factor& f,
   if (!ex && (partner_live || r.state == DEAD_NOW)) return;  // E's thread owns the pair
   const unsigned long long E = ex ? X : Y;
   const int parity = (__popcll(E & f.pmask) + f.pconst) & 1;
-  const double sg = parity ? -1.0 : 1.0;
-  const double ss = parity ? -f.s : f.s;
+  const double ss = neg_if(f.s, parity);
   const double muX = t.lam[i];
   ++pairs;
   if (partner_live) {
@@ -184,7 +199,7 @@ __device__ __forceinline__ void reverse_resolve(const Table& t, const Factor& f,
     const double d0 = __dsub_rn(__dmul_rn(f.c, d1), __dmul_rn(ss, e1));
     const double lE = __dadd_rn(__dmul_rn(f.c, muE), __dmul_rn(ss, muD));
     const double lD = __dsub_rn(__dmul_rn(f.c, muD), __dmul_rn(ss, muE));
-    acc += sg * (lD * e0 - lE * d0);
+    acc += neg_if(lD * e0 - lE * d0, parity);  // s (lam_D psi_E - lam_E psi_D)
     if (t.born[i] == (unsigned int)k) {
       t.amps[i] = dead_value(stamp);
     } else {
@@ -201,8 +216,8 @@ __device__ __forceinline__ void reverse_resolve(const Table& t, const Factor& f,
     // E alone: D was absent before the factor, c_E' = cos c_E.
     const double e0 = __dmul_rn(cX, f.ic);
     const double lE = __dmul_rn(f.c, muX);
-    const double lD = -__dmul_rn(ss, muX);
-    acc += sg * (lD * e0);
+    const double lD = neg_if(__dmul_rn(ss, muX), 1);
+    acc += neg_if(lD * e0, parity);
     t.amps[i] = e0;
     t.lam[i] = lE;
   } else {
@@ -210,7 +225,7 @@ __device__ __forceinline__ void reverse_resolve(const Table& t, const Factor& f,
     const double d0 = __dmul_rn(cX, f.ic);
     const double lD = __dmul_rn(f.c, muX);
     const double lE = __dmul_rn(ss, muX);
-    acc += sg * (-lE * d0);
+    acc += neg_if(lE * d0, parity ^ 1);
     t.amps[i] = d0;
     t.lam[i] = lD;
   }
@@ -219,24 +234,105 @@ __device__ __forceinline__ void reverse_resolve(const Table& t, const Factor& f,
 template <int G>
 __device__ __forceinline__ void reverse_entry(const Table& t, const Factor& f, int k, unsigned int stamp,
                                               unsigned long long i, bool in_range, double& acc, unsigned int& pairs) {
-  bool act = in_range;
-  unsigned long long X = 0;
-  double cX = 0.0;
-  bool ex = false;
-  if (act) {
-    X = t.keys[i];
-    ex = ((X & f.occ) == f.occ) && ((X & f.vir) == 0ull);
-    const bool de = ((X & f.vir) == f.vir) && ((X & f.occ) == 0ull);
-    act = ex || de;
-    if (act) {
-      cX = t.amps[i];
-      act = !is_dead(cX);
-    }
-  }
-  const unsigned long long Y = X ^ (f.occ | f.vir);
-  Lookup r = findG<G>(t, Y, act, stamp);
+  unsigned long long X;
+  double cX;
+  bool ex;
+  const bool act = linked_entry(t, f, i, in_range, X, cX, ex);
+  Lookup r = findG<G>(t, X ^ (f.occ | f.vir), act, stamp);
   if (!act) return;
   reverse_resolve(t, f, k, stamp, i, X, cX, ex, r, acc, pairs);
+}
+
+// Per-warp queue of linked entries in shared memory.  Only a fraction of the
+// stored determinants belong to a given factor's pairs, so a warp that
+// resolved its 32 scanned entries in place would run the pair arithmetic (on
+// the narrow FP64 pipe, where a warp instruction costs the same with one
+// lane as with 32) and the partner probes on mostly idle lanes.  Instead the
+// lanes append the linked entries they find, and while 32 or more are queued
+// the warp resolves them 32 at a time.  The order in which a step's pairs are
+// resolved does not matter: ownership and the dropped-entry stamps decide
+// everything from the state at the start of the step.
+// A warp scans kScanTiles tiles of 32 entries per round, so their key loads
+// (and then the amplitude loads of the linked ones) are in flight together.
+constexpr int kScanTiles = 4;
+constexpr int kQueue = 32 * (kScanTiles + 1);
+constexpr unsigned long long kExBit = 1ull << 63;
+
+struct LinkQueue {
+  unsigned long long i[kQueue];  // entry index, kExBit set for the excited member
+  unsigned long long X[kQueue];
+  double c[kQueue];
+};
+
+// Scan entries [0, n) in warp-strided rounds of kScanTiles tiles and call
+// resolve(i, X, cX, ex, active) on full warps of linked entries (a partial
+// warp at the end).  Every lane of the warp calls this; resolve is called by
+// all lanes together.
+template <class Resolve>
+__device__ __forceinline__ void for_each_linked(const Table& t, const Factor& f, unsigned long long n, LinkQueue& q,
+                                                Resolve resolve) {
+  const unsigned int lane = threadIdx.x & 31u;
+  const unsigned int below_me = (1u << lane) - 1u;
+  const unsigned long long warp = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const unsigned long long nwarps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
+  constexpr unsigned long long kRound = 32ull * kScanTiles;
+  int qn = 0;  // warp-uniform queue length, < 32 between rounds
+  for (unsigned long long base = warp * kRound; base < n; base += nwarps * kRound) {
+    unsigned long long X[kScanTiles];
+    double c[kScanTiles];
+    bool lk[kScanTiles], ex[kScanTiles];
+#pragma unroll
+    for (int u = 0; u < kScanTiles; ++u) {
+      const unsigned long long i = base + 32ull * u + lane;
+      X[u] = i < n ? t.keys[i] : 0ull;
+    }
+#pragma unroll
+    for (int u = 0; u < kScanTiles; ++u) {
+      const unsigned long long i = base + 32ull * u + lane;
+      ex[u] = ((X[u] & f.occ) == f.occ) && ((X[u] & f.vir) == 0ull);
+      const bool de = ((X[u] & f.vir) == f.vir) && ((X[u] & f.occ) == 0ull);
+      lk[u] = i < n && (ex[u] || de);
+    }
+#pragma unroll
+    for (int u = 0; u < kScanTiles; ++u) {
+      const unsigned long long i = base + 32ull * u + lane;
+      c[u] = lk[u] ? t.amps[i] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < kScanTiles; ++u) {
+      const bool act = lk[u] && !is_dead(c[u]);
+      const unsigned int m = __ballot_sync(0xFFFFFFFFu, act);
+      if (act) {
+        const int p = qn + __popc(m & below_me);
+        q.i[p] = (base + 32ull * u + lane) | (ex[u] ? kExBit : 0ull);
+        q.X[p] = X[u];
+        q.c[p] = c[u];
+      }
+      qn += __popc(m);
+    }
+    while (qn >= 32) {
+      __syncwarp();
+      const int p = qn - 32 + (int)lane;
+      const unsigned long long qi = q.i[p];
+      const unsigned long long qX = q.X[p];
+      const double qc = q.c[p];
+      __syncwarp();
+      qn -= 32;
+      resolve(qi & ~kExBit, qX, qc, (qi & kExBit) != 0ull, true);
+    }
+  }
+  __syncwarp();
+  if (qn > 0) {
+    const bool a = (int)lane < qn;
+    unsigned long long qi = 0ull, qX = 0ull;
+    double qc = 0.0;
+    if (a) {
+      qi = q.i[lane];
+      qX = q.X[lane];
+      qc = q.c[lane];
+    }
+    resolve(qi & ~kExBit, qX, qc, (qi & kExBit) != 0ull, a);
+  }
 }
 
 constexpr int kMaxSpin = 32;                          // spin-orbitals of one spin
@@ -360,6 +456,214 @@ __device__ __forceinline__ void probe_connections(const Table& t, int count, int
       part += elem(u, J[v]) * cJ;
     }
   }
+}
+
+// The slot probe of lookup_live, also giving the entry index of a live hit.
+__device__ __forceinline__ bool probe_live_at(const Table& t, unsigned long long key, double* amp,
+                                              unsigned long long* idx) {
+  unsigned long long h = home_slot(t, key);
+  for (int step = 0; step < MAX_PROBE; ++step) {
+    const Slot s = t.slots[h];
+    if (s.key == key) {
+      const double a = t.amps[s.idx];
+      if (is_dead(a)) return false;
+      *amp = a;
+      *idx = s.idx;
+      return true;
+    }
+    if (s.key == 0ull) return false;
+    h = (h + 1) & t.slot_mask;
+  }
+  raise_error(t.cnt, ERR_PROBE_BOUND);
+  return false;
+}
+
+// Spin-orbital p has spin p & 1: alpha on even bits, beta on odd bits.
+constexpr unsigned long long kAlphaBits = 0x5555555555555555ull;
+constexpr unsigned long long kBetaBits = 0xAAAAAAAAAAAAAAAAull;
+
+// Per-warp lists of one determinant I for the lower-triangle sigma.
+struct LowerLists {
+  unsigned char occ[2][kMaxSpin];
+  unsigned char emp[2][kMaxSpin];
+  int n_occ[2], n_emp[2];
+  unsigned short pairs[2][kMaxPairs];       // same-spin empty pairs (r | s << 8), r < s, ordered by s
+  unsigned short opp[kMaxSpin * kMaxSpin];  // (r alpha | s beta << 8), ordered by max(r, s)
+};
+
+// Like probe_connections, for the connections J < I of a lower-triangle
+// pass: a hit adds <I|H|J> c_J to the lane's share of sigma_I and the
+// transposed term <J|H|I> c_I (H is real symmetric) to sigma_J in memory.
+template <class KeyOf, class Elem>
+__device__ __forceinline__ void probe_lower(const Table& t, int count, int lane, double cI, KeyOf key_of, Elem elem,
+                                            double& part, unsigned long long& probes, unsigned long long& hits) {
+  for (int u0 = lane; u0 < count; u0 += 32 * kV) {
+    unsigned long long J[kV];
+    unsigned int w[kV];
+#pragma unroll
+    for (int v = 0; v < kV; ++v) {
+      const int u = u0 + 32 * v;
+      J[v] = u < count ? key_of(u) : 0ull;
+    }
+#pragma unroll
+    for (int v = 0; v < kV; ++v) {
+      const int u = u0 + 32 * v;
+      w[v] = 0u;
+      if (u < count) {
+        if (t.filt) {
+          const unsigned long long b = (J[v] * kFilterMul) >> t.filt_shift;
+          w[v] = (t.filt[b >> 5] >> (b & 31u)) & 1u;
+        } else {
+          w[v] = 1u;
+        }
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < kV; ++v) {
+      const int u = u0 + 32 * v;
+      if (u >= count) continue;
+      ++probes;
+      double cJ;
+      unsigned long long j;
+      if (!w[v] || !probe_live_at(t, J[v], &cJ, &j)) continue;
+      ++hits;
+      const double h = elem(u, J[v]);
+      part += h * cJ;
+      atomicAdd(&t.sigma[j], h * cI);
+    }
+  }
+}
+
+// Lower-triangle sigma for one stored determinant I: the lane's share of
+// sum_{J in S, J < I} <I|H|J> c_J (returned) and of the diagonal <I|H|I>
+// (in diag), with every hit's transposed term sent to sigma_J.  Over all
+// stored I this covers each connected stored pair once, from its larger key.
+// J = I with holes P and particles Q set/cleared is below I exactly when the
+// highest changed spin-orbital is a hole, max(P) > max(Q), so every list
+// below is cut to a prefix by counting the empty orbitals under max(P): no
+// connection J > I is generated.  Every lane of the warp calls this.
+__device__ __forceinline__ double sigma_lower(const Table& t, const Integrals& in, LowerLists& L,
+                                              unsigned long long I, double cI, int lane, double& diag,
+                                              unsigned long long& probes, unsigned long long& hits) {
+  const unsigned long long all = in.n_so >= 64 ? ~0ull : ((1ull << in.n_so) - 1ull);
+  const unsigned long long emask = ~I & all;
+  // empty spin-orbitals of spin sp below orbital m
+  auto empty_below = [&](int sp, int m) { return __popcll(emask & (sp ? kBetaBits : kAlphaBits) & below(m)); };
+  if (lane == 0) {
+    for (int sp = 0; sp < 2; ++sp) L.n_occ[sp] = L.n_emp[sp] = 0;
+    for (int p = 0; p < in.n_so; ++p) {
+      const int sp = p & 1;
+      if ((I >> p) & 1ull)
+        L.occ[sp][L.n_occ[sp]++] = (unsigned char)p;
+      else
+        L.emp[sp][L.n_emp[sp]++] = (unsigned char)p;
+    }
+  }
+  __syncwarp();
+  for (int sp = 0; sp < 2; ++sp) {
+    const int m = L.n_emp[sp];
+    const int np = m * (m - 1) / 2;
+    for (int u = lane; u < np; u += 32) {
+      // u -> (x, y), x < y, column by column: u = y (y - 1) / 2 + x
+      int y = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)u)) * 0.5f);
+      while (y * (y - 1) / 2 > u) --y;
+      while ((y + 1) * y / 2 <= u) ++y;
+      const int x = u - y * (y - 1) / 2;
+      L.pairs[sp][u] = (unsigned short)(L.emp[sp][x] | (L.emp[sp][y] << 8));
+    }
+  }
+  // Opposite-spin empty pairs grouped by their larger orbital o: the pairs
+  // with max < o number (alpha empties below o) * (beta empties below o).
+  for (int o = lane; o < in.n_so; o += 32) {
+    if (!((emask >> o) & 1ull)) continue;
+    const int ra = empty_below(0, o), sb = empty_below(1, o);
+    const int st = ra * sb;
+    if ((o & 1) == 0) {
+      for (int j = 0; j < sb; ++j) L.opp[st + j] = (unsigned short)(o | (L.emp[1][j] << 8));
+    } else {
+      for (int j = 0; j < ra; ++j) L.opp[st + j] = (unsigned short)(L.emp[0][j] | (o << 8));
+    }
+  }
+  __syncwarp();
+
+  // Diagonal: lanes over the first index p.
+  double d = 0.0;
+  for (int sp = 0; sp < 2; ++sp)
+    for (int x = lane; x < L.n_occ[sp]; x += 32) {
+      const int p = L.occ[sp][x];
+      d += h_so(in, p, p);
+      for (int sq = 0; sq < 2; ++sq)
+        for (int y = 0; y < L.n_occ[sq]; ++y) {
+          const int q = L.occ[sq][y];
+          if (q != p) d += 0.5 * anti(in, p, q, p, q);
+        }
+    }
+  diag = d;
+
+  double part = 0.0;
+  // Singles p -> r, same spin, r < p.
+  for (int sp = 0; sp < 2; ++sp)
+    for (int x = 0; x < L.n_occ[sp]; ++x) {
+      const int p = L.occ[sp][x];
+      probe_lower(
+          t, empty_below(sp, p), lane, cI, [&](int u) { return I ^ ((1ull << p) | (1ull << L.emp[sp][u])); },
+          [&](int u, unsigned long long) {
+            const int r = L.emp[sp][u];
+            double v = h_so(in, r, p);
+            for (int sk = 0; sk < 2; ++sk)
+              for (int y = 0; y < L.n_occ[sk]; ++y) {
+                const int kk = L.occ[sk][y];
+                if (kk != p) v += anti(in, r, kk, p, kk);
+              }
+            return single_parity(I, p, r) ? -v : v;
+          },
+          part, probes, hits);
+    }
+  // Doubles, same spin: holes p < q, particles r < s < q.
+  for (int sp = 0; sp < 2; ++sp) {
+    const int no = L.n_occ[sp];
+    for (int x = 0; x < no; ++x)
+      for (int y = x + 1; y < no; ++y) {
+        const int p = L.occ[sp][x], q = L.occ[sp][y];
+        const unsigned long long hole = (1ull << p) | (1ull << q);
+        const int y0 = empty_below(sp, q);
+        probe_lower(
+            t, y0 * (y0 - 1) / 2, lane, cI,
+            [&](int u) {
+              const unsigned short pr = L.pairs[sp][u];
+              return I ^ (hole | (1ull << (pr & 0xFF)) | (1ull << (pr >> 8)));
+            },
+            [&](int u, unsigned long long) {
+              const unsigned short pr = L.pairs[sp][u];
+              const int r = pr & 0xFF, s = pr >> 8;
+              const double v = anti(in, r, s, p, q);
+              return double_parity(I, p, q, r, s) ? -v : v;
+            },
+            part, probes, hits);
+      }
+  }
+  // Doubles, opposite spin: holes p alpha, q beta; particles r alpha, s beta
+  // both below max(p, q).
+  for (int x = 0; x < L.n_occ[0]; ++x)
+    for (int y = 0; y < L.n_occ[1]; ++y) {
+      const int p = L.occ[0][x], q = L.occ[1][y];
+      const int m = p > q ? p : q;
+      const unsigned long long hole = (1ull << p) | (1ull << q);
+      probe_lower(
+          t, empty_below(0, m) * empty_below(1, m), lane, cI,
+          [&](int u) {
+            const unsigned short pr = L.opp[u];
+            return I ^ (hole | (1ull << (pr & 0xFF)) | (1ull << (pr >> 8)));
+          },
+          [&](int u, unsigned long long) {
+            const unsigned short pr = L.opp[u];
+            const int r = pr & 0xFF, s = pr >> 8;
+            const double v = anti(in, r, s, p, q);
+            return double_parity(I, p, q, r, s) ? -v : v;
+          },
+          part, probes, hits);
+    }
+  return part;
 }
 
 // The lane's share of sigma_I = sum_{J in S} <I|H|J> c_J for one stored
