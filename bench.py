@@ -307,6 +307,9 @@ def run_ours(args, prob):
         "e2e": {"value": rot_all / (e2e_ms / 1e3), "unit": UNIT,
                 "h2d_bytes_per_step": 48 * prob.n_exc, "d2h_bytes_per_step": 8 * prob.n_exc + 8},
         "gpu_launches": int(tot["kernel_launches"]),
+        "counts_per_step": {k: int(tot[k] // n_steps) for k in (
+            "rotations", "created", "dropped_new", "dropped_old", "cut", "scanned", "rebuilds", "tape_entries",
+            "sigma_probes", "sigma_hits", "reverse_pairs", "recompute_rotations")},
         "roofline": roof,
         "kernels": {k: {x: v[x] for x in ("achieved", "frac", "launches", "avg_launch_ms", "total_ms")}
                     for k, v in kernels.items()},

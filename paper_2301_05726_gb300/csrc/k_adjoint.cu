@@ -50,12 +50,12 @@ __global__ void __launch_bounds__(kThreads) k_tape_reinsert(Table t, Tape tape, 
 template <int G>
 __global__ void __launch_bounds__(kThreads) k_reverse(Table t, const Factor* __restrict__ factors, int k,
                                                        unsigned int stamp, double* grad) {
-  __shared__ LinkQueue s_q[kThreads / 32];
+  __shared__ LinkScratch s_w[kThreads / 32];
   const Factor f = factors[k];
   const unsigned long long n = min(*((volatile unsigned long long*)&t.cnt->n_tail), t.cap_n);
   double acc = 0.0;
   unsigned int pairs = 0;
-  for_each_linked(t, f, n, s_q[threadIdx.x >> 5],
+  for_each_linked(t, f, n, s_w[threadIdx.x >> 5],
                   [&](unsigned long long i, unsigned long long X, double cX, bool ex, bool act) {
                     Lookup r = findG<G>(t, X ^ (f.occ | f.vir), act, stamp);
                     if (act) reverse_resolve(t, f, k, stamp, i, X, cX, ex, r, acc, pairs);
@@ -90,6 +90,7 @@ cudaError_t launch_tape_reinsert(const Table& t, const Tape& tape, int k, int gr
 
 cudaError_t launch_reverse(const Table& t, const Factor* factors, int k, unsigned int stamp, double* grad,
                            int probe_width, int grid, cudaStream_t st) {
+  if (!scan_aligned(t)) return cudaErrorMisalignedAddress;
   switch (probe_width) {
     case 2:
       k_reverse<2><<<one_wave<k_reverse<2>, kThreads>(grid), kThreads, 0, st>>>(t, factors, k, stamp, grad);

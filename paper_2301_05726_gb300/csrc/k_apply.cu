@@ -48,7 +48,7 @@ template <int G, bool RECORD>
 __global__ void __launch_bounds__(kThreads, 4) k_forward(Table t, const Factor* __restrict__ factors, int k, double eps,
                                                        unsigned int stamp, Tape tape, unsigned long long n_max) {
   __shared__ int s_skip;
-  __shared__ LinkQueue s_q[kThreads / 32];
+  __shared__ LinkScratch s_w[kThreads / 32];
   if (threadIdx.x == 0) s_skip = *((volatile int*)&t.cnt->stop_k) >= 0;
   __syncthreads();
   const bool skip = s_skip != 0;
@@ -56,10 +56,10 @@ __global__ void __launch_bounds__(kThreads, 4) k_forward(Table t, const Factor* 
   if (!skip) {
     const Factor f = factors[k];
     const unsigned long long n = min(*((volatile unsigned long long*)&t.cnt->n_scan), t.cap_n);
-    for_each_linked(t, f, n, s_q[threadIdx.x >> 5],
+    for_each_linked(t, f, n, s_w[threadIdx.x >> 5],
                     [&](unsigned long long i, unsigned long long X, double cX, bool ex, bool act) {
                       Lookup r = findG<G>(t, X ^ (f.occ | f.vir), act, stamp);
-                      if (act) forward_resolve<RECORD>(t, f, k, eps, stamp, tape, i, X, cX, ex, r, sc);
+                      if (act) forward_resolve<RECORD, true>(t, f, k, eps, stamp, tape, i, X, cX, ex, r, sc);
                     });
   }
   block_add_counts(t.cnt, sc.rot, sc.cre, sc.dnew, sc.dold, sc.dead_delta);
@@ -83,6 +83,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_forward(Table t, const Factor* 
     c->done = 0u;
     if (!skip) {
       const unsigned long long nt = ld_cg(&c->n_tail);
+      c->link_from = ld_cg(&c->n_scan);  // this step's appended entries, linked next
+      c->link_to = nt;
       c->scanned += ld_cg(&c->n_scan);
       c->n_scan = nt;
       unsigned long long tn = 0;
@@ -100,6 +102,18 @@ __global__ void __launch_bounds__(kThreads, 4) k_forward(Table t, const Factor* 
       if (!room || cut) c->stop_k = k + 1;
     }
   }
+}
+
+// Hash slots for the entries factor k's step appended (k_forward defers
+// them); skipped with the step itself when an earlier factor stopped the chunk.
+__global__ void __launch_bounds__(kThreads) k_link(Table t, int k) {
+  const int stop = *((volatile int*)&t.cnt->stop_k);
+  if (stop >= 0 && stop <= k) return;
+  const unsigned long long lo = *((volatile unsigned long long*)&t.cnt->link_from);
+  const unsigned long long hi = min(*((volatile unsigned long long*)&t.cnt->link_to), t.cap_n);
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long j = lo + (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; j < hi; j += stride)
+    link_appended(t, t.keys[j], j);
 }
 
 // Copy the live entries of `from` into `to` (unordered), counting in new_n.
@@ -209,8 +223,12 @@ static cudaError_t forward_g(const Table& t, const Factor* factors, int k, doubl
 
 cudaError_t launch_forward(const Table& t, const Factor* factors, int k, double eps, unsigned int stamp, int record,
                            const Tape& tape, unsigned long long n_max, int probe_width, int grid, cudaStream_t st) {
-  return record ? forward_g<true>(t, factors, k, eps, stamp, tape, n_max, probe_width, grid, st)
-                : forward_g<false>(t, factors, k, eps, stamp, tape, n_max, probe_width, grid, st);
+  if (!scan_aligned(t)) return cudaErrorMisalignedAddress;
+  const cudaError_t e = record ? forward_g<true>(t, factors, k, eps, stamp, tape, n_max, probe_width, grid, st)
+                               : forward_g<false>(t, factors, k, eps, stamp, tape, n_max, probe_width, grid, st);
+  if (e != cudaSuccess) return e;
+  k_link<<<one_wave<k_link, kThreads>(grid), kThreads, 0, st>>>(t, k);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_compact(const Table& from, const Table& to, int with_born, int grid, cudaStream_t st) {
@@ -296,11 +314,11 @@ namespace {
 // G-lane probes (the autotuner times it); the result only feeds a checksum.
 template <int G>
 __global__ void __launch_bounds__(256) k_probe_bench(Table t, Factor f, unsigned long long* sink) {
-  __shared__ LinkQueue s_q[256 / 32];
+  __shared__ LinkScratch s_w[256 / 32];
   const unsigned long long n = min(*((volatile unsigned long long*)&t.cnt->n_tail), t.cap_n);
   const unsigned long long m = f.occ | f.vir;
   unsigned long long acc = 0;
-  for_each_linked(t, f, n, s_q[threadIdx.x >> 5],
+  for_each_linked(t, f, n, s_w[threadIdx.x >> 5],
                   [&](unsigned long long, unsigned long long X, double, bool, bool act) {
                     Lookup r = findG<G>(t, X ^ m, act, 0u);
                     if (act) acc += r.idx + (unsigned long long)r.state;
@@ -313,6 +331,7 @@ __global__ void __launch_bounds__(256) k_probe_bench(Table t, Factor f, unsigned
 
 cudaError_t launch_probe_bench(const Table& t, const Factor& f, int probe_width, unsigned long long* sink, int grid,
                                cudaStream_t st) {
+  if (!scan_aligned(t)) return cudaErrorMisalignedAddress;
   switch (probe_width) {
     case 2:
       k_probe_bench<2><<<grid, 256, 0, st>>>(t, f, sink);

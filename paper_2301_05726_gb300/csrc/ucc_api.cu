@@ -498,7 +498,7 @@ ucc_status run_factors(ucc_ctx* c, TableSet& s, double eps, bool record, int k0,
     for (int kk = k; kk < end; ++kk) {
       CUDA_TRY(launch_forward(c->table(s), c->d_factors, kk, eps, (unsigned int)(kk + 1), record ? 1 : 0, c->tape(),
                               n_max, pw, grid, c->stream));
-      c->launches++;
+      c->launches += 2;  // the step and the linking of its appended entries
       c->stats.forward_launches++;
     }
     CUDA_TRY(cudaEventRecord(c->kev[1], c->stream));

@@ -6,22 +6,40 @@
 
 namespace ucc {
 
-// |v| < eps for finite v and eps >= 0, decided on the IEEE bit patterns
-// (non-negative doubles order like their bits), off the scarce FP64 pipe.
+// Bit-pattern tests and sign flips of doubles.  They are written in inline
+// PTX on 32/64-bit integer registers: as plain C++ the compiler recognises
+// the patterns and turns them back into FP64 negations and compares, which
+// run on the GPU's narrow FP64 pipe.
+
+// |v| < eps for finite v and eps >= 0 (non-negative doubles order like their
+// bit patterns).
 __device__ __forceinline__ bool below_eps(double v, double eps) {
-  return ((unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull) <
-         (unsigned long long)__double_as_longlong(eps);
+  unsigned int r;
+  asm("{\n\t.reg .pred q;\n\t.reg .b64 m;\n\t"
+      "and.b64 m, %1, 0x7FFFFFFFFFFFFFFF;\n\t"
+      "setp.lt.u64 q, m, %2;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "l"(__double_as_longlong(v)), "l"(__double_as_longlong(eps)));
+  return r != 0u;
 }
 
-// -v when flip is 1, else v: IEEE negation is a flip of the sign bit, done
-// here on the integer pipe (the same bits as a multiply by -1.0).
+// -v when flip is 1, else v: the sign bit flipped by an integer xor (the
+// same bits as a multiply by -1.0).
 __device__ __forceinline__ double neg_if(double v, int flip) {
-  return __longlong_as_double(
-      (long long)((unsigned long long)__double_as_longlong(v) ^ ((unsigned long long)(flip & 1) << 63)));
+  unsigned int hi;
+  asm("xor.b32 %0, %1, %2;" : "=r"(hi) : "r"(__double2hiint(v)), "r"((unsigned int)(flip & 1) << 31));
+  return __hiloint2double((int)hi, __double2loint(v));
 }
 
 // v != 0.0 (either zero) on the bit pattern.
-__device__ __forceinline__ bool nonzero(double v) { return ((unsigned long long)__double_as_longlong(v) << 1) != 0ull; }
+__device__ __forceinline__ bool nonzero(double v) {
+  unsigned int r;
+  asm("{\n\t.reg .b32 h;\n\tand.b32 h, %1, 0x7FFFFFFF;\n\tor.b32 %0, h, %2;\n\t}"
+      : "=r"(r)
+      : "r"(__double2hiint(v)), "r"(__double2loint(v)));
+  return r != 0u;
+}
 
 struct StepCounts {
   unsigned long long rot = 0, cre = 0, dnew = 0, dold = 0;
@@ -57,7 +75,42 @@ __device__ __forceinline__ void record_kill(const Table& t, const Tape& tape, un
 // lanes); in_range is false for lanes past the end of the table.
 // The rotation, creation and eps rule for one linked entry i (key X, live
 // amplitude cX, ex = X is the excited member) whose partner lookup is r.
-template <bool RECORD>
+// Append a created entry without hashing it: within a factor step no thread
+// looks a created key up (its only partner is the creating entry), so the
+// slot is claimed after the step (link_appended) and the claim's round trip
+// stays off the step's critical path.
+__device__ __forceinline__ void append_unlinked(const Table& t, unsigned long long key, double amp,
+                                                unsigned int born, bool with_born) {
+  const unsigned long long idx = aggregated_add(&t.cnt->n_tail);
+  if (idx >= t.cap_n) {
+    raise_error(t.cnt, ERR_CAPACITY);
+    return;
+  }
+  t.keys[idx] = key;
+  t.amps[idx] = amp;
+  if (with_born) t.born[idx] = born;
+}
+
+// Give appended entry idx its hash slot unless its key already has one (a
+// revived key, whose slot the step repointed).
+__device__ __forceinline__ void link_appended(const Table& t, unsigned long long key, unsigned long long idx) {
+  unsigned long long h = home_slot(t, key);
+  for (int step = 0; step < MAX_PROBE; ++step) {
+    const unsigned long long prev = atomicCAS(&t.slots[h].key, 0ull, key);
+    if (prev == 0ull) {
+      t.slots[h].idx = idx;
+      filter_add(t, key);
+      return;
+    }
+    if (prev == key) return;
+    h = (h + 1) & t.slot_mask;
+  }
+  raise_error(t.cnt, ERR_PROBE_BOUND);
+}
+
+// DEFER: created entries are appended unlinked (link_appended runs after the
+// step); otherwise they are hashed at once.
+template <bool RECORD, bool DEFER = false>
 __device__ __forceinline__ void forward_resolve(const Table& t, const Factor& f, int k, double eps, unsigned int stamp,
                                                 const Tape& tape, unsigned long long i, unsigned long long X,
                                                 double cX, bool ex, const Lookup& r, StepCounts& sc) {
@@ -137,7 +190,10 @@ __device__ __forceinline__ void forward_resolve(const Table& t, const Factor& f,
     }
     ++sc.cre;
   } else {
-    insert_new(t, Y, nY, (unsigned int)k, r.slot, RECORD, false);
+    if (DEFER)
+      append_unlinked(t, Y, nY, (unsigned int)k, RECORD);
+    else
+      insert_new(t, Y, nY, (unsigned int)k, r.slot, RECORD, false);
     ++sc.cre;
   }
 }
@@ -193,13 +249,18 @@ __device__ __forceinline__ void reverse_resolve(const Table& t, const Factor& f,
   ++pairs;
   if (partner_live) {
     // Both members stored: (e, d) = U^T (e', d'), (lamE, lamD) = U^T (muE, muD).
+    // The reverse sweep feeds only the gradient (no eps decision rests on
+    // it), so it contracts to fused multiply-adds: fewer FP64 instructions,
+    // and each result rounded once.
     const double e1 = cX, d1 = r.amp;
     const double muE = muX, muD = t.lam[r.idx];
-    const double e0 = __dadd_rn(__dmul_rn(f.c, e1), __dmul_rn(ss, d1));
-    const double d0 = __dsub_rn(__dmul_rn(f.c, d1), __dmul_rn(ss, e1));
-    const double lE = __dadd_rn(__dmul_rn(f.c, muE), __dmul_rn(ss, muD));
-    const double lD = __dsub_rn(__dmul_rn(f.c, muD), __dmul_rn(ss, muE));
-    acc += neg_if(lD * e0 - lE * d0, parity);  // s (lam_D psi_E - lam_E psi_D)
+    const double e0 = fma(f.c, e1, ss * d1);
+    const double d0 = fma(f.c, d1, -(ss * e1));
+    const double lE = fma(f.c, muE, ss * muD);
+    const double lD = fma(f.c, muD, -(ss * muE));
+    // acc += s (lam_D psi_E - lam_E psi_D)
+    acc = fma(neg_if(lD, parity), e0, acc);
+    acc = fma(neg_if(lE, parity ^ 1), d0, acc);
     if (t.born[i] == (unsigned int)k) {
       t.amps[i] = dead_value(stamp);
     } else {
@@ -217,7 +278,7 @@ __device__ __forceinline__ void reverse_resolve(const Table& t, const Factor& f,
     const double e0 = __dmul_rn(cX, f.ic);
     const double lE = __dmul_rn(f.c, muX);
     const double lD = neg_if(__dmul_rn(ss, muX), 1);
-    acc += neg_if(lD * e0, parity);
+    acc = fma(neg_if(lD, parity), e0, acc);
     t.amps[i] = e0;
     t.lam[i] = lE;
   } else {
@@ -225,7 +286,7 @@ __device__ __forceinline__ void reverse_resolve(const Table& t, const Factor& f,
     const double d0 = __dmul_rn(cX, f.ic);
     const double lD = __dmul_rn(f.c, muX);
     const double lE = __dmul_rn(ss, muX);
-    acc += neg_if(lE * d0, parity ^ 1);
+    acc = fma(neg_if(lE, parity ^ 1), d0, acc);
     t.amps[i] = d0;
     t.lam[i] = lD;
   }
@@ -252,10 +313,13 @@ __device__ __forceinline__ void reverse_entry(const Table& t, const Factor& f, i
 // the warp resolves them 32 at a time.  The order in which a step's pairs are
 // resolved does not matter: ownership and the dropped-entry stamps decide
 // everything from the state at the start of the step.
-// A warp scans kScanTiles tiles of 32 entries per round, so their key loads
-// (and then the amplitude loads of the linked ones) are in flight together.
+// A warp scans rounds of kScanTiles tiles of 32 entries.  The keys and
+// amplitudes of its next round are copied into shared memory (cp.async, two
+// buffers per warp) while it resolves the current one, so the scan's load
+// latency overlaps the pair work.
 constexpr int kScanTiles = 4;
-constexpr int kQueue = 32 * (kScanTiles + 1);
+constexpr int kRound = 32 * kScanTiles;
+constexpr int kQueue = 64;
 constexpr unsigned long long kExBit = 1ull << 63;
 
 struct LinkQueue {
@@ -264,63 +328,110 @@ struct LinkQueue {
   double c[kQueue];
 };
 
-// Scan entries [0, n) in warp-strided rounds of kScanTiles tiles and call
+struct __align__(16) ScanStage {
+  unsigned long long X[kRound];
+  double c[kRound];
+};
+
+// Per-warp shared memory of for_each_linked.
+struct LinkScratch {
+  ScanStage stage[2];
+  LinkQueue q;
+};
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src_bytes) {
+  const unsigned int s = (unsigned int)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all_but_last() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+// The staged scan copies 16-byte pieces starting at even entries, so keys and
+// amps must start on a 16-byte boundary (device allocations do).
+inline bool scan_aligned(const Table& t) {
+  return ((reinterpret_cast<uintptr_t>(t.keys) | reinterpret_cast<uintptr_t>(t.amps)) & 15u) == 0u;
+}
+
+// Copy entries [base, min(base + kRound, n)) of keys and amps into a stage:
+// 16-byte pieces of two entries; the piece holding entry n - 1 alone copies 8
+// bytes (the rest zero-filled) and pieces past n are not issued.
+__device__ __forceinline__ void stage_round(const Table& t, ScanStage& st, unsigned long long base,
+                                            unsigned long long n, unsigned int lane) {
+#pragma unroll
+  for (int h = 0; h < kRound / 64; ++h) {
+    const int e = 2 * (int)(lane + 32u * h);  // first entry of the piece, relative to base
+    const unsigned long long g = base + (unsigned long long)e;
+    if (g < n) {
+      const int bytes = g + 1ull < n ? 16 : 8;
+      cp_async16(&st.X[e], t.keys + g, bytes);
+      cp_async16(&st.c[e], t.amps + g, bytes);
+    }
+  }
+}
+
+// Scan entries [0, n) in warp-strided rounds of kRound entries and call
 // resolve(i, X, cX, ex, active) on full warps of linked entries (a partial
 // warp at the end).  Every lane of the warp calls this; resolve is called by
 // all lanes together.
 template <class Resolve>
-__device__ __forceinline__ void for_each_linked(const Table& t, const Factor& f, unsigned long long n, LinkQueue& q,
-                                                Resolve resolve) {
+__device__ __forceinline__ void for_each_linked(const Table& t, const Factor& f, unsigned long long n,
+                                                LinkScratch& w, Resolve resolve) {
   const unsigned int lane = threadIdx.x & 31u;
   const unsigned int below_me = (1u << lane) - 1u;
   const unsigned long long warp = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const unsigned long long nwarps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
-  constexpr unsigned long long kRound = 32ull * kScanTiles;
-  int qn = 0;  // warp-uniform queue length, < 32 between rounds
-  for (unsigned long long base = warp * kRound; base < n; base += nwarps * kRound) {
-    unsigned long long X[kScanTiles];
-    double c[kScanTiles];
-    bool lk[kScanTiles], ex[kScanTiles];
-#pragma unroll
+  const unsigned long long step = nwarps * (unsigned long long)kRound;
+  LinkQueue& q = w.q;
+  int qn = 0;  // warp-uniform queue length, < 32 between tiles
+  unsigned long long base = warp * (unsigned long long)kRound;
+  if (base < n) stage_round(t, w.stage[0], base, n, lane);
+  cp_async_commit();
+  for (int r = 0; base < n; base += step, ++r) {
+    // Next round's copy into the other buffer (its last reader was round r - 1).
+    if (base + step < n) stage_round(t, w.stage[(r + 1) & 1], base + step, n, lane);
+    cp_async_commit();
+    cp_async_wait_all_but_last();  // this round's copy has landed (this lane's pieces)
+    __syncwarp();                  // ... and every other lane's
+    const ScanStage& st = w.stage[r & 1];
+    // Not unrolled: the body inlines the whole resolve path (instruction cache).
+#pragma unroll 1
     for (int u = 0; u < kScanTiles; ++u) {
-      const unsigned long long i = base + 32ull * u + lane;
-      X[u] = i < n ? t.keys[i] : 0ull;
-    }
-#pragma unroll
-    for (int u = 0; u < kScanTiles; ++u) {
-      const unsigned long long i = base + 32ull * u + lane;
-      ex[u] = ((X[u] & f.occ) == f.occ) && ((X[u] & f.vir) == 0ull);
-      const bool de = ((X[u] & f.vir) == f.vir) && ((X[u] & f.occ) == 0ull);
-      lk[u] = i < n && (ex[u] || de);
-    }
-#pragma unroll
-    for (int u = 0; u < kScanTiles; ++u) {
-      const unsigned long long i = base + 32ull * u + lane;
-      c[u] = lk[u] ? t.amps[i] : 0.0;
-    }
-#pragma unroll
-    for (int u = 0; u < kScanTiles; ++u) {
-      const bool act = lk[u] && !is_dead(c[u]);
+      const int e = 32 * u + (int)lane;
+      const unsigned long long i = base + (unsigned long long)e;
+      bool act = false, ex = false;
+      unsigned long long X = 0ull;
+      double cX = 0.0;
+      if (i < n) {
+        X = st.X[e];
+        ex = ((X & f.occ) == f.occ) && ((X & f.vir) == 0ull);
+        const bool de = ((X & f.vir) == f.vir) && ((X & f.occ) == 0ull);
+        if (ex || de) {
+          cX = st.c[e];
+          act = !is_dead(cX);
+        }
+      }
       const unsigned int m = __ballot_sync(0xFFFFFFFFu, act);
       if (act) {
         const int p = qn + __popc(m & below_me);
-        q.i[p] = (base + 32ull * u + lane) | (ex[u] ? kExBit : 0ull);
-        q.X[p] = X[u];
-        q.c[p] = c[u];
+        q.i[p] = i | (ex ? kExBit : 0ull);
+        q.X[p] = X;
+        q.c[p] = cX;
       }
       qn += __popc(m);
+      if (qn >= 32) {
+        __syncwarp();
+        const int p = qn - 32 + (int)lane;
+        const unsigned long long qi = q.i[p];
+        const unsigned long long qX = q.X[p];
+        const double qc = q.c[p];
+        __syncwarp();
+        qn -= 32;
+        resolve(qi & ~kExBit, qX, qc, (qi & kExBit) != 0ull, true);
+      }
     }
-    while (qn >= 32) {
-      __syncwarp();
-      const int p = qn - 32 + (int)lane;
-      const unsigned long long qi = q.i[p];
-      const unsigned long long qX = q.X[p];
-      const double qc = q.c[p];
-      __syncwarp();
-      qn -= 32;
-      resolve(qi & ~kExBit, qX, qc, (qi & kExBit) != 0ull, true);
-    }
+    __syncwarp();  // every lane is done with this buffer before it is refilled
   }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");  // nothing left in flight
   __syncwarp();
   if (qn > 0) {
     const bool a = (int)lane < qn;
