@@ -309,7 +309,7 @@ def run_ours(args, prob):
         "gpu_launches": int(tot["kernel_launches"]),
         "counts_per_step": {k: int(tot[k] // n_steps) for k in (
             "rotations", "created", "dropped_new", "dropped_old", "cut", "scanned", "rebuilds", "tape_entries",
-            "sigma_probes", "sigma_hits", "reverse_pairs", "recompute_rotations")},
+            "sigma_probes", "sigma_hits", "reverse_pairs", "reverse_scanned", "recompute_rotations")},
         "roofline": roof,
         "kernels": {k: {x: v[x] for x in ("achieved", "frac", "launches", "avg_launch_ms", "total_ms")}
                     for k, v in kernels.items()},

@@ -41,6 +41,9 @@ __global__ void __launch_bounds__(kThreads) k_tape_reinsert(Table t, Tape tape, 
       t.amps[r.idx] = val;
       t.lam[r.idx] = 0.0;
       t.born[r.idx] = born;
+      // one dropped entry fewer (a warp-aggregated decrement)
+      cg::coalesced_group g = cg::coalesced_threads();
+      if (g.thread_rank() == 0) atomicAdd(&t.cnt->n_dead, 0ull - (unsigned long long)g.size());
     } else {
       insert_new(t, key, val, born, r.slot, true, true);
     }
@@ -48,25 +51,34 @@ __global__ void __launch_bounds__(kThreads) k_tape_reinsert(Table t, Tape tape, 
 }
 
 template <int G>
-__global__ void __launch_bounds__(kThreads) k_reverse(Table t, const Factor* __restrict__ factors, int k,
-                                                       unsigned int stamp, double* grad) {
-  __shared__ LinkScratch s_w[kThreads / 32];
+__global__ void __launch_bounds__(kStepThreads, 8) k_reverse(Table t, const Factor* __restrict__ factors, int k,
+                                                             unsigned int stamp, double* grad) {
+  __shared__ LinkScratch s_w[kStepThreads / 32];
   const Factor f = factors[k];
   const unsigned long long n = min(*((volatile unsigned long long*)&t.cnt->n_tail), t.cap_n);
   double acc = 0.0;
-  unsigned int pairs = 0;
-  for_each_linked(t, f, n, s_w[threadIdx.x >> 5],
-                  [&](unsigned long long i, unsigned long long X, double cX, bool ex, bool act) {
-                    Lookup r = findG<G>(t, X ^ (f.occ | f.vir), act, stamp);
-                    if (act) reverse_resolve(t, f, k, stamp, i, X, cX, ex, r, acc, pairs);
-                  });
+  unsigned int pairs = 0, kills = 0;
+  for_each_linked(
+      t, f, n, s_w[threadIdx.x >> 5], [&](unsigned long long i, bool act) { return act ? t.lam[i] : 0.0; },
+      [&](unsigned long long i, unsigned long long X, double cX, bool ex, double mu, bool act) {
+        if (act) reverse_resolve(t, f, k, stamp, i, X, cX, mu, ex, absent_lookup(), acc, pairs, kills);
+      },
+      [&](unsigned long long i, unsigned long long X, double cX, bool ex, bool act) {
+        const double mu = act ? t.lam[i] : 0.0;
+        Lookup r = findG<G>(t, X ^ (f.occ | f.vir), act, stamp);
+        if (act) reverse_resolve(t, f, k, stamp, i, X, cX, mu, ex, r, acc, pairs, kills);
+      });
   {
-    __shared__ unsigned long long s_pairs;
-    if (threadIdx.x == 0) s_pairs = 0;
+    // Entries this step removed (born at factor k) count as dropped, so the
+    // host can compact the table when they pile up.
+    __shared__ unsigned long long s_pairs, s_kills;
+    if (threadIdx.x == 0) s_pairs = s_kills = 0;
     __syncthreads();
     if (pairs) atomicAdd(&s_pairs, (unsigned long long)pairs);
+    if (kills) atomicAdd(&s_kills, (unsigned long long)kills);
     __syncthreads();
     if (threadIdx.x == 0 && s_pairs) atomicAdd(&t.cnt->rev_pairs, s_pairs);
+    if (threadIdx.x == 0 && s_kills) atomicAdd(&t.cnt->n_dead, s_kills);
   }
   const double b = block_sum(acc);
   if (threadIdx.x == 0) t.partials[blockIdx.x] = b;
@@ -76,6 +88,7 @@ __global__ void __launch_bounds__(kThreads) k_reverse(Table t, const Factor* __r
     s = block_sum(s);
     if (threadIdx.x == 0) {
       grad[k] = 2.0 * s;
+      t.cnt->rev_scanned += n;
       t.cnt->done = 0u;
     }
   }
@@ -93,16 +106,16 @@ cudaError_t launch_reverse(const Table& t, const Factor* factors, int k, unsigne
   if (!scan_aligned(t)) return cudaErrorMisalignedAddress;
   switch (probe_width) {
     case 2:
-      k_reverse<2><<<one_wave<k_reverse<2>, kThreads>(grid), kThreads, 0, st>>>(t, factors, k, stamp, grad);
+      k_reverse<2><<<one_wave<k_reverse<2>, kStepThreads>(grid), kStepThreads, 0, st>>>(t, factors, k, stamp, grad);
       break;
     case 4:
-      k_reverse<4><<<one_wave<k_reverse<4>, kThreads>(grid), kThreads, 0, st>>>(t, factors, k, stamp, grad);
+      k_reverse<4><<<one_wave<k_reverse<4>, kStepThreads>(grid), kStepThreads, 0, st>>>(t, factors, k, stamp, grad);
       break;
     case 8:
-      k_reverse<8><<<one_wave<k_reverse<8>, kThreads>(grid), kThreads, 0, st>>>(t, factors, k, stamp, grad);
+      k_reverse<8><<<one_wave<k_reverse<8>, kStepThreads>(grid), kStepThreads, 0, st>>>(t, factors, k, stamp, grad);
       break;
     default:
-      k_reverse<1><<<one_wave<k_reverse<1>, kThreads>(grid), kThreads, 0, st>>>(t, factors, k, stamp, grad);
+      k_reverse<1><<<one_wave<k_reverse<1>, kStepThreads>(grid), kStepThreads, 0, st>>>(t, factors, k, stamp, grad);
       break;
   }
   return cudaGetLastError();

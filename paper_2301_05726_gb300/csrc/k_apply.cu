@@ -45,10 +45,11 @@ __device__ __forceinline__ void block_add_counts(Counters* c, unsigned long long
 // this step carry this step's stamp, so a D-thread can tell "E was live when
 // the step began" (live or DEAD_NOW) from "E absent" (ABSENT or DEAD_OLD).
 template <int G, bool RECORD>
-__global__ void __launch_bounds__(kThreads, 4) k_forward(Table t, const Factor* __restrict__ factors, int k, double eps,
-                                                       unsigned int stamp, Tape tape, unsigned long long n_max) {
+__global__ void __launch_bounds__(kStepThreads, 8) k_forward(Table t, const Factor* __restrict__ factors, int k,
+                                                             double eps, unsigned int stamp, Tape tape,
+                                                             unsigned long long n_max) {
   __shared__ int s_skip;
-  __shared__ LinkScratch s_w[kThreads / 32];
+  __shared__ LinkScratch s_w[kStepThreads / 32];
   if (threadIdx.x == 0) s_skip = *((volatile int*)&t.cnt->stop_k) >= 0;
   __syncthreads();
   const bool skip = s_skip != 0;
@@ -56,11 +57,15 @@ __global__ void __launch_bounds__(kThreads, 4) k_forward(Table t, const Factor* 
   if (!skip) {
     const Factor f = factors[k];
     const unsigned long long n = min(*((volatile unsigned long long*)&t.cnt->n_scan), t.cap_n);
-    for_each_linked(t, f, n, s_w[threadIdx.x >> 5],
-                    [&](unsigned long long i, unsigned long long X, double cX, bool ex, bool act) {
-                      Lookup r = findG<G>(t, X ^ (f.occ | f.vir), act, stamp);
-                      if (act) forward_resolve<RECORD, true>(t, f, k, eps, stamp, tape, i, X, cX, ex, r, sc);
-                    });
+    for_each_linked(
+        t, f, n, s_w[threadIdx.x >> 5], [](unsigned long long, bool) { return 0.0; },
+        [&](unsigned long long i, unsigned long long X, double cX, bool ex, double, bool act) {
+          if (act) forward_resolve<RECORD, true>(t, f, k, eps, stamp, tape, i, X, cX, ex, absent_lookup(), sc);
+        },
+        [&](unsigned long long i, unsigned long long X, double cX, bool ex, bool act) {
+          Lookup r = findG<G>(t, X ^ (f.occ | f.vir), act, stamp);
+          if (act) forward_resolve<RECORD, true>(t, f, k, eps, stamp, tape, i, X, cX, ex, r, sc);
+        });
   }
   block_add_counts(t.cnt, sc.rot, sc.cre, sc.dnew, sc.dold, sc.dead_delta);
   if (t.entropy) {
@@ -202,19 +207,19 @@ static cudaError_t forward_g(const Table& t, const Factor* factors, int k, doubl
                              const Tape& tape, unsigned long long n_max, int pw, int grid, cudaStream_t st) {
   switch (pw) {
     case 2:
-      k_forward<2, RECORD><<<one_wave<k_forward<2, RECORD>, kThreads>(grid), kThreads, 0, st>>>(
+      k_forward<2, RECORD><<<one_wave<k_forward<2, RECORD>, kStepThreads>(grid), kStepThreads, 0, st>>>(
           t, factors, k, eps, stamp, tape, n_max);
       break;
     case 4:
-      k_forward<4, RECORD><<<one_wave<k_forward<4, RECORD>, kThreads>(grid), kThreads, 0, st>>>(
+      k_forward<4, RECORD><<<one_wave<k_forward<4, RECORD>, kStepThreads>(grid), kStepThreads, 0, st>>>(
           t, factors, k, eps, stamp, tape, n_max);
       break;
     case 8:
-      k_forward<8, RECORD><<<one_wave<k_forward<8, RECORD>, kThreads>(grid), kThreads, 0, st>>>(
+      k_forward<8, RECORD><<<one_wave<k_forward<8, RECORD>, kStepThreads>(grid), kStepThreads, 0, st>>>(
           t, factors, k, eps, stamp, tape, n_max);
       break;
     default:
-      k_forward<1, RECORD><<<one_wave<k_forward<1, RECORD>, kThreads>(grid), kThreads, 0, st>>>(
+      k_forward<1, RECORD><<<one_wave<k_forward<1, RECORD>, kStepThreads>(grid), kStepThreads, 0, st>>>(
           t, factors, k, eps, stamp, tape, n_max);
       break;
   }
@@ -313,16 +318,18 @@ namespace {
 // Read-only replay of factor f's partner lookups on the live table with
 // G-lane probes (the autotuner times it); the result only feeds a checksum.
 template <int G>
-__global__ void __launch_bounds__(256) k_probe_bench(Table t, Factor f, unsigned long long* sink) {
-  __shared__ LinkScratch s_w[256 / 32];
+__global__ void __launch_bounds__(kStepThreads) k_probe_bench(Table t, Factor f, unsigned long long* sink) {
+  __shared__ LinkScratch s_w[kStepThreads / 32];
   const unsigned long long n = min(*((volatile unsigned long long*)&t.cnt->n_tail), t.cap_n);
   const unsigned long long m = f.occ | f.vir;
   unsigned long long acc = 0;
-  for_each_linked(t, f, n, s_w[threadIdx.x >> 5],
-                  [&](unsigned long long, unsigned long long X, double, bool, bool act) {
-                    Lookup r = findG<G>(t, X ^ m, act, 0u);
-                    if (act) acc += r.idx + (unsigned long long)r.state;
-                  });
+  for_each_linked(
+      t, f, n, s_w[threadIdx.x >> 5], [](unsigned long long, bool) { return 0.0; },
+      [&](unsigned long long, unsigned long long, double, bool, double, bool) {},
+      [&](unsigned long long, unsigned long long X, double, bool, bool act) {
+        Lookup r = findG<G>(t, X ^ m, act, 0u);
+        if (act) acc += r.idx + (unsigned long long)r.state;
+      });
   acc = warp_sum_u64(acc);
   if ((threadIdx.x & 31u) == 0 && acc) atomicAdd(sink, acc);
 }
@@ -334,16 +341,16 @@ cudaError_t launch_probe_bench(const Table& t, const Factor& f, int probe_width,
   if (!scan_aligned(t)) return cudaErrorMisalignedAddress;
   switch (probe_width) {
     case 2:
-      k_probe_bench<2><<<grid, 256, 0, st>>>(t, f, sink);
+      k_probe_bench<2><<<grid, kStepThreads, 0, st>>>(t, f, sink);
       break;
     case 4:
-      k_probe_bench<4><<<grid, 256, 0, st>>>(t, f, sink);
+      k_probe_bench<4><<<grid, kStepThreads, 0, st>>>(t, f, sink);
       break;
     case 8:
-      k_probe_bench<8><<<grid, 256, 0, st>>>(t, f, sink);
+      k_probe_bench<8><<<grid, kStepThreads, 0, st>>>(t, f, sink);
       break;
     default:
-      k_probe_bench<1><<<grid, 256, 0, st>>>(t, f, sink);
+      k_probe_bench<1><<<grid, kStepThreads, 0, st>>>(t, f, sink);
       break;
   }
   return cudaGetLastError();

@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(kThreads) k_reverse_batch(const JobView* jobs,
   const unsigned long long nwarps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
   int cur = -1;
   double acc = 0.0;
-  unsigned int pairs = 0;
+  unsigned int pairs = 0, kills = 0;  // kills: not used by the batched sweep
   auto flush = [&](int j) {
     const double a = warp_sum(acc);
     const unsigned long long p = warp_sum_u64(pairs);
@@ -296,7 +296,7 @@ __global__ void __launch_bounds__(kThreads) k_reverse_batch(const JobView* jobs,
     const int k = js[j].k;
     const Factor f = jv.factors[k];
     const unsigned long long i = g - s_base[j] + lane;
-    reverse_entry<1>(jv.t, f, k, 0x80000000u | (unsigned int)k, i, i < js[j].n, acc, pairs);
+    reverse_entry<1>(jv.t, f, k, 0x80000000u | (unsigned int)k, i, i < js[j].n, acc, pairs, kills);
   }
   if (cur >= 0) flush(cur);
   __shared__ bool last;

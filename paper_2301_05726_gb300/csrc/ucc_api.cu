@@ -638,6 +638,9 @@ ucc_status run_energy(ucc_ctx* c, double* E, double* norm2) {
 // appends at most its own tape records; the host keeps an upper bound of the
 // stored count and compacts (keeping lam) or grows before a step could pass
 // the table's room.
+// Reverse steps between reads of the dropped-entry count.
+constexpr int kDeadCheck = 16;
+
 ucc_status reverse_segment(ucc_ctx* c, TableSet& s, int k0, int k1) {
   if (k1 <= k0) return UCC_OK;
   std::vector<unsigned long long> off(k1 - k0 + 1);
@@ -650,12 +653,23 @@ ucc_status reverse_segment(ucc_ctx* c, TableSet& s, int k0, int k1) {
   grid = std::max(grid, std::min(grid_full, 4));
   CUDA_TRY(cudaEventRecord(c->kev[0], c->stream));
   float kernel_ms = 0.f;
+  int since_check = 0;
   for (int k = k1 - 1; k >= k0; --k) {
     const unsigned int stamp = 0x80000000u | (unsigned int)k;
     const unsigned long long lo = off[k - k0], hi = off[k - k0 + 1];
     if (hi > c->tape_cap || lo > hi) return fail(UCC_ECUDA, "tape offsets out of range");
     const unsigned long long rec = hi - lo;
-    if (bound + rec > s.cur.cap_n || 4ull * (bound + rec) > 3ull * s.cur.n_slots) {
+    // Every kDeadCheck steps, read the counters: when a third of the stored
+    // entries are dropped (entries the sweep removed, and those the forward
+    // pass dropped since its last rebuild), compact, since every step scans
+    // them all.
+    bool compact = false;
+    if (++since_check >= kDeadCheck) {
+      since_check = 0;
+      UCC_TRY(read_counters(c, s));
+      compact = s.h_cnt->n_dead > 4096 && 3ull * s.h_cnt->n_dead > s.h_cnt->n_tail;
+    }
+    if (compact || bound + rec > s.cur.cap_n || 4ull * (bound + rec) > 3ull * s.cur.n_slots) {
       CUDA_TRY(cudaEventRecord(c->kev[1], c->stream));
       UCC_TRY(read_counters(c, s));
       float ms = 0.f;
@@ -690,6 +704,7 @@ ucc_status reverse_segment(ucc_ctx* c, TableSet& s, int k0, int k1) {
   CUDA_TRY(cudaEventElapsedTime(&ms, c->kev[0], c->kev[1]));
   c->stats.reverse_kernel_ms += kernel_ms + ms;
   c->stats.reverse_pairs += (long long)s.h_cnt->rev_pairs;
+  c->stats.reverse_scanned += (long long)s.h_cnt->rev_scanned;
   return UCC_OK;
 }
 

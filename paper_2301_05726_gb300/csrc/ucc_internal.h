@@ -41,6 +41,7 @@ struct Counters {
   unsigned long long scanned; // keys read by forward steps (sum of n_scan)
   unsigned long long sig_probes, sig_hits;  // hash probes / hits of the energy pass
   unsigned long long rev_pairs;             // pairs handled by the reverse sweep
+  unsigned long long rev_scanned;           // entries scanned by reverse steps (sum of n_tail)
   unsigned long long link_from, link_to;    // entries the last forward step appended without a hash slot
   unsigned int done;          // last-block arrival counter
   int stop_k;                 // first factor skipped: no room, or a cut is due (-1: none)

@@ -237,15 +237,15 @@ __device__ __forceinline__ void forward_entry(const Table& t, const Factor& f, i
 // The reverse step for one linked entry i (key X, live amplitude cX, ex = X
 // is the excited member) whose partner lookup is r.
 __device__ __forceinline__ void reverse_resolve(const Table& t, const Factor& f, int k, unsigned int stamp,
-                                                unsigned long long i, unsigned long long X, double cX, bool ex,
-                                                const Lookup& r, double& acc, unsigned int& pairs) {
+                                                unsigned long long i, unsigned long long X, double cX, double muX,
+                                                bool ex, const Lookup& r, double& acc, unsigned int& pairs,
+                                                unsigned int& kills) {
   const unsigned long long Y = X ^ (f.occ | f.vir);
   const bool partner_live = (r.state == ALIVE);
   if (!ex && (partner_live || r.state == DEAD_NOW)) return;  // E's thread owns the pair
   const unsigned long long E = ex ? X : Y;
   const int parity = (__popcll(E & f.pmask) + f.pconst) & 1;
   const double ss = neg_if(f.s, parity);
-  const double muX = t.lam[i];
   ++pairs;
   if (partner_live) {
     // Both members stored: (e, d) = U^T (e', d'), (lamE, lamD) = U^T (muE, muD).
@@ -263,61 +263,61 @@ __device__ __forceinline__ void reverse_resolve(const Table& t, const Factor& f,
     acc = fma(neg_if(lE, parity ^ 1), d0, acc);
     if (t.born[i] == (unsigned int)k) {
       t.amps[i] = dead_value(stamp);
+      ++kills;
     } else {
       t.amps[i] = e0;
       t.lam[i] = lE;
     }
     if (t.born[r.idx] == (unsigned int)k) {
       t.amps[r.idx] = dead_value(stamp);
+      ++kills;
     } else {
       t.amps[r.idx] = d0;
       t.lam[r.idx] = lD;
     }
-  } else if (ex) {
-    // E alone: D was absent before the factor, c_E' = cos c_E.
-    const double e0 = __dmul_rn(cX, f.ic);
-    const double lE = __dmul_rn(f.c, muX);
-    const double lD = neg_if(__dmul_rn(ss, muX), 1);
-    acc = fma(neg_if(lD, parity), e0, acc);
-    t.amps[i] = e0;
-    t.lam[i] = lE;
   } else {
-    // D alone: E was absent before the factor, c_D' = cos c_D.
-    const double d0 = __dmul_rn(cX, f.ic);
-    const double lD = __dmul_rn(f.c, muX);
-    const double lE = __dmul_rn(ss, muX);
-    acc = fma(neg_if(lE, parity ^ 1), d0, acc);
-    t.amps[i] = d0;
-    t.lam[i] = lD;
+    // X alone: its partner was absent before the factor (and is not stored
+    // after it), so c_X' = cos c_X.  For X = E the partner's adjoint is
+    // lam_D = -s mu_E and the term s lam_D psi_E; for X = D it is
+    // lam_E = s mu_D and the term -s lam_E psi_D: both are -s (ss mu_X) psi_X.
+    const double x0 = __dmul_rn(cX, f.ic);
+    acc = fma(neg_if(__dmul_rn(ss, muX), parity ^ 1), x0, acc);
+    t.amps[i] = x0;
+    t.lam[i] = __dmul_rn(f.c, muX);
   }
 }
 
 template <int G>
 __device__ __forceinline__ void reverse_entry(const Table& t, const Factor& f, int k, unsigned int stamp,
-                                              unsigned long long i, bool in_range, double& acc, unsigned int& pairs) {
+                                              unsigned long long i, bool in_range, double& acc, unsigned int& pairs,
+                                              unsigned int& kills) {
   unsigned long long X;
   double cX;
   bool ex;
   const bool act = linked_entry(t, f, i, in_range, X, cX, ex);
   Lookup r = findG<G>(t, X ^ (f.occ | f.vir), act, stamp);
   if (!act) return;
-  reverse_resolve(t, f, k, stamp, i, X, cX, ex, r, acc, pairs);
+  reverse_resolve(t, f, k, stamp, i, X, cX, t.lam[i], ex, r, acc, pairs, kills);
 }
 
-// Per-warp queue of linked entries in shared memory.  Only a fraction of the
-// stored determinants belong to a given factor's pairs, so a warp that
-// resolved its 32 scanned entries in place would run the pair arithmetic (on
-// the narrow FP64 pipe, where a warp instruction costs the same with one
-// lane as with 32) and the partner probes on mostly idle lanes.  Instead the
-// lanes append the linked entries they find, and while 32 or more are queued
-// the warp resolves them 32 at a time.  The order in which a step's pairs are
-// resolved does not matter: ownership and the dropped-entry stamps decide
-// everything from the state at the start of the step.
-// A warp scans rounds of kScanTiles tiles of 32 entries.  The keys and
-// amplitudes of its next round are copied into shared memory (cp.async, two
-// buffers per warp) while it resolves the current one, so the scan's load
-// latency overlaps the pair work.
-constexpr int kScanTiles = 4;
+// Per-warp queues of linked entries in shared memory.  Only a fraction of
+// the stored determinants belong to a given factor's pairs, and for most of
+// those the existence filter proves the partner absent.  A warp that resolved
+// its 32 scanned entries in place would run the pair arithmetic (on the narrow
+// FP64 pipe, where a warp instruction costs the same with one lane as with 32)
+// and the partner probes on mostly idle lanes, and every lane would wait for
+// the slowest lane's probe chain.  Instead the lanes append the linked entries
+// they find to a queue; each 32 taken from it test their partners' filter
+// bits together, the lanes whose partner is proved absent resolve at once
+// (no slot probe), and the rest move to a probe queue that is resolved, slot
+// probe first, 32 at a time.  The order in which a step's pairs are resolved
+// does not matter: ownership and the dropped-entry stamps decide everything
+// from the state at the start of the step.
+//
+// The keys and amplitudes of a warp's next round of kScanTiles tiles are
+// copied into shared memory (cp.async, two buffers per warp) while it works on
+// the current one, so the scan's load latency overlaps the pair work.
+constexpr int kScanTiles = 2;
 constexpr int kRound = 32 * kScanTiles;
 constexpr int kQueue = 64;
 constexpr unsigned long long kExBit = 1ull << 63;
@@ -336,8 +336,14 @@ struct __align__(16) ScanStage {
 // Per-warp shared memory of for_each_linked.
 struct LinkScratch {
   ScanStage stage[2];
-  LinkQueue q;
+  LinkQueue linked;  // linked entries, before the filter test
+  LinkQueue probe;   // linked entries whose partner may be stored
 };
+
+// Threads per block of the kernels built on for_each_linked: with four warps
+// per block, the eight blocks an SM holds at 64 registers per thread also fit
+// its shared memory with their LinkScratch.
+constexpr int kStepThreads = 128;
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src_bytes) {
   const unsigned int s = (unsigned int)__cvta_generic_to_shared(smem);
@@ -369,20 +375,91 @@ __device__ __forceinline__ void stage_round(const Table& t, ScanStage& st, unsig
   }
 }
 
-// Scan entries [0, n) in warp-strided rounds of kRound entries and call
-// resolve(i, X, cX, ex, active) on full warps of linked entries (a partial
-// warp at the end).  Every lane of the warp calls this; resolve is called by
-// all lanes together.
-template <class Resolve>
+// A lookup result for a key the existence filter proved absent.
+__device__ __forceinline__ Lookup absent_lookup() {
+  Lookup r;
+  r.state = ABSENT;
+  r.slot = 0ull;
+  r.idx = 0ull;
+  r.amp = 0.0;
+  return r;
+}
+
+// Append (i, X, c, ex) of the active lanes (ballot m) to queue q at qn.
+__device__ __forceinline__ void enqueue(LinkQueue& q, int qn, unsigned int m, unsigned int below_me, bool act,
+                                        unsigned long long i, unsigned long long X, double c, bool ex) {
+  if (act) {
+    const int p = qn + __popc(m & below_me);
+    q.i[p] = i | (ex ? kExBit : 0ull);
+    q.X[p] = X;
+    q.c[p] = c;
+  }
+}
+
+// Pop the last 32 entries of a queue holding qn >= 32 into the lanes and call
+// f(i, X, c, ex, true).
+template <class F>
+__device__ __forceinline__ void drain32(LinkQueue& q, int& qn, unsigned int lane, F& f) {
+  __syncwarp();
+  const int p = qn - 32 + (int)lane;
+  const unsigned long long qi = q.i[p];
+  const unsigned long long qX = q.X[p];
+  const double qc = q.c[p];
+  __syncwarp();
+  qn -= 32;
+  f(qi & ~kExBit, qX, qc, (qi & kExBit) != 0ull, true);
+}
+
+// The qn < 32 entries left in a queue (lanes past qn inactive); empties it.
+template <class F>
+__device__ __forceinline__ void drain_rest(LinkQueue& q, int& qn, unsigned int lane, F& f) {
+  __syncwarp();
+  const bool a = (int)lane < qn;
+  unsigned long long qi = 0ull, qX = 0ull;
+  double qc = 0.0;
+  if (a) {
+    qi = q.i[lane];
+    qX = q.X[lane];
+    qc = q.c[lane];
+  }
+  __syncwarp();
+  qn = 0;
+  f(qi & ~kExBit, qX, qc, (qi & kExBit) != 0ull, a);
+}
+
+// Scan entries [0, n) in warp-strided rounds of kRound entries and resolve
+// every live linked entry: lone(i, X, cX, ex, aux, active) when the filter
+// proves its partner absent, probe(i, X, cX, ex, active) otherwise.  aux =
+// pre(i, active) is loaded together with the filter word, so a lone entry
+// that needs one more value of its own (the adjoint, in the reverse sweep)
+// waits for a single round trip.  Every lane of the warp calls this; lone and
+// probe are called by all lanes together.
+template <class Pre, class Lone, class Probe>
 __device__ __forceinline__ void for_each_linked(const Table& t, const Factor& f, unsigned long long n,
-                                                LinkScratch& w, Resolve resolve) {
+                                                LinkScratch& w, Pre pre, Lone lone, Probe probe) {
   const unsigned int lane = threadIdx.x & 31u;
   const unsigned int below_me = (1u << lane) - 1u;
   const unsigned long long warp = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const unsigned long long nwarps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
   const unsigned long long step = nwarps * (unsigned long long)kRound;
-  LinkQueue& q = w.q;
-  int qn = 0;  // warp-uniform queue length, < 32 between tiles
+  const unsigned long long m = f.occ | f.vir;
+  int nl = 0, np = 0;  // warp-uniform lengths of the linked and probe queues
+  // Up to 32 linked entries: the partner's filter bit sends each lane to lone
+  // at once or onto the probe queue.
+  auto split = [&](unsigned long long i, unsigned long long X, double c, bool ex, bool act) {
+    const double aux = pre(i, act);
+    bool maybe = act;
+    if (act && t.filt) {
+      const unsigned long long b = ((X ^ m) * kFilterMul) >> t.filt_shift;
+      maybe = (t.filt[b >> 5] >> (b & 31u)) & 1u;
+    }
+    const bool pr = act && maybe;
+    const unsigned int mp = __ballot_sync(0xFFFFFFFFu, pr);
+    enqueue(w.probe, np, mp, below_me, pr, i, X, c, ex);
+    np += __popc(mp);
+    lone(i, X, c, ex, aux, act && !maybe);
+    if (np >= 32) drain32(w.probe, np, lane, probe);
+  };
   unsigned long long base = warp * (unsigned long long)kRound;
   if (base < n) stage_round(t, w.stage[0], base, n, lane);
   cp_async_commit();
@@ -393,7 +470,7 @@ __device__ __forceinline__ void for_each_linked(const Table& t, const Factor& f,
     cp_async_wait_all_but_last();  // this round's copy has landed (this lane's pieces)
     __syncwarp();                  // ... and every other lane's
     const ScanStage& st = w.stage[r & 1];
-    // Not unrolled: the body inlines the whole resolve path (instruction cache).
+    // Not unrolled: the body inlines the resolve paths (instruction cache).
 #pragma unroll 1
     for (int u = 0; u < kScanTiles; ++u) {
       const int e = 32 * u + (int)lane;
@@ -410,40 +487,16 @@ __device__ __forceinline__ void for_each_linked(const Table& t, const Factor& f,
           act = !is_dead(cX);
         }
       }
-      const unsigned int m = __ballot_sync(0xFFFFFFFFu, act);
-      if (act) {
-        const int p = qn + __popc(m & below_me);
-        q.i[p] = i | (ex ? kExBit : 0ull);
-        q.X[p] = X;
-        q.c[p] = cX;
-      }
-      qn += __popc(m);
-      if (qn >= 32) {
-        __syncwarp();
-        const int p = qn - 32 + (int)lane;
-        const unsigned long long qi = q.i[p];
-        const unsigned long long qX = q.X[p];
-        const double qc = q.c[p];
-        __syncwarp();
-        qn -= 32;
-        resolve(qi & ~kExBit, qX, qc, (qi & kExBit) != 0ull, true);
-      }
+      const unsigned int ml = __ballot_sync(0xFFFFFFFFu, act);
+      enqueue(w.linked, nl, ml, below_me, act, i, X, cX, ex);
+      nl += __popc(ml);
+      if (nl >= 32) drain32(w.linked, nl, lane, split);
     }
     __syncwarp();  // every lane is done with this buffer before it is refilled
   }
   asm volatile("cp.async.wait_all;\n" ::: "memory");  // nothing left in flight
-  __syncwarp();
-  if (qn > 0) {
-    const bool a = (int)lane < qn;
-    unsigned long long qi = 0ull, qX = 0ull;
-    double qc = 0.0;
-    if (a) {
-      qi = q.i[lane];
-      qX = q.X[lane];
-      qc = q.c[lane];
-    }
-    resolve(qi & ~kExBit, qX, qc, (qi & kExBit) != 0ull, a);
-  }
+  if (nl > 0) drain_rest(w.linked, nl, lane, split);
+  if (np > 0) drain_rest(w.probe, np, lane, probe);
 }
 
 constexpr int kMaxSpin = 32;                          // spin-orbitals of one spin
