@@ -273,7 +273,9 @@ def run_ours(args, prob):
     # per stored determinant: key + amplitude read, sigma written; per connected stored pair (visited once):
     # the partner amplitude read and one sigma update
     sig_bytes = 24.0 * tot["n_det"] + 16.0 * tot["sigma_hits"]
-    rev_bytes = 80.0 * tot["reverse_pairs"]
+    # per pair as in the forward step plus lam of both members; the scan term counts the entries of psi_k
+    # (the forward step's scan), not the dropped entries the sweep carries until it compacts
+    rev_bytes = 8.0 * tot["scanned"] + 80.0 * tot["reverse_pairs"]
     kernels = {
         "k_forward": _roofline("k_forward", fwd_bytes, tot["forward_kernel_ms"], tot["forward_launches"], hbm,
                                peak_kind),
