@@ -31,7 +31,7 @@ __global__ void __launch_bounds__(256) k_sigma_zero(Table t) {
     t.sigma[i] = 0.0;
 }
 
-__global__ void __launch_bounds__(kThreads) k_sigma(Table t, Integrals in) {
+__global__ void __launch_bounds__(kThreads, 4) k_sigma(Table t, Integrals in) {
   __shared__ LowerLists lists[kWarps];
   const int w = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;

@@ -713,15 +713,20 @@ __device__ __forceinline__ double sigma_lower(const Table& t, const Integrals& i
   const unsigned long long emask = ~I & all;
   // empty spin-orbitals of spin sp below orbital m
   auto empty_below = [&](int sp, int m) { return __popcll(emask & (sp ? kBetaBits : kAlphaBits) & below(m)); };
-  if (lane == 0) {
-    for (int sp = 0; sp < 2; ++sp) L.n_occ[sp] = L.n_emp[sp] = 0;
-    for (int p = 0; p < in.n_so; ++p) {
-      const int sp = p & 1;
-      if ((I >> p) & 1ull)
-        L.occ[sp][L.n_occ[sp]++] = (unsigned char)p;
-      else
-        L.emp[sp][L.n_emp[sp]++] = (unsigned char)p;
-    }
+  // Occupied and empty lists by spin, ascending: lanes over the orbitals, each
+  // placed at the count of same-kind, same-spin orbitals below it.
+  for (int p = lane; p < in.n_so; p += 32) {
+    const int sp = p & 1;
+    const unsigned long long spin = sp ? kBetaBits : kAlphaBits;
+    if ((I >> p) & 1ull)
+      L.occ[sp][__popcll(I & spin & below(p))] = (unsigned char)p;
+    else
+      L.emp[sp][__popcll(emask & spin & below(p))] = (unsigned char)p;
+  }
+  if (lane < 2) {
+    const unsigned long long spin = lane ? kBetaBits : kAlphaBits;
+    L.n_occ[lane] = __popcll(I & all & spin);
+    L.n_emp[lane] = __popcll(emask & spin);
   }
   __syncwarp();
   for (int sp = 0; sp < 2; ++sp) {
