@@ -450,8 +450,8 @@ __device__ __forceinline__ void for_each_linked(const Table& t, const Factor& f,
     const double aux = pre(i, act);
     bool maybe = act;
     if (act && t.filt) {
-      const unsigned long long b = ((X ^ m) * kFilterMul) >> t.filt_shift;
-      maybe = (t.filt[b >> 5] >> (b & 31u)) & 1u;
+      const unsigned long long h = (X ^ m) * kFilterMul;
+      maybe = filter_hit(t, t.filt[filter_word(t, h)], h);
     }
     const bool pr = act && maybe;
     const unsigned int mp = __ballot_sync(0xFFFFFFFFu, pr);
@@ -590,7 +590,7 @@ __device__ __forceinline__ void probe_connections(const Table& t, int count, int
                                                   unsigned long long& hits) {
   for (int u0 = lane; u0 < count; u0 += 32 * kV) {
     unsigned long long J[kV];
-    unsigned int w[kV];
+    bool w[kV];
 #pragma unroll
     for (int v = 0; v < kV; ++v) {
       const int u = u0 + 32 * v;
@@ -599,13 +599,13 @@ __device__ __forceinline__ void probe_connections(const Table& t, int count, int
 #pragma unroll
     for (int v = 0; v < kV; ++v) {
       const int u = u0 + 32 * v;
-      w[v] = 0u;
+      w[v] = false;
       if (u < count) {
         if (t.filt) {
-          const unsigned long long b = (J[v] * kFilterMul) >> t.filt_shift;
-          w[v] = (t.filt[b >> 5] >> (b & 31u)) & 1u;
+          const unsigned long long h = J[v] * kFilterMul;
+          w[v] = filter_hit(t, t.filt[filter_word(t, h)], h);
         } else {
-          w[v] = 1u;
+          w[v] = true;
         }
       }
     }
@@ -663,7 +663,7 @@ __device__ __forceinline__ void probe_lower(const Table& t, int count, int lane,
                                             double& part, unsigned long long& probes, unsigned long long& hits) {
   for (int u0 = lane; u0 < count; u0 += 32 * kV) {
     unsigned long long J[kV];
-    unsigned int w[kV];
+    bool w[kV];
 #pragma unroll
     for (int v = 0; v < kV; ++v) {
       const int u = u0 + 32 * v;
@@ -672,13 +672,13 @@ __device__ __forceinline__ void probe_lower(const Table& t, int count, int lane,
 #pragma unroll
     for (int v = 0; v < kV; ++v) {
       const int u = u0 + 32 * v;
-      w[v] = 0u;
+      w[v] = false;
       if (u < count) {
         if (t.filt) {
-          const unsigned long long b = (J[v] * kFilterMul) >> t.filt_shift;
-          w[v] = (t.filt[b >> 5] >> (b & 31u)) & 1u;
+          const unsigned long long h = J[v] * kFilterMul;
+          w[v] = filter_hit(t, t.filt[filter_word(t, h)], h);
         } else {
-          w[v] = 1u;
+          w[v] = true;
         }
       }
     }
