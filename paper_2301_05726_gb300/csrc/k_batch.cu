@@ -17,6 +17,9 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
+// The energy kernel's blocks: four warps keep the job table and the warps'
+// connection lists within the static shared-memory limit.
+constexpr int kSigmaWarps = 4;
 
 __device__ __forceinline__ int job_of(const unsigned long long* base, int n_jobs, unsigned long long g) {
   int lo = 0, hi = n_jobs - 1;  // largest j with base[j] <= g
@@ -171,16 +174,16 @@ __global__ void __launch_bounds__(kThreads) k_sigma_zero_batch(const JobView* jo
 // sigma and the energy sums of every job; one warp per stored entry, each
 // connected stored pair of a job visited once from its larger key (the
 // single-problem energy kernel's lower-triangle pass).
-__global__ void __launch_bounds__(kThreads) k_sigma_batch(const JobView* jobs, JobState* js, int n_jobs,
-                                                           BatchHeader* bh) {
+__global__ void __launch_bounds__(kSigmaWarps * 32) k_sigma_batch(const JobView* jobs, JobState* js,
+                                                                   int n_jobs, BatchHeader* bh) {
   __shared__ unsigned long long s_base[kMaxBatchJobs + 1];
-  __shared__ LowerLists lists[kWarps];
+  __shared__ LowerLists lists[kSigmaWarps];
   load_bases(js, n_jobs, bh, s_base);
   const unsigned long long total = s_base[n_jobs];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   LowerLists& L = lists[w];
-  const unsigned long long gw = (unsigned long long)blockIdx.x * kWarps + w;
-  const unsigned long long nw = (unsigned long long)gridDim.x * kWarps;
+  const unsigned long long gw = (unsigned long long)blockIdx.x * kSigmaWarps + w;
+  const unsigned long long nw = (unsigned long long)gridDim.x * kSigmaWarps;
   int cur = -1;
   double se = 0.0, sn = 0.0;
   unsigned long long probes = 0, hits = 0;
@@ -339,7 +342,7 @@ cudaError_t launch_forward_batch(const JobView* jobs, JobState* js, int n_jobs, 
 cudaError_t launch_sigma_batch(const JobView* jobs, JobState* js, int n_jobs, BatchHeader* bh, int grid,
                                cudaStream_t st) {
   k_sigma_zero_batch<<<grid, kThreads, 0, st>>>(jobs, js, n_jobs, bh);
-  k_sigma_batch<<<grid, kThreads, 0, st>>>(jobs, js, n_jobs, bh);
+  k_sigma_batch<<<2 * grid, kSigmaWarps * 32, 0, st>>>(jobs, js, n_jobs, bh);
   return cudaGetLastError();
 }
 

@@ -502,13 +502,6 @@ __device__ __forceinline__ void for_each_linked(const Table& t, const Factor& f,
 constexpr int kMaxSpin = 32;                          // spin-orbitals of one spin
 constexpr int kMaxPairs = kMaxSpin * (kMaxSpin - 1) / 2;  // same-spin empty pairs
 
-struct WarpLists {
-  unsigned char occ[2][kMaxSpin];
-  unsigned char emp[2][kMaxSpin];
-  int n_occ[2], n_emp[2];
-  unsigned short pairs[2][kMaxPairs];  // same-spin empty pairs (r | s << 8), r < s
-  int n_pairs[2];
-};
 
 __device__ __forceinline__ unsigned long long below(int p) { return (1ull << p) - 1ull; }
 
@@ -542,87 +535,13 @@ __device__ __forceinline__ int single_parity(unsigned long long I, int p, int r)
   return (__popcll(I & (below(p) ^ below(r))) + (p < r)) & 1;
 }
 
-__device__ __forceinline__ bool lookup_live(const Table& t, unsigned long long key, double* amp) {
-  if (!filter_maybe(t, key)) return false;
-  unsigned long long h = home_slot(t, key);
-  for (int step = 0; step < MAX_PROBE; ++step) {
-    const Slot s = t.slots[h];
-    if (s.key == key) {
-      const double a = t.amps[s.idx];
-      if (is_dead(a)) return false;
-      *amp = a;
-      return true;
-    }
-    if (s.key == 0ull) return false;
-    h = (h + 1) & t.slot_mask;
-  }
-  raise_error(t.cnt, ERR_PROBE_BOUND);
-  return false;
-}
 
-// The slot probe of lookup_live, for a key the filter did not exclude.
-__device__ __forceinline__ bool probe_live(const Table& t, unsigned long long key, double* amp) {
-  unsigned long long h = home_slot(t, key);
-  for (int step = 0; step < MAX_PROBE; ++step) {
-    const Slot s = t.slots[h];
-    if (s.key == key) {
-      const double a = t.amps[s.idx];
-      if (is_dead(a)) return false;
-      *amp = a;
-      return true;
-    }
-    if (s.key == 0ull) return false;
-    h = (h + 1) & t.slot_mask;
-  }
-  raise_error(t.cnt, ERR_PROBE_BOUND);
-  return false;
-}
 
-// Lanes walk connections u = lane, lane + 32, ... < count, kV at a time: the
-// kV connection keys and their filter words are all requested before any is
-// tested, so each lane keeps kV independent loads in flight.  key_of(u) gives
-// the connected determinant, elem(u) its matrix element; hits add elem * c_J.
-constexpr int kV = 4;
+// Connections a lane tests per round of the energy pass (filter words in flight).
+constexpr int kV = 2;
 
-template <class KeyOf, class Elem>
-__device__ __forceinline__ void probe_connections(const Table& t, int count, int lane, KeyOf key_of, Elem elem,
-                                                  double& part, unsigned long long& probes,
-                                                  unsigned long long& hits) {
-  for (int u0 = lane; u0 < count; u0 += 32 * kV) {
-    unsigned long long J[kV];
-    bool w[kV];
-#pragma unroll
-    for (int v = 0; v < kV; ++v) {
-      const int u = u0 + 32 * v;
-      J[v] = u < count ? key_of(u) : 0ull;
-    }
-#pragma unroll
-    for (int v = 0; v < kV; ++v) {
-      const int u = u0 + 32 * v;
-      w[v] = false;
-      if (u < count) {
-        if (t.filt) {
-          const unsigned long long h = J[v] * kFilterMul;
-          w[v] = filter_hit(t, t.filt[filter_word(t, h)], h);
-        } else {
-          w[v] = true;
-        }
-      }
-    }
-#pragma unroll
-    for (int v = 0; v < kV; ++v) {
-      const int u = u0 + 32 * v;
-      if (u >= count) continue;
-      ++probes;
-      double cJ;
-      if (!w[v] || !probe_live(t, J[v], &cJ)) continue;
-      ++hits;
-      part += elem(u, J[v]) * cJ;
-    }
-  }
-}
-
-// The slot probe of lookup_live, also giving the entry index of a live hit.
+// Slot probe for a key the filter did not exclude: whether it is stored and
+// live, with its amplitude and entry index.
 __device__ __forceinline__ bool probe_live_at(const Table& t, unsigned long long key, double* amp,
                                               unsigned long long* idx) {
   unsigned long long h = home_slot(t, key);
@@ -653,27 +572,43 @@ struct LowerLists {
   int n_occ[2], n_emp[2];
   unsigned short pairs[2][kMaxPairs];       // same-spin empty pairs (r | s << 8), r < s, ordered by s
   unsigned short opp[kMaxSpin * kMaxSpin];  // (r alpha | s beta << 8), ordered by max(r, s)
+  unsigned long long hitJ[32 * (kV + 1)];   // connections whose filter word holds all their bits
+  unsigned int hitCode[32 * (kV + 1)];      // and their excitation (connection_code)
 };
 
-// Like probe_connections, for the connections J < I of a lower-triangle
-// pass: a hit adds <I|H|J> c_J to the lane's share of sigma_I and the
-// transposed term <J|H|I> c_I (H is real symmetric) to sigma_J in memory.
-template <class KeyOf, class Elem>
-__device__ __forceinline__ void probe_lower(const Table& t, int count, int lane, double cI, KeyOf key_of, Elem elem,
-                                            double& part, unsigned long long& probes, unsigned long long& hits) {
-  for (int u0 = lane; u0 < count; u0 += 32 * kV) {
+// An excitation of I packed in 26 bits: kind (0 single p -> r, 1 double
+// p, q -> r, s) and the four spin-orbital indices.
+__device__ __forceinline__ unsigned int connection_code(int kind, int p, int q, int r, int s) {
+  return (unsigned int)kind | ((unsigned int)p << 2) | ((unsigned int)q << 8) | ((unsigned int)r << 14) |
+         ((unsigned int)s << 20);
+}
+
+// The connections J < I of the lower-triangle energy pass, with the warp in
+// lock step (count is warp-uniform): the lanes test kV filter words each and
+// queue the connections whose word holds all their bits (key_of(u) gives J,
+// code_of(u) its excitation); whenever 32 or more are queued after a round,
+// resolve_hits takes them 32 at a time, so the slot probes of rare hits run
+// on full warps instead of stalling the loop once per hit.  The queue holds
+// fewer than 32 between rounds.
+template <class KeyOf, class CodeOf, class Resolve>
+__device__ __forceinline__ void probe_lower(const Table& t, LowerLists& L, int& qn, int count, int lane,
+                                            KeyOf key_of, CodeOf code_of, Resolve resolve_hits,
+                                            unsigned long long& probes) {
+  const unsigned int below_me = (1u << lane) - 1u;
+  for (int u0 = 0; u0 < count; u0 += 32 * kV) {
     unsigned long long J[kV];
     bool w[kV];
 #pragma unroll
     for (int v = 0; v < kV; ++v) {
-      const int u = u0 + 32 * v;
+      const int u = u0 + 32 * v + lane;
       J[v] = u < count ? key_of(u) : 0ull;
     }
 #pragma unroll
     for (int v = 0; v < kV; ++v) {
-      const int u = u0 + 32 * v;
+      const int u = u0 + 32 * v + lane;
       w[v] = false;
       if (u < count) {
+        ++probes;
         if (t.filt) {
           const unsigned long long h = J[v] * kFilterMul;
           w[v] = filter_hit(t, t.filt[filter_word(t, h)], h);
@@ -684,17 +619,16 @@ __device__ __forceinline__ void probe_lower(const Table& t, int count, int lane,
     }
 #pragma unroll
     for (int v = 0; v < kV; ++v) {
-      const int u = u0 + 32 * v;
-      if (u >= count) continue;
-      ++probes;
-      double cJ;
-      unsigned long long j;
-      if (!w[v] || !probe_live_at(t, J[v], &cJ, &j)) continue;
-      ++hits;
-      const double h = elem(u, J[v]);
-      part += h * cJ;
-      atomicAdd(&t.sigma[j], h * cI);
+      const int u = u0 + 32 * v + lane;
+      const unsigned int m = __ballot_sync(0xFFFFFFFFu, w[v]);
+      if (w[v]) {
+        const int p = qn + __popc(m & below_me);
+        L.hitJ[p] = J[v];
+        L.hitCode[p] = code_of(u);
+      }
+      qn += __popc(m);
     }
+    while (qn >= 32) resolve_hits(32);
   }
 }
 
@@ -770,23 +704,48 @@ __device__ __forceinline__ double sigma_lower(const Table& t, const Integrals& i
   diag = d;
 
   double part = 0.0;
+  int qn = 0;  // warp-uniform length of the hit queue
+  // <J|H|I> for the queued excitation code of J = tau I.
+  auto elem = [&](unsigned int code) {
+    const int p = (code >> 2) & 63, q = (code >> 8) & 63, r = (code >> 14) & 63, s = (code >> 20) & 63;
+    if ((code & 3u) == 0u) {
+      double v = h_so(in, r, p);
+      for (int sk = 0; sk < 2; ++sk)
+        for (int y = 0; y < L.n_occ[sk]; ++y) {
+          const int kk = L.occ[sk][y];
+          if (kk != p) v += anti(in, r, kk, p, kk);
+        }
+      return single_parity(I, p, r) ? -v : v;
+    }
+    const double v = anti(in, r, s, p, q);
+    return double_parity(I, p, q, r, s) ? -v : v;
+  };
+  // The last `take` queued connections, one per lane: probe the slot array;
+  // on a live hit add <I|H|J> c_J here and the transposed term to sigma_J.
+  auto resolve_hits = [&](int take) {
+    __syncwarp();
+    const bool a = lane < take;
+    const int pidx = qn - take + lane;
+    const unsigned long long J = a ? L.hitJ[pidx] : 0ull;
+    const unsigned int code = a ? L.hitCode[pidx] : 0u;
+    __syncwarp();
+    qn -= take;
+    double cJ;
+    unsigned long long j;
+    if (a && probe_live_at(t, J, &cJ, &j)) {
+      ++hits;
+      const double h = elem(code);
+      part += h * cJ;
+      atomicAdd(&t.sigma[j], h * cI);
+    }
+  };
   // Singles p -> r, same spin, r < p.
   for (int sp = 0; sp < 2; ++sp)
     for (int x = 0; x < L.n_occ[sp]; ++x) {
       const int p = L.occ[sp][x];
       probe_lower(
-          t, empty_below(sp, p), lane, cI, [&](int u) { return I ^ ((1ull << p) | (1ull << L.emp[sp][u])); },
-          [&](int u, unsigned long long) {
-            const int r = L.emp[sp][u];
-            double v = h_so(in, r, p);
-            for (int sk = 0; sk < 2; ++sk)
-              for (int y = 0; y < L.n_occ[sk]; ++y) {
-                const int kk = L.occ[sk][y];
-                if (kk != p) v += anti(in, r, kk, p, kk);
-              }
-            return single_parity(I, p, r) ? -v : v;
-          },
-          part, probes, hits);
+          t, L, qn, empty_below(sp, p), lane, [&](int u) { return I ^ ((1ull << p) | (1ull << L.emp[sp][u])); },
+          [&](int u) { return connection_code(0, p, 0, L.emp[sp][u], 0); }, resolve_hits, probes);
     }
   // Doubles, same spin: holes p < q, particles r < s < q.
   for (int sp = 0; sp < 2; ++sp) {
@@ -797,18 +756,16 @@ __device__ __forceinline__ double sigma_lower(const Table& t, const Integrals& i
         const unsigned long long hole = (1ull << p) | (1ull << q);
         const int y0 = empty_below(sp, q);
         probe_lower(
-            t, y0 * (y0 - 1) / 2, lane, cI,
+            t, L, qn, y0 * (y0 - 1) / 2, lane,
             [&](int u) {
               const unsigned short pr = L.pairs[sp][u];
               return I ^ (hole | (1ull << (pr & 0xFF)) | (1ull << (pr >> 8)));
             },
-            [&](int u, unsigned long long) {
+            [&](int u) {
               const unsigned short pr = L.pairs[sp][u];
-              const int r = pr & 0xFF, s = pr >> 8;
-              const double v = anti(in, r, s, p, q);
-              return double_parity(I, p, q, r, s) ? -v : v;
+              return connection_code(1, p, q, pr & 0xFF, pr >> 8);
             },
-            part, probes, hits);
+            resolve_hits, probes);
       }
   }
   // Doubles, opposite spin: holes p alpha, q beta; particles r alpha, s beta
@@ -819,133 +776,21 @@ __device__ __forceinline__ double sigma_lower(const Table& t, const Integrals& i
       const int m = p > q ? p : q;
       const unsigned long long hole = (1ull << p) | (1ull << q);
       probe_lower(
-          t, empty_below(0, m) * empty_below(1, m), lane, cI,
+          t, L, qn, empty_below(0, m) * empty_below(1, m), lane,
           [&](int u) {
             const unsigned short pr = L.opp[u];
             return I ^ (hole | (1ull << (pr & 0xFF)) | (1ull << (pr >> 8)));
           },
-          [&](int u, unsigned long long) {
+          [&](int u) {
             const unsigned short pr = L.opp[u];
-            const int r = pr & 0xFF, s = pr >> 8;
-            const double v = anti(in, r, s, p, q);
-            return double_parity(I, p, q, r, s) ? -v : v;
+            return connection_code(1, p, q, pr & 0xFF, pr >> 8);
           },
-          part, probes, hits);
+          resolve_hits, probes);
     }
+  if (qn > 0) resolve_hits(qn);
+  __syncwarp();  // the lists of I are read until here
   return part;
 }
 
-// The lane's share of sigma_I = sum_{J in S} <I|H|J> c_J for one stored
-// determinant I (the warp's lanes split I's connections; sum with warp_sum).
-// L is this warp's shared-memory scratch.  Every lane of the warp calls this.
-__device__ __forceinline__ double sigma_entry(const Table& t, const Integrals& in, WarpLists& L,
-                                              unsigned long long I, double cI, int lane, unsigned long long& probes,
-                                              unsigned long long& hits) {
-  if (lane == 0) {
-    for (int sp = 0; sp < 2; ++sp) L.n_occ[sp] = L.n_emp[sp] = 0;
-    for (int p = 0; p < in.n_so; ++p) {
-      const int sp = p & 1;
-      if ((I >> p) & 1ull)
-        L.occ[sp][L.n_occ[sp]++] = (unsigned char)p;
-      else
-        L.emp[sp][L.n_emp[sp]++] = (unsigned char)p;
-    }
-  }
-  __syncwarp();
-  for (int sp = 0; sp < 2; ++sp) {
-    const int m = L.n_emp[sp];
-    const int np = m * (m - 1) / 2;
-    for (int u = lane; u < np; u += 32) {
-      // u -> (x, y), x < y, row-major over the strict upper triangle
-      int x = 0, rem = u;
-      while (rem >= m - 1 - x) {
-        rem -= m - 1 - x;
-        ++x;
-      }
-      const int y = x + 1 + rem;
-      L.pairs[sp][u] = (unsigned short)(L.emp[sp][x] | (L.emp[sp][y] << 8));
-    }
-    if (lane == 0) L.n_pairs[sp] = np;
-  }
-  __syncwarp();
-
-  double part = 0.0;
-  // Diagonal: lanes over the first index p.
-  {
-    double d = 0.0;
-    for (int sp = 0; sp < 2; ++sp)
-      for (int x = lane; x < L.n_occ[sp]; x += 32) {
-        const int p = L.occ[sp][x];
-        d += h_so(in, p, p);
-        for (int sq = 0; sq < 2; ++sq)
-          for (int y = 0; y < L.n_occ[sq]; ++y) {
-            const int q = L.occ[sq][y];
-            if (q != p) d += 0.5 * anti(in, p, q, p, q);
-          }
-      }
-    part += d * cI;
-  }
-  // Singles p -> r, same spin.
-  for (int sp = 0; sp < 2; ++sp) {
-    const int no = L.n_occ[sp], ne = L.n_emp[sp];
-    probe_connections(
-        t, no * ne, lane,
-        [&](int u) { return I ^ ((1ull << L.occ[sp][u / ne]) | (1ull << L.emp[sp][u % ne])); },
-        [&](int u, unsigned long long) {
-          const int p = L.occ[sp][u / ne], r = L.emp[sp][u % ne];
-          double v = h_so(in, r, p);
-          for (int sk = 0; sk < 2; ++sk)
-            for (int y = 0; y < L.n_occ[sk]; ++y) {
-              const int kk = L.occ[sk][y];
-              if (kk != p) v += anti(in, r, kk, p, kk);
-            }
-          return single_parity(I, p, r) ? -v : v;
-        },
-        part, probes, hits);
-  }
-  // Doubles: same-spin (p < q from one spin, r < s from the same spin).
-  for (int sp = 0; sp < 2; ++sp) {
-    const int no = L.n_occ[sp];
-    const int np = L.n_pairs[sp];
-    for (int x = 0; x < no; ++x)
-      for (int y = x + 1; y < no; ++y) {
-        const int p = L.occ[sp][x], q = L.occ[sp][y];
-        const unsigned long long hole = (1ull << p) | (1ull << q);
-        probe_connections(
-            t, np, lane,
-            [&](int u) {
-              const unsigned short pr = L.pairs[sp][u];
-              return I ^ (hole | (1ull << (pr & 0xFF)) | (1ull << (pr >> 8)));
-            },
-            [&](int u, unsigned long long) {
-              const unsigned short pr = L.pairs[sp][u];
-              const int r = pr & 0xFF, s = pr >> 8;
-              const double v = anti(in, r, s, p, q);
-              return double_parity(I, p, q, r, s) ? -v : v;
-            },
-            part, probes, hits);
-      }
-  }
-  // Doubles: opposite spin (p alpha, q beta -> r alpha, s beta).
-  {
-    const int noa = L.n_occ[0], nob = L.n_occ[1], nea = L.n_emp[0], neb = L.n_emp[1];
-    const int nE = nea * neb;
-    for (int x = 0; x < noa; ++x)
-      for (int y = 0; y < nob; ++y) {
-        const int p = L.occ[0][x], q = L.occ[1][y];
-        const unsigned long long hole = (1ull << p) | (1ull << q);
-        probe_connections(
-            t, nE, lane,
-            [&](int u) { return I ^ (hole | (1ull << L.emp[0][u / neb]) | (1ull << L.emp[1][u % neb])); },
-            [&](int u, unsigned long long) {
-              const int r = L.emp[0][u / neb], s = L.emp[1][u % neb];
-              const double v = anti(in, r, s, p, q);
-              return double_parity(I, p, q, r, s) ? -v : v;
-            },
-            part, probes, hits);
-      }
-  }
-  return part;
-}
 
 }  // namespace ucc
