@@ -22,6 +22,8 @@ namespace ucc {
 namespace {
 
 constexpr int kThreads = 256;
+// Records from which a factor's re-insertion takes the bulk path.
+constexpr unsigned long long kBulkRecords = 1024;
 
 // Re-insert the entries factor k dropped, with their values just before the
 // drop, a zero adjoint, and their original birth factor.
@@ -48,6 +50,90 @@ __global__ void __launch_bounds__(kThreads) k_tape_reinsert(Table t, Tape tape, 
       insert_new(t, key, val, born, r.slot, true, true);
     }
   }
+}
+
+// Bulk re-insertion (a cut's records): each warp takes 128 records per round,
+// four per lane, tests their filter words together, revives in place the few
+// whose key is still stored (dropped), and appends the rest without a hash
+// slot, one reservation per warp and round; k_link_tail then hashes the
+// appended range.  This replaces a per-record chain of filter load, slot
+// claim and tail reservation.
+__global__ void k_mark_tail(Table t) {
+  if (threadIdx.x == 0) t.cnt->link_from = *((volatile unsigned long long*)&t.cnt->n_tail);
+}
+
+__global__ void __launch_bounds__(kThreads) k_tape_append(Table t, Tape tape, int k) {
+  const unsigned long long hi = min(tape.off[k + 1], tape.cap);
+  const unsigned long long lo = min(tape.off[k], hi);
+  const unsigned int lane = threadIdx.x & 31u;
+  const unsigned int below_me = (1u << lane) - 1u;
+  const unsigned long long warp = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const unsigned long long nwarps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
+  unsigned long long revived = 0;
+  for (unsigned long long base = lo + warp * 128ull; base < hi; base += nwarps * 128ull) {  // warp-uniform
+    TapeRec rec[4];
+    bool add[4], maybe[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const unsigned long long x = base + 32ull * j + lane;
+      add[j] = x < hi;
+      if (add[j]) rec[j] = tape_at(tape, x);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) maybe[j] = add[j] && filter_maybe(t, rec[j].key);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (!maybe[j]) continue;
+      const Lookup r = find1(t, rec[j].key, 0u);
+      if (r.state == ALIVE) {
+        raise_error(t.cnt, ERR_CONSISTENCY);
+        add[j] = false;
+      } else if (r.state == DEAD_OLD || r.state == DEAD_NOW) {
+        t.amps[r.idx] = rec[j].val;
+        t.lam[r.idx] = 0.0;
+        t.born[r.idx] = rec[j].born;
+        ++revived;
+        add[j] = false;
+      }
+    }
+    unsigned int m[4];
+    int total = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      m[j] = __ballot_sync(0xFFFFFFFFu, add[j]);
+      total += __popc(m[j]);
+    }
+    if (total == 0) continue;  // warp-uniform
+    unsigned long long at = 0;
+    if (lane == 0) at = atomicAdd(&t.cnt->n_tail, (unsigned long long)total);
+    at = __shfl_sync(0xFFFFFFFFu, at, 0);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (add[j]) {
+        const unsigned long long idx = at + __popc(m[j] & below_me);
+        if (idx < t.cap_n) {
+          t.keys[idx] = rec[j].key;
+          t.amps[idx] = rec[j].val;
+          t.born[idx] = rec[j].born;
+          t.lam[idx] = 0.0;
+        } else {
+          raise_error(t.cnt, ERR_CAPACITY);
+        }
+      }
+      at += __popc(m[j]);
+    }
+  }
+  revived = warp_sum_u64(revived);
+  if (lane == 0 && revived) atomicAdd(&t.cnt->n_dead, 0ull - revived);  // dropped entries revived
+}
+
+// Hash slots for the entries appended since k_mark_tail.
+__global__ void __launch_bounds__(kThreads) k_link_tail(Table t) {
+  const unsigned long long lo = *((volatile unsigned long long*)&t.cnt->link_from);
+  const unsigned long long hi = min(*((volatile unsigned long long*)&t.cnt->n_tail), t.cap_n);
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long j = lo + (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; j < hi; j += stride)
+    link_appended(t, t.keys[j], j);
 }
 
 template <int G>
@@ -96,8 +182,17 @@ __global__ void __launch_bounds__(kStepThreads, 8) k_reverse(Table t, const Fact
 
 }  // namespace
 
-cudaError_t launch_tape_reinsert(const Table& t, const Tape& tape, int k, int grid, cudaStream_t st) {
-  k_tape_reinsert<<<grid, kThreads, 0, st>>>(t, tape, k);
+cudaError_t launch_tape_reinsert(const Table& t, const Tape& tape, int k, unsigned long long records, int grid,
+                                 cudaStream_t st, long long* launches) {
+  if (records < kBulkRecords) {
+    k_tape_reinsert<<<grid, kThreads, 0, st>>>(t, tape, k);
+    *launches += 1;
+  } else {
+    k_mark_tail<<<1, 32, 0, st>>>(t);
+    k_tape_append<<<grid, kThreads, 0, st>>>(t, tape, k);
+    k_link_tail<<<grid, kThreads, 0, st>>>(t);
+    *launches += 3;
+  }
   return cudaGetLastError();
 }
 

@@ -16,7 +16,6 @@ namespace ucc {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kWarps = kThreads / 32;
 // The energy kernel's blocks: four warps keep the job table and the warps'
 // connection lists within the static shared-memory limit.
 constexpr int kSigmaWarps = 4;

@@ -690,8 +690,7 @@ ucc_status reverse_segment(ucc_ctx* c, TableSet& s, int k0, int k1) {
     }
     if (rec) {
       const int g2 = (int)std::min<unsigned long long>((unsigned long long)grid_full, (rec + 255) / 256);
-      CUDA_TRY(launch_tape_reinsert(c->table(s), c->tape(), k, std::max(g2, 1), c->stream));
-      c->launches++;
+      CUDA_TRY(launch_tape_reinsert(c->table(s), c->tape(), k, rec, std::max(g2, 1), c->stream, &c->launches));
     }
     CUDA_TRY(launch_reverse(c->table(s), c->d_factors, k, stamp, c->d_grad, pick_probe_width(c), grid, c->stream));
     c->launches++;

@@ -160,7 +160,8 @@ cudaError_t launch_export(const Table& t, unsigned long long cap, unsigned long 
                           double* sigma, int grid, cudaStream_t st);
 cudaError_t launch_sigma(const Table& t, const Integrals& in, int grid, cudaStream_t st);
 cudaError_t launch_lambda_init(const Table& t, int grid, cudaStream_t st);
-cudaError_t launch_tape_reinsert(const Table& t, const Tape& tape, int k, int grid, cudaStream_t st);
+cudaError_t launch_tape_reinsert(const Table& t, const Tape& tape, int k, unsigned long long records, int grid,
+                                 cudaStream_t st, long long* launches);
 cudaError_t launch_reverse(const Table& t, const Factor* factors, int k, unsigned int stamp, double* grad,
                            int probe_width, int grid, cudaStream_t st);
 cudaError_t launch_restore(const Table& t, const unsigned long long* keys, const double* amps, unsigned long long n,
