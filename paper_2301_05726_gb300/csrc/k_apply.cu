@@ -123,32 +123,85 @@ __global__ void __launch_bounds__(kThreads) k_link(Table t, int k) {
 
 // Copy the live entries of `from` into `to` (unordered), counting in new_n.
 // with_born: 0 keys and amplitudes, 1 also born, 2 also born and lam.
+// Each warp takes four tiles of 32 entries per round: their amplitudes are
+// loaded together and one reservation per round places the live ones.
 __global__ void __launch_bounds__(kThreads) k_compact(Table from, Table to, int with_born) {
   const unsigned long long n = min(*((volatile unsigned long long*)&from.cnt->n_tail), from.cap_n);
-  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    const double a = from.amps[i];
-    if (is_dead(a)) continue;
-    const unsigned long long j = aggregated_add(&from.cnt->new_n);
-    if (j >= to.cap_n) {
-      raise_error(from.cnt, ERR_CAPACITY);
-      continue;
+  const unsigned int lane = threadIdx.x & 31u;
+  const unsigned int below_me = (1u << lane) - 1u;
+  const unsigned long long warp = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const unsigned long long nwarps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
+  for (unsigned long long base = warp * 128ull; base < n; base += nwarps * 128ull) {  // warp-uniform
+    double a[4];
+    bool live[4];
+    unsigned int m[4];
+    int total = 0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const unsigned long long i = base + 32ull * u + lane;
+      a[u] = i < n ? from.amps[i] : 0.0;
     }
-    to.keys[j] = from.keys[i];
-    to.amps[j] = a;
-    if (with_born) to.born[j] = from.born[i];
-    if (with_born > 1) to.lam[j] = from.lam[i];  // mid reverse sweep: keep the adjoint
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      live[u] = base + 32ull * u + lane < n && !is_dead(a[u]);
+      m[u] = __ballot_sync(0xFFFFFFFFu, live[u]);
+      total += __popc(m[u]);
+    }
+    if (total == 0) continue;  // warp-uniform
+    unsigned long long at = 0;
+    if (lane == 0) at = atomicAdd(&from.cnt->new_n, (unsigned long long)total);
+    at = __shfl_sync(0xFFFFFFFFu, at, 0);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (live[u]) {
+        const unsigned long long i = base + 32ull * u + lane;
+        const unsigned long long j = at + __popc(m[u] & below_me);
+        if (j < to.cap_n) {
+          to.keys[j] = from.keys[i];
+          to.amps[j] = a[u];
+          if (with_born) to.born[j] = from.born[i];
+          if (with_born > 1) to.lam[j] = from.lam[i];  // mid reverse sweep: keep the adjoint
+        } else {
+          raise_error(from.cnt, ERR_CAPACITY);
+        }
+      }
+      at += __popc(m[u]);
+    }
   }
 }
 
 // Insert entries [0, new_n) into an empty slot array.
+// Four entries per thread and round: their keys are loaded and their home
+// slots claimed together (the home slot is usually free), and only the
+// entries whose home slot was taken probe on.
 __global__ void __launch_bounds__(kThreads) k_rehash(Table t) {
   const unsigned long long n = min(*((volatile unsigned long long*)&t.cnt->new_n), t.cap_n);
   const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    const unsigned long long key = t.keys[i];
-    const unsigned long long s = claim_slot(t, key, home_slot(t, key));
-    if (s != ~0ull) t.slots[s].idx = i;
+  for (unsigned long long i0 = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += 4 * stride) {
+    unsigned long long key[4], h[4], prev[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const unsigned long long i = i0 + u * stride;
+      key[u] = i < n ? t.keys[i] : 0ull;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      h[u] = home_slot(t, key[u]);
+      prev[u] = key[u] ? atomicCAS(&t.slots[h[u]].key, 0ull, key[u]) : 1ull;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (!key[u]) continue;
+      const unsigned long long i = i0 + u * stride;
+      unsigned long long s = h[u];
+      if (prev[u] == 0ull) {
+        filter_add(t, key[u]);
+      } else {
+        if (prev[u] == key[u]) raise_error(t.cnt, ERR_CONSISTENCY);
+        s = claim_slot(t, key[u], h[u] + 1);
+      }
+      if (s != ~0ull) t.slots[s].idx = i;
+    }
   }
 }
 
