@@ -41,9 +41,11 @@ __device__ __forceinline__ bool nonzero(double v) {
   return r != 0u;
 }
 
+// Per-thread counts of one launch (32 bits: a thread handles far fewer than
+// 2^32 entries per launch; blocks sum them in 64 bits).
 struct StepCounts {
-  unsigned long long rot = 0, cre = 0, dnew = 0, dold = 0;
-  long long dead_delta = 0;
+  unsigned int rot = 0, cre = 0, dnew = 0, dold = 0;
+  int dead_delta = 0;
   double dS = 0.0;  // change of the Eq. 6 entropy (when recorded)
 };
 
@@ -208,9 +210,9 @@ __device__ __forceinline__ bool linked_entry(const Table& t, const Factor& f, un
   ex = false;
   if (!in_range) return false;
   X = t.keys[i];
-  ex = ((X & f.occ) == f.occ) && ((X & f.vir) == 0ull);
-  const bool de = ((X & f.vir) == f.vir) && ((X & f.occ) == 0ull);
-  if (!(ex || de)) return false;
+  const unsigned long long tX = X & (f.occ | f.vir);  // occ and vir are disjoint
+  ex = tX == f.occ;
+  if (!(ex || tX == f.vir)) return false;
   cX = t.amps[i];
   return !is_dead(cX);
 }
@@ -480,9 +482,11 @@ __device__ __forceinline__ void for_each_linked(const Table& t, const Factor& f,
       double cX = 0.0;
       if (i < n) {
         X = st.X[e];
-        ex = ((X & f.occ) == f.occ) && ((X & f.vir) == 0ull);
-        const bool de = ((X & f.vir) == f.vir) && ((X & f.occ) == 0ull);
-        if (ex || de) {
+        // occ and vir are disjoint: E holds exactly occ of the factor's
+        // orbitals, D exactly vir
+        const unsigned long long tX = X & m;
+        ex = tX == f.occ;
+        if (ex || tX == f.vir) {
           cX = st.c[e];
           act = !is_dead(cX);
         }
