@@ -172,9 +172,17 @@ def flush_l2(buf):
     buf.add_(1.0)
 
 
+# DRAM traffic per algorithmic byte of a kernel, from one ncu capture of every launch of one evaluation
+# of the 1000-factor prefix (profiles/k_reverse_traffic_64so_prefix1000.md); a launch's traffic is taken
+# as this ratio times its algorithmic bytes.  To be re-measured (or removed) whenever the kernel changes.
+TRAFFIC_PER_ALGORITHMIC_BYTE = {"k_reverse": 1.74}
+
+
 def _roofline(kernel, bytes_, ms, launches, hbm, peak_kind):
     ach = bytes_ / (ms / 1e3) / 1e9 if ms > 0 else 0.0
-    return {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": None,
+    ratio = TRAFFIC_PER_ALGORITHMIC_BYTE.get(kernel)
+    traffic = ratio * bytes_ / max(1, launches) if ratio else None
+    return {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": traffic,
             "kernel": kernel, "peak_kind": peak_kind, "launches": launches,
             "avg_launch_ms": ms / max(1, launches), "algorithmic_bytes": bytes_, "total_ms": ms}
 
