@@ -81,7 +81,7 @@ struct Arrays {
   double* lam = nullptr;
   double* sigma = nullptr;
   Slot* slots = nullptr;
-  unsigned long long* filt = nullptr;  // one 64-bit word per 8 slots
+  unsigned int* filt = nullptr;  // one 32-bit word per 4 slots
   void release() {
     dfree(filt);
     dfree(keys);
@@ -100,7 +100,7 @@ struct Arrays {
     UCC_TRY(dalloc(&lam, cn));
     UCC_TRY(dalloc(&sigma, cn));
     UCC_TRY(dalloc(&slots, ns));
-    UCC_TRY(dalloc(&filt, ns / 8));
+    UCC_TRY(dalloc(&filt, ns / 4));
     cap_n = cn;
     n_slots = ns;
     return UCC_OK;
@@ -199,7 +199,7 @@ struct ucc_ctx {
     t.slot_mask = s.cur.n_slots - 1;
     t.slot_shift = 64 - __builtin_ctzll(s.cur.n_slots);
     t.filt = s.cur.filt;
-    t.filt_shift = 64 - (__builtin_ctzll(s.cur.n_slots) - 3);
+    t.filt_shift = 32 - (__builtin_ctzll(s.cur.n_slots) - 2);
     t.cap_n = s.cur.cap_n;
     t.cnt = s.d_cnt;
     t.partials = d_partials;
@@ -297,11 +297,11 @@ ucc_status rebuild(ucc_ctx* c, TableSet& s, unsigned long long new_cap, bool wit
   to.slot_mask = ns - 1;
   to.slot_shift = 64 - __builtin_ctzll(ns);
   to.filt = s.spare.filt;
-  to.filt_shift = 64 - (__builtin_ctzll(ns) - 3);
+  to.filt_shift = 32 - (__builtin_ctzll(ns) - 2);
   to.cap_n = new_cap;
   CUDA_TRY(cudaMemsetAsync(&s.d_cnt->new_n, 0, sizeof(unsigned long long), c->stream));
   CUDA_TRY(cudaMemsetAsync(to.slots, 0, ns * sizeof(Slot), c->stream));
-  CUDA_TRY(cudaMemsetAsync(to.filt, 0, ns / 8 * sizeof(unsigned long long), c->stream));
+  CUDA_TRY(cudaMemsetAsync(to.filt, 0, ns / 4 * sizeof(unsigned int), c->stream));
   int grid = c->full_grid();
   CUDA_TRY(launch_compact(from, to, with_lam ? 2 : 1, grid, c->stream));
   CUDA_TRY(launch_rehash(to, grid, c->stream));
@@ -354,7 +354,7 @@ ucc_status reset_table(ucc_ctx* c, TableSet& s) {
   if (s.cur.cap_n == 0) UCC_TRY(s.cur.allocate(1 << 12, slots_for(1 << 12)));
   CUDA_TRY(cudaMemsetAsync(s.d_cnt, 0, sizeof(Counters), c->stream));
   CUDA_TRY(cudaMemsetAsync(s.cur.slots, 0, s.cur.n_slots * sizeof(Slot), c->stream));
-  CUDA_TRY(cudaMemsetAsync(s.cur.filt, 0, s.cur.n_slots / 8 * sizeof(unsigned long long), c->stream));
+  CUDA_TRY(cudaMemsetAsync(s.cur.filt, 0, s.cur.n_slots / 4 * sizeof(unsigned int), c->stream));
   CUDA_TRY(launch_reset(c->table(s), reference_key(c), c->stream));
   c->launches++;
   return UCC_OK;
@@ -374,7 +374,7 @@ ucc_status load_snapshot(ucc_ctx* c, TableSet& s, const Snapshot& snap) {
   if (s.cur.cap_n < cap) UCC_TRY(s.cur.allocate(cap, slots_for(cap)));
   CUDA_TRY(cudaMemsetAsync(s.d_cnt, 0, sizeof(Counters), c->stream));
   CUDA_TRY(cudaMemsetAsync(s.cur.slots, 0, s.cur.n_slots * sizeof(Slot), c->stream));
-  CUDA_TRY(cudaMemsetAsync(s.cur.filt, 0, s.cur.n_slots / 8 * sizeof(unsigned long long), c->stream));
+  CUDA_TRY(cudaMemsetAsync(s.cur.filt, 0, s.cur.n_slots / 4 * sizeof(unsigned int), c->stream));
   const int grid = c->full_grid();
   CUDA_TRY(launch_restore(c->table(s), snap.keys, snap.amps, snap.n, grid, c->stream));
   CUDA_TRY(launch_rehash(c->table(s), grid, c->stream));

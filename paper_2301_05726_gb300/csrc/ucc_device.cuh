@@ -24,12 +24,13 @@ __device__ __forceinline__ unsigned long long home_slot(const Table& t, unsigned
   return (key * kFibonacci) >> t.slot_shift;
 }
 
-// Existence filter: a blocked Bloom filter of 64-bit words, 8 filter bits per
+// Existence filter: a blocked Bloom filter of 32-bit words, 8 filter bits per
 // hash slot (1/16 the size of the slot array, so it mostly stays in L2).  A
 // key's filter hash h = key * kFilterMul (a second odd constant, the
 // SplitMix64 finalizer's first multiplier, so it does not follow the slot)
 // picks one word by its top bits and three bit positions in that word by the
-// next 18 bits; the key sets all three.  A lookup is one load: a word missing
+// next 15 bits; the key sets all three.  Word and bits come from the high
+// half of h and one funnel shift, so the test is 32-bit integer work.  A lookup is one load: a word missing
 // any of the key's bits proves the key absent and saves the probe; a word
 // holding all three (a stored key, or a collision) falls through to the
 // probe.  Three bits in one word make collisions far rarer than one bit per
@@ -37,16 +38,17 @@ __device__ __forceinline__ unsigned long long home_slot(const Table& t, unsigned
 // of absent keys).
 constexpr unsigned long long kFilterMul = 0xbf58476d1ce4e5b9ull;
 
-__device__ __forceinline__ unsigned long long filter_word(const Table& t, unsigned long long h) {
-  return h >> t.filt_shift;
+__device__ __forceinline__ unsigned int filter_word(const Table& t, unsigned long long h) {
+  return (unsigned int)(h >> 32) >> t.filt_shift;  // the top log2(words) bits of h
 }
-__device__ __forceinline__ unsigned long long filter_bits(const Table& t, unsigned long long h) {
-  const unsigned long long r = h << (64 - t.filt_shift);  // the bits below the word index, moved to the top
-  return (1ull << (r >> 58)) | (1ull << ((r >> 52) & 63ull)) | (1ull << ((r >> 46) & 63ull));
+__device__ __forceinline__ unsigned int filter_bits(const Table& t, unsigned long long h) {
+  // the 32 bits of h just below the word index
+  const unsigned int r = __funnelshift_l((unsigned int)h, (unsigned int)(h >> 32), 32 - t.filt_shift);
+  return (1u << (r >> 27)) | (1u << ((r >> 22) & 31u)) | (1u << ((r >> 17) & 31u));
 }
 // Whether filter word w holds every bit of the key with filter hash h.
-__device__ __forceinline__ bool filter_hit(const Table& t, unsigned long long w, unsigned long long h) {
-  const unsigned long long m = filter_bits(t, h);
+__device__ __forceinline__ bool filter_hit(const Table& t, unsigned int w, unsigned long long h) {
+  const unsigned int m = filter_bits(t, h);
   return (w & m) == m;
 }
 

@@ -68,8 +68,8 @@ struct Table {
   Slot* slots;               // [slot_mask + 1], a power of two
   unsigned long long slot_mask;
   int slot_shift;            // 64 - log2(slot_mask + 1): home slot = (key * phi64) >> slot_shift
-  int filt_shift;            // 64 - log2(filter words)
-  unsigned long long* filt;  // existence filter, one 64-bit word per 8 slots (nullptr: none)
+  int filt_shift;            // 32 - log2(filter words)
+  unsigned int* filt;        // existence filter, one 32-bit word per 4 slots (nullptr: none)
   unsigned long long cap_n;
   Counters* cnt;
   double* partials;          // [grid] per-block partial sums

@@ -115,7 +115,7 @@ extern "C" ucc_status ucc_energy_static(int32_t n_spatial, int32_t n_alpha, int3
   t.slot_mask = kStaticSlots - 1;
   t.slot_shift = 64 - __builtin_ctzll(kStaticSlots);
   t.filt = nullptr;
-  t.filt_shift = 64;
+  t.filt_shift = 32;
   t.cap_n = n_det;
   t.cnt = &S->cnt;
   t.partials = S->partials;
