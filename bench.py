@@ -121,26 +121,44 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def oracle_sample(prob, seconds, with_grad=True):
-    """Time the CPU oracle on a prefix of the workload sized to ~`seconds`.
-    Returns (forward rotations per eval second, evals/s, description, prefix)."""
+def oracle_time(prob, n_factors, with_grad=True):
+    """One oracle evaluation (apply + energy + adjoint) of the first n_factors factors:
+    (forward rotations, seconds)."""
     import oracle
-    o = oracle.Oracle(prob)
-    pre = 16
-    best = None
+    sub = prob.prefix(min(n_factors, prob.n_exc))
+    o = oracle.Oracle(sub)
+    t0 = time.perf_counter()
+    _, _, cnt = o.apply()
+    if with_grad:
+        o.gradient()
+    return cnt["rotations"], time.perf_counter() - t0
+
+
+def oracle_prefix(prob, seconds, with_grad=True):
+    """The longest factor prefix whose oracle evaluation should take at most ~`seconds`: prefixes grow
+    by 1.5x while the cost of the next one, extrapolated from the growth of the last two (the map and so
+    the cost per factor grow with the prefix), stays within the budget.
+    Returns (prefix, its forward rotations, its seconds)."""
+    pre, prev = 16, None
     while True:
-        sub = prob.prefix(min(pre, prob.n_exc))
-        os_ = oracle.Oracle(sub)
-        t0 = time.perf_counter()
-        _, _, cnt = os_.apply()
-        E, g = os_.gradient() if with_grad else (None, None)
-        dt = time.perf_counter() - t0
-        best = (cnt["rotations"], dt, sub.n_exc)
-        if dt > seconds / 4 or sub.n_exc >= prob.n_exc:
-            break
-        pre *= 2
-    del o
-    rot, dt, nf = best
+        rot, dt = oracle_time(prob, pre, with_grad)
+        nxt = min(prob.n_exc, max(pre + 1, int(pre * 1.5)))
+        if pre >= prob.n_exc:
+            return pre, rot, dt
+        growth = max(1.5, dt / prev) if prev else 4.0
+        if dt * growth > seconds:
+            return pre, rot, dt
+        pre, prev = nxt, dt
+
+
+def oracle_sample(prob, seconds, with_grad=True, n_factors=None):
+    """Time the CPU oracle on a prefix of the workload sized to ~`seconds` (or on the first n_factors).
+    Returns (forward rotations per eval second, evals/s, prefix, seconds)."""
+    if n_factors is None:
+        nf, rot, dt = oracle_prefix(prob, seconds, with_grad)
+    else:
+        nf = n_factors
+        rot, dt = oracle_time(prob, nf, with_grad)
     return rot / dt, 1.0 / dt, nf, dt
 
 
@@ -150,10 +168,11 @@ def run_reference(args, prob):
     if rank != 0:
         return
     per_step = max(1.0, 60.0 / max(1, args.steps + args.warmup))
+    nf_fixed = oracle_prefix(prob, per_step)[0]  # one calibration; every step then runs the same prefix
     rates = []
     desc = None
     for s in range(args.warmup + args.steps):
-        r, evals, nf, dt = oracle_sample(prob, per_step * 4)
+        r, evals, nf, dt = oracle_sample(prob, per_step, n_factors=nf_fixed)
         if s >= args.warmup:
             rates.append(r)
             desc = f"{prob.name} first {nf} of {prob.n_exc} factors: apply + energy + adjoint, {dt:.1f}s"
