@@ -578,6 +578,7 @@ struct LowerLists {
   unsigned short opp[kMaxSpin * kMaxSpin];  // (r alpha | s beta << 8), ordered by max(r, s)
   unsigned long long hitJ[32 * (kV + 1)];   // connections whose filter word holds all their bits
   unsigned int hitCode[32 * (kV + 1)];      // and their excitation (connection_code)
+  unsigned long long mulBit[64];            // kFilterMul * 2^x: filter-hash term of spin-orbital x
 };
 
 // An excitation of I packed in 26 bits: kind (0 single p -> r, 1 double
@@ -589,24 +590,19 @@ __device__ __forceinline__ unsigned int connection_code(int kind, int p, int q, 
 
 // The connections J < I of the lower-triangle energy pass, with the warp in
 // lock step (count is warp-uniform): the lanes test kV filter words each and
-// queue the connections whose word holds all their bits (key_of(u) gives J,
-// code_of(u) its excitation); whenever 32 or more are queued after a round,
-// resolve_hits takes them 32 at a time, so the slot probes of rare hits run
-// on full warps instead of stalling the loop once per hit.  The queue holds
-// fewer than 32 between rounds.
-template <class KeyOf, class CodeOf, class Resolve>
+// queue the connections whose word holds all their bits (hash_of(u) gives
+// J's filter hash J * kFilterMul, key_of(u) J itself, code_of(u) its
+// excitation); whenever 32 or more are queued after a round, resolve_hits
+// takes them 32 at a time, so the slot probes of rare hits run on full warps
+// instead of stalling the loop once per hit.  The queue holds fewer than 32
+// between rounds.
+template <class HashOf, class KeyOf, class CodeOf, class Resolve>
 __device__ __forceinline__ void probe_lower(const Table& t, LowerLists& L, int& qn, int count, int lane,
-                                            KeyOf key_of, CodeOf code_of, Resolve resolve_hits,
+                                            HashOf hash_of, KeyOf key_of, CodeOf code_of, Resolve resolve_hits,
                                             unsigned long long& probes) {
   const unsigned int below_me = (1u << lane) - 1u;
   for (int u0 = 0; u0 < count; u0 += 32 * kV) {
-    unsigned long long J[kV];
     bool w[kV];
-#pragma unroll
-    for (int v = 0; v < kV; ++v) {
-      const int u = u0 + 32 * v + lane;
-      J[v] = u < count ? key_of(u) : 0ull;
-    }
 #pragma unroll
     for (int v = 0; v < kV; ++v) {
       const int u = u0 + 32 * v + lane;
@@ -614,7 +610,7 @@ __device__ __forceinline__ void probe_lower(const Table& t, LowerLists& L, int& 
       if (u < count) {
         ++probes;
         if (t.filt) {
-          const unsigned long long h = J[v] * kFilterMul;
+          const unsigned long long h = hash_of(u);
           w[v] = filter_hit(t, t.filt[filter_word(t, h)], h);
         } else {
           w[v] = true;
@@ -627,7 +623,7 @@ __device__ __forceinline__ void probe_lower(const Table& t, LowerLists& L, int& 
       const unsigned int m = __ballot_sync(0xFFFFFFFFu, w[v]);
       if (w[v]) {
         const int p = qn + __popc(m & below_me);
-        L.hitJ[p] = J[v];
+        L.hitJ[p] = key_of(u);
         L.hitCode[p] = code_of(u);
       }
       qn += __popc(m);
@@ -679,6 +675,10 @@ __device__ __forceinline__ double sigma_lower(const Table& t, const Integrals& i
       L.pairs[sp][u] = (unsigned short)(L.emp[sp][x] | (L.emp[sp][y] << 8));
     }
   }
+  // Filter-hash terms: J = (I with the holes cleared) + 2^r + 2^s exactly (the
+  // particles are empty in I), so J * kFilterMul = base + mulBit[r] + mulBit[s]
+  // modulo 2^64, with one base per hole set.
+  for (int x = lane; x < 64; x += 32) L.mulBit[x] = kFilterMul << x;
   // Opposite-spin empty pairs grouped by their larger orbital o: the pairs
   // with max < o number (alpha empties below o) * (beta empties below o).
   for (int o = lane; o < in.n_so; o += 32) {
@@ -747,8 +747,10 @@ __device__ __forceinline__ double sigma_lower(const Table& t, const Integrals& i
   for (int sp = 0; sp < 2; ++sp)
     for (int x = 0; x < L.n_occ[sp]; ++x) {
       const int p = L.occ[sp][x];
+      const unsigned long long base = (I ^ (1ull << p)) * kFilterMul;
       probe_lower(
-          t, L, qn, empty_below(sp, p), lane, [&](int u) { return I ^ ((1ull << p) | (1ull << L.emp[sp][u])); },
+          t, L, qn, empty_below(sp, p), lane, [&](int u) { return base + L.mulBit[L.emp[sp][u]]; },
+          [&](int u) { return I ^ ((1ull << p) | (1ull << L.emp[sp][u])); },
           [&](int u) { return connection_code(0, p, 0, L.emp[sp][u], 0); }, resolve_hits, probes);
     }
   // Doubles, same spin: holes p < q, particles r < s < q.
@@ -758,9 +760,14 @@ __device__ __forceinline__ double sigma_lower(const Table& t, const Integrals& i
       for (int y = x + 1; y < no; ++y) {
         const int p = L.occ[sp][x], q = L.occ[sp][y];
         const unsigned long long hole = (1ull << p) | (1ull << q);
+        const unsigned long long base = (I ^ hole) * kFilterMul;
         const int y0 = empty_below(sp, q);
         probe_lower(
             t, L, qn, y0 * (y0 - 1) / 2, lane,
+            [&](int u) {
+              const unsigned short pr = L.pairs[sp][u];
+              return base + L.mulBit[pr & 0xFF] + L.mulBit[pr >> 8];
+            },
             [&](int u) {
               const unsigned short pr = L.pairs[sp][u];
               return I ^ (hole | (1ull << (pr & 0xFF)) | (1ull << (pr >> 8)));
@@ -779,8 +786,13 @@ __device__ __forceinline__ double sigma_lower(const Table& t, const Integrals& i
       const int p = L.occ[0][x], q = L.occ[1][y];
       const int m = p > q ? p : q;
       const unsigned long long hole = (1ull << p) | (1ull << q);
+      const unsigned long long base = (I ^ hole) * kFilterMul;
       probe_lower(
           t, L, qn, empty_below(0, m) * empty_below(1, m), lane,
+          [&](int u) {
+            const unsigned short pr = L.opp[u];
+            return base + L.mulBit[pr & 0xFF] + L.mulBit[pr >> 8];
+          },
           [&](int u) {
             const unsigned short pr = L.opp[u];
             return I ^ (hole | (1ull << (pr & 0xFF)) | (1ull << (pr >> 8)));
