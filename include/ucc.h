@@ -125,6 +125,7 @@ typedef struct {
   int64_t reverse_launches;    /* reverse factor launches */
   int64_t probe_width;         /* lanes per hash probe in use (fixed or autotuned) */
   int64_t reverse_scanned;     /* entries scanned by the reverse sweep's factor steps */
+  int64_t reverse_compactions; /* compactions of the table during the reverse sweep */
   double apply_ms;          /* device time of the last forward pass */
   double energy_ms;         /* device time of the last energy evaluation */
   double reverse_ms;        /* device time of the last reverse sweep */

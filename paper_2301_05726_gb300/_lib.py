@@ -44,7 +44,7 @@ class Stats(ctypes.Structure):
         "n_det", "rotations", "created", "dropped_new", "dropped_old", "cut", "peak_entries", "capacity_entries",
         "hash_slots", "rebuilds", "tape_entries", "kernel_launches", "scanned", "sigma_probes", "sigma_hits",
         "reverse_pairs", "recompute_scanned", "recompute_rotations", "recompute_created", "forward_launches",
-        "reverse_launches", "probe_width", "reverse_scanned")] + \
+        "reverse_launches", "probe_width", "reverse_scanned", "reverse_compactions")] + \
         [(n, ctypes.c_double) for n in ("apply_ms", "energy_ms", "reverse_ms", "forward_kernel_ms",
                                         "reverse_kernel_ms")]
 

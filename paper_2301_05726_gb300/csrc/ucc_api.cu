@@ -677,6 +677,7 @@ ucc_status reverse_segment(ucc_ctx* c, TableSet& s, int k0, int k1) {
       kernel_ms += ms;
       // Live entries now: stored minus those the sweep or the forward dropped.
       UCC_TRY(rebuild(c, s, s.cur.cap_n, true));
+      c->stats.reverse_compactions++;
       UCC_TRY(read_counters(c, s));
       bound = s.h_cnt->n_tail;
       if (bound + rec > s.cur.cap_n || 4ull * (bound + rec) > 3ull * s.cur.n_slots) {

@@ -170,6 +170,22 @@ def test_gradient_vs_oracle(torch_cuda, case):
         assert st["tape_entries"] > 0  # the irreversible path was exercised
 
 
+def test_reverse_sweep_compacts(torch_cuda):
+    """The reverse sweep removes the entries each factor created; on this
+    prefix (39k determinants) a third of the table is dropped well before the
+    sweep ends, so it compacts the table (keeping the adjoint) at least once,
+    and the gradient still matches the oracle's."""
+    prob = synth.config_problem(3).prefix(60)
+    E_ref, g_ref = load_golden("cfg3_prefix60_energy_gradient.txt")
+    ctx = ctx_for(prob)
+    E, g = ctx.gradient()
+    st = ctx.stats()
+    assert st["reverse_compactions"] >= 1
+    assert st["reverse_scanned"] > 0
+    assert abs(E - E_ref) <= E_TOL
+    assert np.max(np.abs(g - g_ref)) <= G_TOL
+
+
 def test_gradient_cfg2(torch_cuda):
     prob = synth.config_problem(2)
     E_ref, g_ref = load_golden("cfg2_energy_gradient.txt")
