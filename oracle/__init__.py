@@ -7,7 +7,8 @@ leg may import this package.  It shares no code with the CUDA library in
 arithmetic).
 
 ``ucc_oracle.cpp`` is the sparse reference (Eq. 3 factor by factor on a
-``std::unordered_map``, Slater-Condon energy, checkpointed adjoint);
+``std::unordered_map``, Slater-Condon energy, checkpointed adjoint), built
+with 64-bit and with 128-bit determinant keys;
 ``dense.py`` is an independent state-vector brute force used to pin it.
 """
 from __future__ import annotations
@@ -27,11 +28,20 @@ _lock = threading.Lock()
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with g++ (no fused multiply-add contraction)."""
+    """Compile the oracle with g++ (no fused multiply-add contraction): the same
+    source twice, with 64-bit keys (entry points orc_*) and with 128-bit keys
+    (orc128_*), linked into one library."""
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-shared", "-fPIC",
-                               "-o", tmp, _SRC])
+        objs = []
+        for bits in (64, 128):
+            obj = f"{tmp}.{bits}.o"
+            subprocess.check_call(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fPIC", "-c",
+                                   f"-DORC_KEY_BITS={bits}", "-o", obj, _SRC])
+            objs.append(obj)
+        subprocess.check_call(["g++", "-shared", "-o", tmp] + objs)
+        for obj in objs:
+            os.remove(obj)
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -71,6 +81,15 @@ def _load():
         lib.orc_tau.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, u64p]
         lib.orc_gradient.argtypes = [vp, dp, ctypes.c_double, ctypes.c_longlong, ctypes.c_longlong, ctypes.c_int,
                                      dp, dp]
+        # the 128-bit build: the same calls, keys as (low, high) pairs of words
+        for name in ("problem_new", "problem_free", "apply", "wf_from_arrays", "wf_size", "wf_export", "wf_free",
+                     "sigma", "energy", "sigma_at", "gradient"):
+            f64, f128 = getattr(lib, "orc_" + name), getattr(lib, "orc128_" + name)
+            f128.restype, f128.argtypes = f64.restype, f64.argtypes
+        lib.orc128_hmat.restype = ctypes.c_double
+        lib.orc128_hmat.argtypes = [vp, u64p, u64p]
+        lib.orc128_tau.restype = ctypes.c_int
+        lib.orc128_tau.argtypes = [vp, ctypes.c_int, ctypes.c_int, u64p, u64p]
         _lib = lib
         return lib
 
@@ -80,22 +99,36 @@ def _dp(a):
 
 
 class Oracle:
-    """One problem loaded into the oracle (integrals + factor list)."""
+    """One problem loaded into the oracle (integrals + factor list).
 
-    def __init__(self, prob):
+    key_bits: 64 (keys are uint64 arrays) or 128 (keys are (n, 2) uint64
+    arrays of (low, high) words; needed above 64 spin-orbitals).  By default
+    the smallest that holds the problem's spin-orbitals."""
+
+    def __init__(self, prob, key_bits=None):
         self.lib = _load()
         self.prob = prob
+        n_so = 2 * int(prob.n_spatial)
+        if key_bits is None:
+            key_bits = 64 if n_so <= 64 else 128
+        if key_bits not in (64, 128) or n_so > key_bits:
+            raise ValueError(f"{n_so} spin-orbitals do not fit {key_bits}-bit keys")
+        self.key_bits = key_bits
+        self._p = "orc_" if key_bits == 64 else "orc128_"
         self._h = np.ascontiguousarray(prob.h, dtype=np.float64)
         self._g = np.ascontiguousarray(prob.g, dtype=np.float64)
         self._exc = np.ascontiguousarray(prob.exc, dtype=np.int32)
-        self.handle = self.lib.orc_problem_new(
+        self.handle = self._f("problem_new")(
             prob.n_spatial, prob.n_alpha, prob.n_beta, _dp(self._h), _dp(self._g), int(self._exc.shape[0]),
             self._exc.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+
+    def _f(self, name):
+        return getattr(self.lib, self._p + name)
 
     def __del__(self):
         h = getattr(self, "handle", None)
         if h:
-            self.lib.orc_problem_free(h)
+            self._f("problem_free")(h)
             self.handle = None
 
     def _theta(self, theta):
@@ -116,10 +149,10 @@ class Oracle:
         n_max, n_cut = self._cut(n_max, n_cut)
         nf = len(th) if n_factors is None else int(n_factors)
         cnt = _Counts()
-        wf = self.lib.orc_apply(self.handle, _dp(th), nf, float(eps), int(n_max), int(n_cut), ctypes.byref(cnt),
+        wf = self._f("apply")(self.handle, _dp(th), nf, float(eps), int(n_max), int(n_cut), ctypes.byref(cnt),
                                 None)
-        keys, amps = _export(self.lib, wf)
-        self.lib.orc_wf_free(wf)
+        keys, amps = self._export(wf)
+        self._f("wf_free")(wf)
         counts = {f: getattr(cnt, f) for f, _ in _Counts._fields_}
         return keys, amps, counts
 
@@ -131,51 +164,77 @@ class Oracle:
         nf = len(th) if n_factors is None else int(n_factors)
         out = np.zeros(nf)
         cnt = _Counts()
-        wf = self.lib.orc_apply(self.handle, _dp(th), nf, float(eps), int(n_max), int(n_cut), ctypes.byref(cnt),
+        wf = self._f("apply")(self.handle, _dp(th), nf, float(eps), int(n_max), int(n_cut), ctypes.byref(cnt),
                                 _dp(out))
-        self.lib.orc_wf_free(wf)
+        self._f("wf_free")(wf)
         return out
 
+    def _keys(self, keys):
+        k = np.ascontiguousarray(keys, dtype=np.uint64)
+        if self.key_bits == 128 and (k.ndim != 2 or k.shape[1] != 2):
+            raise ValueError("128-bit keys are (n, 2) arrays of (low, high) words")
+        return k
+
+    def _export(self, wf):
+        n = self._f("wf_size")(wf)
+        keys = np.zeros((n,) if self.key_bits == 64 else (n, 2), dtype=np.uint64)
+        amps = np.zeros(n, dtype=np.float64)
+        if n:
+            self._f("wf_export")(wf, keys.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), _dp(amps))
+        return keys, amps
+
     def _wf(self, keys, amps):
-        keys = np.ascontiguousarray(keys, dtype=np.uint64)
+        keys = self._keys(keys)
         amps = np.ascontiguousarray(amps, dtype=np.float64)
-        return self.lib.orc_wf_from_arrays(len(keys), keys.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
-                                           _dp(amps))
+        return self._f("wf_from_arrays")(len(keys), keys.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                         _dp(amps))
 
     def energy(self, keys, amps, route="lookup"):
         """(E, <psi|psi>) of the map keys -> amps; route 'lookup' or 'pairwise'."""
         wf = self._wf(keys, amps)
         E, n2 = ctypes.c_double(), ctypes.c_double()
-        self.lib.orc_energy(self.handle, wf, 1 if route == "pairwise" else 0, ctypes.byref(E), ctypes.byref(n2))
-        self.lib.orc_wf_free(wf)
+        self._f("energy")(self.handle, wf, 1 if route == "pairwise" else 0, ctypes.byref(E), ctypes.byref(n2))
+        self._f("wf_free")(wf)
         return E.value, n2.value
 
     def sigma(self, keys, amps, route="lookup"):
         """sigma_I = sum_J <I|H|J> c_J over the map, in sorted-key order."""
         wf = self._wf(keys, amps)
-        n = self.lib.orc_wf_size(wf)
-        sk, _ = _export(self.lib, wf)
+        n = self._f("wf_size")(wf)
+        sk, _ = self._export(wf)
         out = np.zeros(n)
-        self.lib.orc_sigma(self.handle, wf, 1 if route == "pairwise" else 0, _dp(out))
-        self.lib.orc_wf_free(wf)
+        self._f("sigma")(self.handle, wf, 1 if route == "pairwise" else 0, _dp(out))
+        self._f("wf_free")(wf)
         return sk, out
 
     def sigma_at(self, keys, amps, query):
         """sigma at the given determinants only (one by one)."""
         wf = self._wf(keys, amps)
-        q = np.ascontiguousarray(query, dtype=np.uint64)
+        q = self._keys(query)
         out = np.zeros(len(q))
-        self.lib.orc_sigma_at(self.handle, wf, len(q), q.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), _dp(out))
-        self.lib.orc_wf_free(wf)
+        self._f("sigma_at")(self.handle, wf, len(q), q.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), _dp(out))
+        self._f("wf_free")(wf)
         return out
 
     def hmat(self, I, J):
-        return self.lib.orc_hmat(self.handle, int(I), int(J))
+        """<J|H|I> for determinants given as Python integers."""
+        if self.key_bits == 64:
+            return self.lib.orc_hmat(self.handle, int(I), int(J))
+        a, b = words(int(I)), words(int(J))
+        return self.lib.orc128_hmat(self.handle, a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                    b.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)))
 
     def tau(self, k, det, dagger=False):
-        out = ctypes.c_uint64()
-        s = self.lib.orc_tau(self.handle, int(k), 1 if dagger else 0, int(det), ctypes.byref(out))
-        return (s, out.value) if s else (0, None)
+        """(sign, tau_k |det>) or (0, None), determinants as Python integers."""
+        if self.key_bits == 64:
+            out = ctypes.c_uint64()
+            s = self.lib.orc_tau(self.handle, int(k), 1 if dagger else 0, int(det), ctypes.byref(out))
+            return (s, out.value) if s else (0, None)
+        d, out = words(int(det)), np.zeros(2, dtype=np.uint64)
+        s = self.lib.orc128_tau(self.handle, int(k), 1 if dagger else 0,
+                                d.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)))
+        return (s, int(out[0]) | (int(out[1]) << 64)) if s else (0, None)
 
     def run_energy(self, theta=None, eps=None, n_factors=None, n_max=None, n_cut=None):
         keys, amps, _ = self.apply(theta, eps, n_factors, n_max, n_cut)
@@ -188,15 +247,19 @@ class Oracle:
         n_max, n_cut = self._cut(n_max, n_cut)
         g = np.zeros(len(th))
         E = ctypes.c_double()
-        self.lib.orc_gradient(self.handle, _dp(th), float(eps), int(n_max), int(n_cut), int(stride),
+        self._f("gradient")(self.handle, _dp(th), float(eps), int(n_max), int(n_cut), int(stride),
                               ctypes.byref(E), _dp(g))
         return E.value, g
 
 
-def _export(lib, wf):
-    n = lib.orc_wf_size(wf)
-    keys = np.zeros(n, dtype=np.uint64)
-    amps = np.zeros(n, dtype=np.float64)
-    if n:
-        lib.orc_wf_export(wf, keys.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), _dp(amps))
-    return keys, amps
+def words(key: int) -> np.ndarray:
+    """A determinant key as its (low, high) 64-bit words."""
+    return np.array([key & 0xFFFFFFFFFFFFFFFF, key >> 64], dtype=np.uint64)
+
+
+def key_ints(keys) -> list:
+    """Keys (a uint64 array, or an (n, 2) array of (low, high) words) as Python integers."""
+    k = np.asarray(keys, dtype=np.uint64)
+    if k.ndim == 1:
+        return [int(x) for x in k]
+    return [int(lo) | (int(hi) << 64) for lo, hi in k]

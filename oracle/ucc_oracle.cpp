@@ -33,8 +33,14 @@
 //     two members of every rotated pair;
 //   * no renormalisation: E = <psi|H|psi>/<psi|psi>.
 //
-// Build: g++ -O2 -std=c++17 -ffp-contract=off -shared -fPIC (no fused
-// multiply-add, so each rotation is two rounded products and one rounded sum).
+// Build: g++ -O2 -std=c++17 -ffp-contract=off (no fused multiply-add, so each
+// rotation is two rounded products and one rounded sum), once with
+// ORC_KEY_BITS=64 (determinant keys in one 64-bit word, up to 64
+// spin-orbitals; entry points orc_*) and once with ORC_KEY_BITS=128 (keys in a
+// 128-bit integer, up to 128 spin-orbitals; entry points orc128_*, keys passed
+// as (low, high) pairs of 64-bit words), both linked into one library.  The
+// two builds are the same source: only the key type and the entry-point
+// names differ.
 // Parity: pinned by the tests in tests/test_oracle_*.py (dense state-vector
 // brute force, closed forms, invariants, finite differences and the exact
 // parameter-shift rule).
@@ -48,9 +54,42 @@
 #include <utility>
 #include <vector>
 
+#ifndef ORC_KEY_BITS
+#define ORC_KEY_BITS 64
+#endif
+
 namespace {
 
-typedef std::unordered_map<uint64_t, double> Psi;
+#if ORC_KEY_BITS == 64
+typedef uint64_t Key;
+typedef std::hash<uint64_t> KeyHash;
+#define ORC(name) orc_##name
+// Keys at the C boundary: one 64-bit word each.
+Key load_key(const uint64_t* a, long long t) { return a[t]; }
+void store_key(uint64_t* a, long long t, Key k) { a[t] = k; }
+#elif ORC_KEY_BITS == 128
+typedef unsigned __int128 Key;
+struct KeyHash {
+  size_t operator()(Key k) const {
+    const uint64_t lo = (uint64_t)k, hi = (uint64_t)(k >> 64);
+    return std::hash<uint64_t>()(lo ^ (hi * 0x9E3779B97F4A7C15ULL));
+  }
+};
+#define ORC(name) orc128_##name
+// Keys at the C boundary: two 64-bit words each, low word first.
+Key load_key(const uint64_t* a, long long t) { return ((Key)a[2 * t + 1] << 64) | (Key)a[2 * t]; }
+void store_key(uint64_t* a, long long t, Key k) {
+  a[2 * t] = (uint64_t)k;
+  a[2 * t + 1] = (uint64_t)(k >> 64);
+}
+#else
+#error "ORC_KEY_BITS must be 64 or 128"
+#endif
+
+constexpr int kKeyBits = ORC_KEY_BITS;
+Key bit(int p) { return (Key)1 << p; }
+
+typedef std::unordered_map<Key, double, KeyHash> Psi;
 
 struct Excitation {
   int i, j, a, b;  // j = b = -1 for a single
@@ -62,10 +101,10 @@ struct Problem {
   std::vector<double> g;  // n_spatial^4, chemist (pq|rs)
   std::vector<Excitation> exc;
   int n_so() const { return 2 * n_spatial; }
-  uint64_t reference() const {
-    uint64_t det = 0;
-    for (int s = 0; s < n_alpha; ++s) det |= 1ULL << (2 * s);
-    for (int s = 0; s < n_beta; ++s) det |= 1ULL << (2 * s + 1);
+  Key reference() const {
+    Key det = 0;
+    for (int s = 0; s < n_alpha; ++s) det |= bit(2 * s);
+    for (int s = 0; s < n_beta; ++s) det |= bit(2 * s + 1);
     return det;
   }
 };
@@ -79,35 +118,35 @@ struct Counts {
 };
 
 // ------------------------------------------------------------------------
-// Jordan-Wigner second quantisation on 64-bit determinant keys.
+// Jordan-Wigner second quantisation on determinant keys (bit p = spin-orbital p).
 // ------------------------------------------------------------------------
-bool is_occupied(uint64_t det, int p) { return ((det >> p) & 1ULL) != 0; }
+bool is_occupied(Key det, int p) { return ((det >> p) & 1) != 0; }
 
-int occupied_below(uint64_t det, int p) {
+int occupied_below(Key det, int p) {
   int count = 0;
   for (int q = 0; q < p; ++q)
     if (is_occupied(det, q)) ++count;
   return count;
 }
 
-bool annihilate(uint64_t& det, int p, int& sign) {
+bool annihilate(Key& det, int p, int& sign) {
   if (!is_occupied(det, p)) return false;
   if (occupied_below(det, p) % 2 == 1) sign = -sign;
-  det &= ~(1ULL << p);
+  det &= ~bit(p);
   return true;
 }
 
-bool create(uint64_t& det, int p, int& sign) {
+bool create(Key& det, int p, int& sign) {
   if (is_occupied(det, p)) return false;
   if (occupied_below(det, p) % 2 == 1) sign = -sign;
-  det |= (1ULL << p);
+  det |= bit(p);
   return true;
 }
 
 // tau |det> = sign |out>, operators applied right to left: a_i, a_j, a+_b, a+_a.
-bool apply_tau(const Excitation& e, uint64_t det, uint64_t* out, int* sign) {
+bool apply_tau(const Excitation& e, Key det, Key* out, int* sign) {
   int s = 1;
-  uint64_t d = det;
+  Key d = det;
   if (!annihilate(d, e.i, s)) return false;
   if (e.j >= 0 && !annihilate(d, e.j, s)) return false;
   if (e.b >= 0 && !create(d, e.b, s)) return false;
@@ -118,9 +157,9 @@ bool apply_tau(const Excitation& e, uint64_t det, uint64_t* out, int* sign) {
 }
 
 // tau^+ |det> = sign |out>, tau^+ = a+_i a+_j a_b a_a, applied right to left.
-bool apply_tau_dagger(const Excitation& e, uint64_t det, uint64_t* out, int* sign) {
+bool apply_tau_dagger(const Excitation& e, Key det, Key* out, int* sign) {
   int s = 1;
-  uint64_t d = det;
+  Key d = det;
   if (!annihilate(d, e.a, s)) return false;
   if (e.b >= 0 && !annihilate(d, e.b, s)) return false;
   if (e.j >= 0 && !create(d, e.j, s)) return false;
@@ -132,20 +171,20 @@ bool apply_tau_dagger(const Excitation& e, uint64_t det, uint64_t* out, int* sig
 
 // A linked pair of factor k: E is the member tau excites, D = tau E up to sign.
 struct Pair {
-  uint64_t E, D;
+  Key E, D;
   int sign;  // tau|E> = sign |D>
 };
 
 // Classify det under factor k.  Returns false if tau and tau^+ both kill it.
-bool pair_of(const Excitation& e, uint64_t det, Pair* out) {
-  uint64_t other;
+bool pair_of(const Excitation& e, Key det, Pair* out) {
+  Key other;
   int sign;
   if (apply_tau(e, det, &other, &sign)) {
     *out = Pair{det, other, sign};
     return true;
   }
   if (apply_tau_dagger(e, det, &other, &sign)) {
-    uint64_t back;
+    Key back;
     int s2;
     apply_tau(e, other, &back, &s2);  // the sign is defined from the excited side
     *out = Pair{other, det, s2};
@@ -154,7 +193,7 @@ bool pair_of(const Excitation& e, uint64_t det, Pair* out) {
   return false;
 }
 
-double value_or_zero(const Psi& psi, uint64_t key) {
+double value_or_zero(const Psi& psi, Key key) {
   auto it = psi.find(key);
   return it == psi.end() ? 0.0 : it->second;
 }
@@ -162,7 +201,7 @@ double value_or_zero(const Psi& psi, uint64_t key) {
 // ------------------------------------------------------------------------
 // One factor of Eq. 3 (Eqs. 4-5 in the rotation form) plus the eps rule.
 // ------------------------------------------------------------------------
-void store_or_drop(Psi& out, uint64_t key, double v, double eps, bool existed, Counts& cnt) {
+void store_or_drop(Psi& out, Key key, double v, double eps, bool existed, Counts& cnt) {
   if (std::fabs(v) < eps) {
     if (existed) {
       out.erase(key);
@@ -201,8 +240,8 @@ Psi apply_factor(const Excitation& e, double c, double s, double eps, const Psi&
 // remain, keep the n_cut of largest |c| (ties: smaller key first).
 void truncate_top(Psi& psi, long long n_max, long long n_cut, Counts& cnt) {
   if (n_max <= 0 || (long long)psi.size() <= n_max) return;
-  std::vector<std::pair<uint64_t, double>> all(psi.begin(), psi.end());
-  std::sort(all.begin(), all.end(), [](const std::pair<uint64_t, double>& x, const std::pair<uint64_t, double>& y) {
+  std::vector<std::pair<Key, double>> all(psi.begin(), psi.end());
+  std::sort(all.begin(), all.end(), [](const std::pair<Key, double>& x, const std::pair<Key, double>& y) {
     double ax = std::fabs(x.second), ay = std::fabs(y.second);
     if (ax != ay) return ax > ay;
     return x.first < y.first;
@@ -267,18 +306,18 @@ double anti(const Problem& P, int p, int q, int r, int s) { return phys(P, p, q,
 // The set bits of a key, ascending.
 struct Bits {
   int n = 0;
-  int p[64];
+  int p[kKeyBits];
 };
 
-Bits bits_of(uint64_t x) {
+Bits bits_of(Key x) {
   Bits out;
-  for (int q = 0; q < 64; ++q)
+  for (int q = 0; q < kKeyBits; ++q)
     if (is_occupied(x, q)) out.p[out.n++] = q;
   return out;
 }
 
 // <J|H|I>
-double hmat(const Problem& P, uint64_t I, uint64_t J) {
+double hmat(const Problem& P, Key I, Key J) {
   Bits holes = bits_of(I & ~J);      // occupied in I, empty in J
   Bits particles = bits_of(J & ~I);  // empty in I, occupied in J
   if (holes.n != particles.n || holes.n > 2) return 0.0;
@@ -293,7 +332,7 @@ double hmat(const Problem& P, uint64_t I, uint64_t J) {
   if (holes.n == 1) {
     int i = holes.p[0], a = particles.p[0];
     int sign = 1;
-    uint64_t d = I;
+    Key d = I;
     annihilate(d, i, sign);
     create(d, a, sign);
     double v = h_so(P, a, i);
@@ -303,7 +342,7 @@ double hmat(const Problem& P, uint64_t I, uint64_t J) {
   }
   int i = holes.p[0], j = holes.p[1], a = particles.p[0], b = particles.p[1];
   int sign = 1;
-  uint64_t d = I;
+  Key d = I;
   annihilate(d, i, sign);
   annihilate(d, j, sign);
   create(d, b, sign);
@@ -328,7 +367,7 @@ struct Sum {
 // sigma_I = sum_{J in psi} <I|H|J> c_J for one I (psi's keys only), by
 // generating every determinant one spin-conserving single or double away from
 // I and looking it up.
-double sigma_one(const Problem& P, const Psi& psi, uint64_t I) {
+double sigma_one(const Problem& P, const Psi& psi, Key I) {
   Bits occ = bits_of(I);
   Bits emp;
   for (int p = 0; p < P.n_so(); ++p)
@@ -339,7 +378,7 @@ double sigma_one(const Problem& P, const Psi& psi, uint64_t I) {
     for (int u = 0; u < emp.n; ++u) {
       int p = occ.p[x], q = emp.p[u];
       if ((p & 1) != (q & 1)) continue;
-      uint64_t J = (I & ~(1ULL << p)) | (1ULL << q);
+      Key J = (I & ~bit(p)) | bit(q);
       auto it = psi.find(J);
       if (it != psi.end()) acc.add(hmat(P, I, J) * it->second);
     }
@@ -349,7 +388,7 @@ double sigma_one(const Problem& P, const Psi& psi, uint64_t I) {
         for (int v = u + 1; v < emp.n; ++v) {
           int p = occ.p[x], q = occ.p[y], r = emp.p[u], s = emp.p[v];
           if ((p & 1) + (q & 1) != (r & 1) + (s & 1)) continue;
-          uint64_t J = (I & ~(1ULL << p) & ~(1ULL << q)) | (1ULL << r) | (1ULL << s);
+          Key J = (I & ~bit(p) & ~bit(q)) | bit(r) | bit(s);
           auto it = psi.find(J);
           if (it != psi.end()) acc.add(hmat(P, I, J) * it->second);
         }
@@ -423,12 +462,12 @@ void gradient(const Problem& P, const double* theta, double eps, long long n_max
       double c = std::cos(theta[k]), s = std::sin(theta[k]);
       // lambda = U_k^T mu on every pair touching mu's support; elsewhere lambda = mu.
       Psi lambda = mu;
-      std::unordered_set<uint64_t> candidates;
+      std::unordered_set<Key, KeyHash> candidates;
       for (const auto& kv : mu) candidates.insert(kv.first);
       for (const auto& kv : before) candidates.insert(kv.first);
-      std::unordered_set<uint64_t> done;
+      std::unordered_set<Key, KeyHash> done;
       Sum gk;
-      for (uint64_t key : candidates) {
+      for (Key key : candidates) {
         Pair p;
         if (!pair_of(e, key, &p)) continue;
         if (done.count(p.E)) continue;
@@ -454,12 +493,12 @@ void gradient(const Problem& P, const double* theta, double eps, long long n_max
 }
 
 struct WF {
-  std::vector<uint64_t> keys;
+  std::vector<Key> keys;
   std::vector<double> amps;
 };
 
 WF export_sorted(const Psi& psi) {
-  std::vector<std::pair<uint64_t, double>> all(psi.begin(), psi.end());
+  std::vector<std::pair<Key, double>> all(psi.begin(), psi.end());
   std::sort(all.begin(), all.end());
   WF w;
   for (const auto& kv : all) {
@@ -471,7 +510,13 @@ WF export_sorted(const Psi& psi) {
 
 Psi from_arrays(long long n, const uint64_t* keys, const double* amps) {
   Psi psi;
-  for (long long t = 0; t < n; ++t) psi[keys[t]] = amps[t];
+  for (long long t = 0; t < n; ++t) psi[load_key(keys, t)] = amps[t];
+  return psi;
+}
+
+Psi from_wf(const WF& w) {
+  Psi psi;
+  for (size_t t = 0; t < w.keys.size(); ++t) psi[w.keys[t]] = w.amps[t];
   return psi;
 }
 
@@ -483,7 +528,7 @@ struct orc_counts {
   long long rotations, created, dropped_new, dropped_old, cut;
 };
 
-void* orc_problem_new(int n_spatial, int n_alpha, int n_beta, const double* h, const double* g, int n_exc,
+void* ORC(problem_new)(int n_spatial, int n_alpha, int n_beta, const double* h, const double* g, int n_exc,
                       const int* exc) {
   Problem* P = new Problem;
   P->n_spatial = n_spatial;
@@ -496,11 +541,11 @@ void* orc_problem_new(int n_spatial, int n_alpha, int n_beta, const double* h, c
   return P;
 }
 
-void orc_problem_free(void* p) { delete static_cast<Problem*>(p); }
+void ORC(problem_free)(void* p) { delete static_cast<Problem*>(p); }
 
 // Apply factors [0, n_factors) to the reference; returns a wavefunction handle.
 // entropy_out (optional, n_factors doubles): Eq. 6 after each factor.
-void* orc_apply(const void* prob, const double* theta, int n_factors, double eps, long long n_max, long long n_cut,
+void* ORC(apply)(const void* prob, const double* theta, int n_factors, double eps, long long n_max, long long n_cut,
                 orc_counts* counts, double* entropy_out) {
   const Problem& P = *static_cast<const Problem*>(prob);
   Counts cnt;
@@ -511,63 +556,81 @@ void* orc_apply(const void* prob, const double* theta, int n_factors, double eps
   return new WF(export_sorted(psi));
 }
 
-void* orc_wf_from_arrays(long long n, const uint64_t* keys, const double* amps) {
+// keys: n keys at the C boundary (see load_key).
+void* ORC(wf_from_arrays)(long long n, const uint64_t* keys, const double* amps) {
   return new WF(export_sorted(from_arrays(n, keys, amps)));
 }
 
-long long orc_wf_size(const void* wf) { return (long long)static_cast<const WF*>(wf)->keys.size(); }
+long long ORC(wf_size)(const void* wf) { return (long long)static_cast<const WF*>(wf)->keys.size(); }
 
-void orc_wf_export(const void* wf, uint64_t* keys, double* amps) {
+void ORC(wf_export)(const void* wf, uint64_t* keys, double* amps) {
   const WF& w = *static_cast<const WF*>(wf);
-  if (!w.keys.empty()) {
-    std::memcpy(keys, w.keys.data(), w.keys.size() * sizeof(uint64_t));
-    std::memcpy(amps, w.amps.data(), w.amps.size() * sizeof(double));
-  }
+  for (size_t t = 0; t < w.keys.size(); ++t) store_key(keys, (long long)t, w.keys[t]);
+  if (!w.amps.empty()) std::memcpy(amps, w.amps.data(), w.amps.size() * sizeof(double));
 }
 
-void orc_wf_free(void* wf) { delete static_cast<WF*>(wf); }
+void ORC(wf_free)(void* wf) { delete static_cast<WF*>(wf); }
 
 // sigma over the wavefunction's keys (sorted by key), route 0 = generate and
 // look up, route 1 = all pairs.
-void orc_sigma(const void* prob, const void* wf, int route, double* sigma_out) {
+void ORC(sigma)(const void* prob, const void* wf, int route, double* sigma_out) {
   const Problem& P = *static_cast<const Problem*>(prob);
   const WF& w = *static_cast<const WF*>(wf);
-  Psi psi = from_arrays((long long)w.keys.size(), w.keys.data(), w.amps.data());
+  Psi psi = from_wf(w);
   Psi sigma = route == 1 ? sigma_pairwise(P, psi) : sigma_lookup(P, psi);
   for (size_t t = 0; t < w.keys.size(); ++t) sigma_out[t] = sigma.at(w.keys[t]);
 }
 
 // sigma_I for the n query keys I (each must be a key of the wavefunction or
 // not: sigma is P_S H psi evaluated at I either way).
-void orc_sigma_at(const void* prob, const void* wf, long long n, const uint64_t* query, double* out) {
+void ORC(sigma_at)(const void* prob, const void* wf, long long n, const uint64_t* query, double* out) {
   const Problem& P = *static_cast<const Problem*>(prob);
   const WF& w = *static_cast<const WF*>(wf);
-  Psi psi = from_arrays((long long)w.keys.size(), w.keys.data(), w.amps.data());
-  for (long long t = 0; t < n; ++t) out[t] = sigma_one(P, psi, query[t]);
+  Psi psi = from_wf(w);
+  for (long long t = 0; t < n; ++t) out[t] = sigma_one(P, psi, load_key(query, t));
 }
 
-void orc_energy(const void* prob, const void* wf, int route, double* E, double* norm2) {
+void ORC(energy)(const void* prob, const void* wf, int route, double* E, double* norm2) {
   const Problem& P = *static_cast<const Problem*>(prob);
   const WF& w = *static_cast<const WF*>(wf);
-  Psi psi = from_arrays((long long)w.keys.size(), w.keys.data(), w.amps.data());
+  Psi psi = from_wf(w);
   Psi sigma = route == 1 ? sigma_pairwise(P, psi) : sigma_lookup(P, psi);
   energy_from_sigma(psi, sigma, E, norm2);
 }
 
-double orc_hmat(const void* prob, uint64_t I, uint64_t J) {
+// <J|H|I> and tau_k |det> (which = 0) or tau_k^+ |det> (which = 1; returns
+// the sign, or 0 when the operator annihilates det).  The 64-bit build takes
+// keys by value; the 128-bit build takes pointers to (low, high) pairs.
+#if ORC_KEY_BITS == 64
+double ORC(hmat)(const void* prob, uint64_t I, uint64_t J) {
   return hmat(*static_cast<const Problem*>(prob), I, J);
 }
 
-// tau_k |det> (which = 0) or tau_k^+ |det> (which = 1): returns the sign, or 0
-// when the operator annihilates det.
-int orc_tau(const void* prob, int k, int which, uint64_t det, uint64_t* out) {
+int ORC(tau)(const void* prob, int k, int which, uint64_t det, uint64_t* out) {
   const Problem& P = *static_cast<const Problem*>(prob);
   int sign = 0;
-  bool ok = which == 0 ? apply_tau(P.exc[k], det, out, &sign) : apply_tau_dagger(P.exc[k], det, out, &sign);
+  Key o = 0;
+  bool ok = which == 0 ? apply_tau(P.exc[k], det, &o, &sign) : apply_tau_dagger(P.exc[k], det, &o, &sign);
+  *out = o;
   return ok ? sign : 0;
 }
+#else
+double ORC(hmat)(const void* prob, const uint64_t* I, const uint64_t* J) {
+  return hmat(*static_cast<const Problem*>(prob), load_key(I, 0), load_key(J, 0));
+}
 
-void orc_gradient(const void* prob, const double* theta, double eps, long long n_max, long long n_cut, int stride,
+int ORC(tau)(const void* prob, int k, int which, const uint64_t* det, uint64_t* out) {
+  const Problem& P = *static_cast<const Problem*>(prob);
+  int sign = 0;
+  Key o = 0;
+  const Key d = load_key(det, 0);
+  bool ok = which == 0 ? apply_tau(P.exc[k], d, &o, &sign) : apply_tau_dagger(P.exc[k], d, &o, &sign);
+  store_key(out, 0, o);
+  return ok ? sign : 0;
+}
+#endif
+
+void ORC(gradient)(const void* prob, const double* theta, double eps, long long n_max, long long n_cut, int stride,
                   double* E, double* grad) {
   gradient(*static_cast<const Problem*>(prob), theta, eps, n_max, n_cut, stride, E, grad);
 }
