@@ -82,6 +82,34 @@ def test_validation_rejects_too_many_orbitals(lib):
     assert st == UCC_EINVAL and "n_spatial" in msg
 
 
+def test_static_energy_rejects_on_the_host(lib):
+    """ucc_energy_static checks its sizes, counts and pointers before any
+    device call: oversized and empty inputs and null outputs are refused with
+    UCC_EINVAL and a message (the header's UCC_STATIC_MAX_DETS is the limit)."""
+    from paper_2301_05726_gb300._lib import UCC_EINVAL
+    src = open(os.path.join(ROOT, "include", "ucc.h")).read()
+    cap = int(re.search(r"#define UCC_STATIC_MAX_DETS (\d+)", src).group(1))
+    buf = np.zeros(8)
+    p = ctypes.c_void_p(buf.ctypes.data)
+    E, n2 = ctypes.c_double(), ctypes.c_double()
+
+    def call(n_spatial=6, n_det=16, sigma=p, e_nuc=0.0):
+        st = lib.ucc_energy_static(n_spatial, 2, 2, e_nuc, p, p, n_det, p, p, sigma, ctypes.byref(E),
+                                   ctypes.byref(n2), None)
+        return st, lib.ucc_last_error().decode()
+
+    st, msg = call(n_det=cap + 1)
+    assert st == UCC_EINVAL and str(cap) in msg
+    st, msg = call(n_det=0)
+    assert st == UCC_EINVAL and "n_det" in msg
+    st, msg = call(n_spatial=33)
+    assert st == UCC_EINVAL and "out of range" in msg
+    st, msg = call(sigma=None)
+    assert st == UCC_EINVAL and "null" in msg
+    st, msg = call(e_nuc=float("nan"))
+    assert st == UCC_EINVAL and "e_nuc" in msg
+
+
 def test_no_cpu_fallback_in_binding():
     # The binding has no path that computes without the library.
     src = open(os.path.join(ROOT, "paper_2301_05726_gb300", "api.py")).read()
