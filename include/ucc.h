@@ -201,8 +201,9 @@ ucc_status ucc_batch_run(int n_jobs, ucc_ctx* const* jobs, double eps, double* E
  *
  * Inputs (device pointers on the current device, owned by the caller): h
  * (n_spatial^2) and g (n_spatial^4, chemist order) as in ucc_hamiltonian;
- * keys[n_det] distinct determinants with n_alpha + n_beta electrons in
- * 2*n_spatial spin-orbitals, amps[n_det] finite amplitudes.  Outputs:
+ * keys[n_det] distinct determinants with n_alpha electrons on the even
+ * (alpha) and n_beta on the odd (beta) spin-orbitals below 2*n_spatial,
+ * amps[n_det] finite amplitudes.  Outputs:
  * sigma[n_det] (device) = P_S H psi at each key, *E = <psi|H|psi>/<psi|psi>
  * + e_nuc and *norm2 (host; norm2 may be NULL).  Work is enqueued on
  * cuda_stream and the call synchronises it before returning.
@@ -211,8 +212,10 @@ ucc_status ucc_batch_run(int n_jobs, ucc_ctx* const* jobs, double eps, double* E
  * scratch (hash slots over the keys, partial sums, counters, about 8.4 MB) is
  * one file-scope device array that every device loading the library holds
  * until the process exits.  The first call on a device, with that device
- * current, looks up the array's device address (cudaGetSymbolAddress); make
- * that first call before any stream capture.  Every call reuses the array
+ * current, looks up the array's device address (cudaGetSymbolAddress) and
+ * keeps it for the life of the library; make that first call before any
+ * stream capture.  Resetting the device (cudaDeviceReset) after that call is
+ * not supported: the module reloads and the kept address goes stale.  Every call reuses the array
  * and clears it first, so calls whose work overlaps on the GPU race: do not
  * run two at once on one device.  n_det above UCC_STATIC_MAX_DETS, or 0,
  * returns UCC_EINVAL; malformed keys or amplitudes return UCC_EINVAL. */

@@ -49,14 +49,17 @@ constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
 StaticScratch* g_addr[kMaxDevices] = {};
 
-// Checks the caller's keys (electron count, nonzero) and amplitudes (finite)
-// and records n in the counters.
+// Checks the caller's keys (n_alpha electrons on the even spin-orbitals,
+// n_beta on the odd ones, none past n_so) and amplitudes (finite) and records
+// n in the counters.
 __global__ void k_static_init(Counters* c, const unsigned long long* keys, const double* amps,
-                              unsigned long long n, int n_elec, int n_so) {
+                              unsigned long long n, int n_alpha, int n_beta, int n_so) {
+  constexpr unsigned long long kAlpha = 0x5555555555555555ull;  // spin-orbital p has spin p & 1
   const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
   for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     const unsigned long long k = keys[i];
-    const bool bad_key = __popcll(k) != n_elec || (n_so < 64 && (k >> n_so) != 0ull);
+    const bool bad_key = __popcll(k & kAlpha) != n_alpha || __popcll(k & ~kAlpha) != n_beta ||
+                         (n_so < 64 && (k >> n_so) != 0ull);
     if (bad_key || !isfinite(amps[i])) atomicOr(&c->error, ERR_CONSISTENCY);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -87,7 +90,9 @@ extern "C" ucc_status ucc_energy_static(int32_t n_spatial, int32_t n_alpha, int3
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
     return err(UCC_ECUDA, "no usable current device");
   // Set-up, once per device, with that device current: the scratch's device
-  // address.
+  // address.  The address is cached for the life of the library: a device
+  // reset (cudaDeviceReset) unloads the module and would leave it stale, so
+  // resetting a device that has called this entry point is not supported.
   StaticScratch* S = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_setup_mutex);
@@ -104,7 +109,7 @@ extern "C" ucc_status ucc_energy_static(int32_t n_spatial, int32_t n_alpha, int3
     return err(UCC_ECUDA, "clearing the scratch failed");
   const int n_so = 2 * n_spatial;
   k_static_init<<<kStaticGrid, 256, 0, st>>>(&S->cnt, (const unsigned long long*)keys, amps,
-                                             (unsigned long long)n_det, n_alpha + n_beta, n_so);
+                                             (unsigned long long)n_det, n_alpha, n_beta, n_so);
   Table t{};
   t.keys = const_cast<unsigned long long*>((const unsigned long long*)keys);
   t.amps = const_cast<double*>(amps);
@@ -132,8 +137,8 @@ extern "C" ucc_status ucc_energy_static(int32_t n_spatial, int32_t n_alpha, int3
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return err(UCC_ECUDA, std::string("energy pass failed: ") + cudaGetErrorString(e));
   if (host.error & ERR_CONSISTENCY)
-    return err(UCC_EINVAL, "keys must be distinct determinants with n_alpha + n_beta electrons in 2*n_spatial "
-                           "spin-orbitals, amplitudes finite");
+    return err(UCC_EINVAL, "keys must be distinct determinants with n_alpha electrons on the even and n_beta on "
+                           "the odd spin-orbitals below 2*n_spatial, amplitudes finite");
   if (host.error) return err(UCC_ECUDA, "device error word " + std::to_string(host.error));
   if (!(host.norm2 > 0.0)) return err(UCC_EINVAL, "zero wavefunction");
   *E = host.e_num / host.norm2 + e_nuc;

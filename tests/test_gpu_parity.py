@@ -359,3 +359,55 @@ def test_entropy_per_factor(torch_cuda, case):
     S = ctx.entropy()
     assert np.max(np.abs(S - S_ref)) <= 1e-10
     assert S_ref[-1] > 0.0
+
+
+# ---------------------------------------------------------------------------
+# The benchmarked configuration: 64 spin-orbitals, eps = 1e-6, with the cut
+# ---------------------------------------------------------------------------
+def test_gradient_64so_with_cut_vs_oracle(torch_cuda):
+    # The first 400 factors of the 64-spin-orbital workload with the paper's own
+    # production cut (N_MAX = 8,000, N_CUT = 5,000; Methods section): the cut
+    # fires after most factors, so this runs the bench's path -- one tape over
+    # the whole run with the cut's records, in-place inverse rotations, lone
+    # members divided by cos(theta), bulk re-insertion of cut records.
+    prob = synth.config_problem(4).prefix(400)
+    n_max, n_cut = 8000, 5000
+    o = oracle_for(prob)
+    ok, oa, oc = o.apply(n_max=n_max, n_cut=n_cut)
+    E_ref, g_ref = o.gradient(n_max=n_max, n_cut=n_cut)
+    assert oc["cut"] > 100 * n_cut
+    ctx = ctx_for(prob)
+    ctx.set_options(n_max=n_max, n_cut=n_cut)
+    ctx.apply()
+    gk, ga = ctx.wavefunction()
+    assert_same_state(gk, ga, ok, oa)
+    assert ctx.stats()["cut"] == oc["cut"]
+    E, g = ctx.gradient()
+    assert abs(E - E_ref) <= E_TOL
+    assert np.max(np.abs(g - g_ref)) <= G_TOL
+    st = ctx.stats()
+    assert st["recompute_rotations"] == 0 and st["tape_entries"] >= oc["cut"]
+
+
+def test_one_tape_vs_sqrt_k_checkpoints_64so(torch_cuda):
+    # 1,500 factors of the 64-spin-orbital workload with a cut that fires every
+    # few factors (N_MAX = 1e6, N_CUT = 6.25e5): the one-tape sweep undoes
+    # every factor in place (inverse rotations, 1/cos(theta) on lone members),
+    # the checkpointed sweep recomputes each sqrt(K)-long segment forward from
+    # a snapshot.  The two gradients differ only by the round-off the in-place
+    # inversion accumulates.
+    prob = synth.config_problem(4).prefix(1500)
+    ctx = ctx_for(prob)
+    ctx.set_options(n_max=1_000_000, n_cut=625_000)
+    E1, g1 = ctx.gradient()
+    st1 = ctx.stats()
+    assert st1["cut"] > 0 and st1["recompute_rotations"] == 0
+    stride = int(np.ceil(np.sqrt(prob.n_exc)))
+    ctx.set_options(checkpoint_stride=stride)
+    E2, g2 = ctx.gradient()
+    st2 = ctx.stats()
+    assert st2["recompute_rotations"] > 0
+    assert abs(E1 - E2) <= 1e-12  # the same state; sigma sums in a different order
+    drift = np.max(np.abs(g1 - g2))
+    print(f"one tape vs sqrt(K) checkpoints: max |dg| = {drift:.3e} (|g|max = {np.max(np.abs(g1)):.3e})")
+    assert drift <= 1e-10
