@@ -47,6 +47,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--plain-components", type=int, default=2,
+                    help="theta components timed by central differences on the main workload")
+    ap.add_argument("--no-n1", action="store_true", help="skip the 40-spin-orbital adjoint/batched vs plain leg")
+    ap.add_argument("--n1-fd-components", type=int, default=8)
+    ap.add_argument("--n1-batch", type=int, default=4, help="theta vectors in the 40-spin-orbital batched leg")
     return ap.parse_args()
 
 
@@ -166,27 +171,71 @@ def oracle_sample(prob, seconds, with_grad=True, n_factors=None):
     return rot / dt, 1.0 / dt, nf, dt
 
 
+# The CPU oracle's sample of the 64-spin-orbital workload, the same in the CPU-baseline leg and in the
+# reference arm: its first 40 factors (apply + energy + adjoint, a few seconds on one core).
+ORACLE_PREFIX = 40
+
+# Bytes the library uploads per factor when theta comes from the host (the factor table entry: masks,
+# Jordan-Wigner parity terms, cos, sin and 1/cos).
+FACTOR_BYTES = 56
+
+
+def host_info():
+    """The host the oracle runs on: logical CPUs and the CPU model."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if model is None:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith(("model name", "cpu model")):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    return {"nproc": os.cpu_count(), "cpu_model": model, "machine": os.uname().machine}
+
+
+def oracle_leg(prob, repeats):
+    """The oracle on the fixed prefix, `repeats` times: (median rate, median seconds, description)."""
+    nf = min(ORACLE_PREFIX, prob.n_exc)
+    runs = [oracle_time(prob, nf) for _ in range(repeats)]
+    runs.sort(key=lambda r: r[1])
+    rot, dt = runs[len(runs) // 2]
+    desc = (f"{prob.name}: first {nf} of {prob.n_exc} factors (cut n_max={prob.n_max}, n_cut={prob.n_cut}), "
+            f"apply + energy + adjoint, median of {repeats}: {dt:.2f} s")
+    return rot / dt, dt, desc
+
+
+def workload_config(prob):
+    return {"workload": prob.name, "n_so": prob.n_so, "n_elec": prob.n_elec, "n_factors": prob.n_exc,
+            "eps": prob.eps, "n_max": prob.n_max, "n_cut": prob.n_cut}
+
+
 def run_reference(args, prob):
     import torch  # noqa: F401  (same environment as the other arm)
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    per_step = max(1.0, 60.0 / max(1, args.steps + args.warmup))
-    nf_fixed = oracle_prefix(prob, per_step)[0]  # one calibration; every step then runs the same prefix
-    rates = []
-    desc = None
+    rates, desc = [], None
     for s in range(args.warmup + args.steps):
-        r, evals, nf, dt = oracle_sample(prob, per_step, n_factors=nf_fixed)
+        r, dt, desc = oracle_leg(prob, 1)
         if s >= args.warmup:
             rates.append(r)
-            desc = f"{prob.name} first {nf} of {prob.n_exc} factors: apply + energy + adjoint, {dt:.1f}s"
     val = sorted(rates)[len(rates) // 2]
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": prob.name, "n_so": prob.n_so, "n_elec": prob.n_elec, "n_factors": prob.n_exc,
-                       "eps": prob.eps},
-            "cpu_baseline": {"kind": "oracle", "value": val, "unit": UNIT, "cores": 1, "sample": desc},
+            "config": dict(workload_config(prob), parallelism="single"),
+            "cpu_baseline": {"kind": "oracle", "value": val, "unit": UNIT, "cores": 1, "sample": desc,
+                             "host": host_info()},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -195,10 +244,11 @@ def flush_l2(buf):
     buf.add_(1.0)
 
 
-# DRAM traffic per algorithmic byte of a kernel, from one ncu capture of every launch of one evaluation
-# of the 1000-factor prefix (profiles/k_reverse_traffic_64so_prefix1000.md); a launch's traffic is taken
-# as this ratio times its algorithmic bytes.  To be re-measured (or removed) whenever the kernel changes.
-TRAFFIC_PER_ALGORITHMIC_BYTE = {"k_reverse": 1.75}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per algorithmic byte of a kernel, from one
+# ncu capture of a few launches of that kernel alone on a full-size table; a launch's traffic is taken as
+# this ratio times its algorithmic bytes.  Empty (traffic reported as null) until the current build of
+# the kernel has been captured.
+TRAFFIC_PER_ALGORITHMIC_BYTE = {}
 
 
 def _roofline(kernel, bytes_, ms, launches, hbm, peak_kind):
@@ -210,7 +260,120 @@ def _roofline(kernel, bytes_, ms, launches, hbm, peak_kind):
             "avg_launch_ms": ms / max(1, launches), "algorithmic_bytes": bytes_, "total_ms": ms}
 
 
+def byte_models(tot):
+    """Algorithmic bytes of the timed steps for the three kernels, in two models.
+
+    pair model: every rotation is charged a full pair (both members' amplitudes read and written and a
+    slot probe, 48 B; the reverse step also both adjoints, 80 B), whether or not the partner is stored.
+    member model: a rotation whose partner is absent (created, or computed below eps and never stored)
+    touches only its own member (16 B forward: amplitude read and write; 32 B reverse: amplitude and
+    adjoint read and written); a stored pair is charged as in the pair model.  Both charge 8 B per key
+    scanned and 32 B per created entry (key and amplitude written, slot claimed)."""
+    scanned = tot["scanned"] + tot["recompute_scanned"]
+    rot = tot["rotations"] + tot["recompute_rotations"]
+    cre = tot["created"] + tot["recompute_created"]
+    lone = min(rot, tot["created"] + tot["dropped_new"] + tot["recompute_created"])
+    both = rot - lone
+    rev_lone = min(tot["reverse_pairs"], tot["dropped_new"])
+    rev_both = tot["reverse_pairs"] - rev_lone
+    sig = 24.0 * tot["n_det"] + 16.0 * tot["sigma_hits"]
+    return {
+        "pair": {"k_forward": 8.0 * scanned + 48.0 * rot + 32.0 * cre, "k_sigma": sig,
+                 "k_reverse": 8.0 * tot["scanned"] + 80.0 * tot["reverse_pairs"]},
+        "member": {"k_forward": 8.0 * scanned + 16.0 * lone + 48.0 * both + 32.0 * cre, "k_sigma": sig,
+                   "k_reverse": 8.0 * tot["scanned"] + 32.0 * rev_lone + 80.0 * rev_both},
+    }
+
+
+def plain_fd(ctx, prob, m, h=1e-6, seed=7):
+    """Per-theta central differences on the GPU through the public API, timed on m randomly chosen
+    components (2m energy evaluations: theta uploaded, apply, energy), and the extrapolation to all
+    2K + 1 evaluations of a full gradient."""
+    import numpy as np
+    import torch
+    rng = np.random.default_rng(seed)
+    comps = rng.choice(prob.n_exc, size=min(m, prob.n_exc), replace=False)
+    th = np.array(prob.theta, dtype=np.float64)
+    fd = []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in comps:
+        e = []
+        for sgn in (1.0, -1.0):
+            tt = th.copy()
+            tt[k] += sgn * h
+            ctx.set_theta(tt)
+            ctx.apply()
+            e.append(ctx.energy()[0])
+        fd.append((e[0] - e[1]) / (2 * h))
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    ctx.set_theta(th)
+    n_eval = 2 * len(comps)
+    return {"components": [int(k) for k in comps], "energy_evaluations": n_eval, "seconds": dt,
+            "s_per_energy_evaluation": dt / n_eval,
+            "extrapolated_gradient_s": dt / n_eval * (2 * prob.n_exc + 1)}, np.array(fd)
+
+
+def timed_gradients(ctx, n, out=None):
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(n):
+        E, g = ctx.gradient(out=out)
+    torch.cuda.synchronize()
+    return (time.perf_counter() - t0) / n, E, g
+
+
+def n1_leg(args):
+    """The 40-spin-orbital workload (12 electrons, 9,954 factors, eps = 1e-8, the cut, gradient with
+    sqrt(K) checkpointing): one adjoint gradient against per-theta central differences (timed on a
+    random subset of components), and the batched form on several theta vectors."""
+    import math
+    import numpy as np
+    from paper_2301_05726_gb300 import synth
+    from paper_2301_05726_gb300.api import UCCContext, batch_run
+    prob = synth.config_problem(3)
+    stride = int(math.ceil(math.sqrt(prob.n_exc)))
+    ctx = UCCContext(prob)
+    ctx.set_options(checkpoint_stride=stride)
+    ctx.gradient()  # warm-up
+    t_adj, E, g = timed_gradients(ctx, 2)
+    st = ctx.stats()
+    plain, fd = plain_fd(ctx, prob, args.n1_fd_components)
+    comps = plain["components"]
+    out = {"workload": prob.name, "n_so": prob.n_so, "n_elec": prob.n_elec, "n_factors": prob.n_exc,
+           "eps": prob.eps, "n_max": prob.n_max, "n_cut": prob.n_cut, "checkpoint_stride": stride,
+           "n_det": st["n_det"], "adjoint_gradient_s": t_adj, "plain": plain,
+           "fd_vs_adjoint_max_abs": float(np.max(np.abs(fd - g[comps]))) if len(comps) else None,
+           "speedup_adjoint_vs_plain": plain["extrapolated_gradient_s"] / t_adj, "target": 20.0}
+    # Batched form: B theta vectors of the same problem (each its own context) in one call.
+    B = args.n1_batch
+    if B > 0:
+        rng = np.random.default_rng(11)
+        jobs = []
+        for b in range(B):
+            th = prob.theta * (1.0 + 0.01 * rng.standard_normal(prob.n_exc))
+            c = UCCContext(prob.with_theta(th))
+            c.set_options(checkpoint_stride=stride)
+            jobs.append(c)
+        batch_run(jobs, prob.eps, with_grad=True)  # warm-up
+        import torch
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        batch_run(jobs, prob.eps, with_grad=True)
+        torch.cuda.synchronize()
+        tb = time.perf_counter() - t0
+        out["batched"] = {"jobs": B, "seconds": tb, "gradient_s_per_job": tb / B,
+                          "speedup_vs_plain": plain["extrapolated_gradient_s"] / (tb / B)}
+        for c in jobs:
+            c.close()
+    ctx.close()
+    return out
+
+
 def run_ours(args, prob):
+    import numpy as np
     import torch
     import torch.distributed as dist
 
@@ -270,12 +433,12 @@ def run_ours(args, prob):
     # Replicas: the slowest rank's step time, the work of all ranks.
     from paper_2301_05726_gb300.replicas import combine_step
     ms, rot_all = combine_step(ms, tot["rotations"] / n_steps, device=dev)
-    rot_per_eval = tot["rotations"] / n_steps
     value = rot_all / (ms / 1e3)
+    g_dev = grad_dev.cpu().numpy()
 
-    # End to end through the public API with host buffers.
+    # End to end through the public API with host buffers (a few steps).
     e2e_times = []
-    for _ in range(0 if args.no_e2e else max(1, args.steps)):
+    for _ in range(0 if args.no_e2e else max(1, min(args.steps, 3))):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ctx.set_theta(theta_host.numpy())
@@ -284,68 +447,65 @@ def run_ours(args, prob):
         e2e_times.append(time.perf_counter() - t0)
     e2e_ms = 1e3 * sum(e2e_times) / len(e2e_times) if e2e_times else float("nan")
 
-    # "Plain": per-theta central differences on the GPU need 2K + 1 energy
-    # evaluations (apply + energy); one is measured, the total extrapolated.
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    ctx.apply()
-    ctx.energy()
-    torch.cuda.synchronize()
-    energy_eval_s = time.perf_counter() - t0
-    plain_s = (2 * prob.n_exc + 1) * energy_eval_s
+    # "Plain": per-theta central differences on the GPU (2K + 1 energy evaluations per gradient), timed on
+    # a random subset of components through the public API and extrapolated.
+    plain = None
+    if args.plain_components > 0:
+        plain, fd = plain_fd(ctx, prob, args.plain_components)
+        plain["fd_vs_adjoint_max_abs"] = float(np.max(np.abs(fd - g_dev[plain["components"]])))
+        plain["adjoint_gradient_s"] = ms / 1e3
+        plain["speedup_adjoint_vs_plain"] = plain["extrapolated_gradient_s"] / (ms / 1e3)
+    ctx.close()
+
+    n1 = None
+    if rank == 0 and not args.no_n1:
+        n1 = n1_leg(args)
 
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
         return
     hbm, peak_kind = peaks()
-    fwd_bytes = 8.0 * (tot["scanned"] + tot["recompute_scanned"]) + \
-        48.0 * (tot["rotations"] + tot["recompute_rotations"]) + 32.0 * (tot["created"] + tot["recompute_created"])
-    # per stored determinant: key + amplitude read, sigma written; per connected stored pair (visited once):
-    # the partner amplitude read and one sigma update
-    sig_bytes = 24.0 * tot["n_det"] + 16.0 * tot["sigma_hits"]
-    # per pair as in the forward step plus lam of both members; the scan term counts the entries of psi_k
-    # (the forward step's scan), not the dropped entries the sweep carries until it compacts
-    rev_bytes = 8.0 * tot["scanned"] + 80.0 * tot["reverse_pairs"]
-    kernels = {
-        "k_forward": _roofline("k_forward", fwd_bytes, tot["forward_kernel_ms"], tot["forward_launches"], hbm,
-                               peak_kind),
-        "k_sigma": _roofline("k_sigma", sig_bytes, tot["energy_ms"], n_steps, hbm, peak_kind),
-        "k_reverse": _roofline("k_reverse", rev_bytes, tot["reverse_kernel_ms"], tot["reverse_launches"], hbm,
-                               peak_kind),
-    }
-    dom = max(kernels.values(), key=lambda r: r["total_ms"])
+    models = byte_models(tot)
+    kernel_ms = {"k_forward": (tot["forward_kernel_ms"], tot["forward_launches"]),
+                 "k_sigma": (tot["energy_ms"], n_steps),
+                 "k_reverse": (tot["reverse_kernel_ms"], tot["reverse_launches"])}
+    kernels = {m: {k: _roofline(k, models[m][k], t, n, hbm, peak_kind) for k, (t, n) in kernel_ms.items()}
+               for m in models}
+    dom = max(kernels["member"].values(), key=lambda r: r["total_ms"])
     roof = {k: dom[k] for k in ("bound", "achieved", "peak", "unit", "frac", "traffic", "kernel", "peak_kind",
                                 "avg_launch_ms")}
+    roof["byte_model"] = "member (a rotation whose partner is absent is charged its own member only)"
+    roof["frac_pair_model"] = kernels["pair"][dom["kernel"]]["frac"]
     cpu = None
     if not args.no_cpu_baseline:
-        r, evals, nf, dt = oracle_sample(prob, args.cpu_seconds)
-        cpu = {"value": r, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{prob.name}: first {nf} of {prob.n_exc} factors, apply + energy + adjoint in {dt:.1f}s"}
+        r, dt, desc = oracle_leg(prob, 3)
+        cpu = {"value": r, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc, "host": host_info()}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": prob.name, "n_so": prob.n_so, "n_elec": prob.n_elec, "n_factors": prob.n_exc,
-                   "eps": prob.eps, "n_max": prob.n_max, "n_cut": prob.n_cut, "n_det": tot["n_det"] // n_steps,
-                   "l2": "table larger than L2 + 256 MB flush per step",
-                   "parallelism": "replicas" if world > 1 else "single"},
+        "config": dict(workload_config(prob), n_det=tot["n_det"] // n_steps,
+                       l2="table larger than L2 + 256 MB flush per step",
+                       parallelism="replicas" if world > 1 else "single"),
         "evals_per_s": world * 1e3 / ms,
         "apply_det_rotations_per_s": tot["rotations"] / (tot["apply_ms"] / 1e3) if tot["apply_ms"] > 0 else None,
         "phase_ms": {"forward": tot["apply_ms"] / n_steps, "energy": tot["energy_ms"] / n_steps,
-                     "reverse_incl_recompute": tot["reverse_ms"] / n_steps},
-        "vs_plain": {"plain": "per-theta central differences on the GPU, 2K+1 energy evaluations",
-                     "energy_eval_s": energy_eval_s, "plain_gradient_s_extrapolated": plain_s,
-                     "adjoint_gradient_s": ms / 1e3, "speedup": plain_s / (ms / 1e3)},
-        "e2e": {"value": rot_all / (e2e_ms / 1e3), "unit": UNIT,
-                "h2d_bytes_per_step": 48 * prob.n_exc, "d2h_bytes_per_step": 8 * prob.n_exc + 8},
+                     "reverse_incl_recompute": tot["reverse_ms"] / n_steps,
+                     "forward_kernels": tot["forward_kernel_ms"] / n_steps,
+                     "reverse_kernels": tot["reverse_kernel_ms"] / n_steps},
+        "vs_plain": plain,
+        "n1_40so": n1,
+        "e2e": {"value": rot_all / (e2e_ms / 1e3), "unit": UNIT, "steps": len(e2e_times),
+                "h2d_bytes_per_step": FACTOR_BYTES * prob.n_exc, "d2h_bytes_per_step": 8 * prob.n_exc + 8},
         "gpu_launches": int(tot["kernel_launches"]),
         "counts_per_step": {k: int(tot[k] // n_steps) for k in (
             "rotations", "created", "dropped_new", "dropped_old", "cut", "scanned", "rebuilds", "tape_entries",
-            "sigma_probes", "sigma_hits", "reverse_pairs", "reverse_scanned", "recompute_rotations")},
+            "sigma_probes", "sigma_hits", "reverse_pairs", "reverse_scanned", "recompute_rotations",
+            "forward_launches", "reverse_launches")},
         "roofline": roof,
-        "kernels": {k: {x: v[x] for x in ("achieved", "frac", "launches", "avg_launch_ms", "total_ms")}
-                    for k, v in kernels.items()},
+        "kernels": {m: {k: {x: v[x] for x in ("achieved", "frac", "launches", "avg_launch_ms", "total_ms")}
+                        for k, v in ks.items()} for m, ks in kernels.items()},
         "clocks": clocks,
         "cpu_baseline": cpu,
     }

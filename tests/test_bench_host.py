@@ -44,7 +44,25 @@ def test_oracle_sample_reuses_a_fixed_prefix(monkeypatch):
     assert seen == [54] and nf == 54 and rate == 10 * 54 / 0.5 and evals == 2.0
 
 
-def test_traffic_is_scaled_from_algorithmic_bytes():
+def test_traffic_is_scaled_from_algorithmic_bytes(monkeypatch):
+    monkeypatch.setattr(bench, "TRAFFIC_PER_ALGORITHMIC_BYTE", {"k_reverse": 1.5})
     r = bench._roofline("k_reverse", 4e9, 10.0, 4, 6000.0, "measured")
-    assert r["traffic"] == bench.TRAFFIC_PER_ALGORITHMIC_BYTE["k_reverse"] * 1e9
+    assert r["traffic"] == 1.5 * 1e9
     assert bench._roofline("k_sigma", 1e9, 10.0, 1, 6000.0, "measured")["traffic"] is None
+
+
+def test_member_model_charges_lone_rotations_one_member():
+    tot = dict(scanned=1000, recompute_scanned=0, rotations=100, recompute_rotations=0, created=10,
+               recompute_created=0, dropped_new=80, reverse_pairs=100, n_det=50, sigma_hits=7)
+    m = bench.byte_models(tot)
+    # 90 lone rotations (10 created + 80 dropped), 10 with both members stored
+    assert m["pair"]["k_forward"] == 8 * 1000 + 48 * 100 + 32 * 10
+    assert m["member"]["k_forward"] == 8 * 1000 + 16 * 90 + 48 * 10 + 32 * 10
+    assert m["pair"]["k_reverse"] == 8 * 1000 + 80 * 100
+    assert m["member"]["k_reverse"] == 8 * 1000 + 32 * 80 + 80 * 20
+    assert m["member"]["k_sigma"] == m["pair"]["k_sigma"] == 24 * 50 + 16 * 7
+
+
+def test_host_info_names_the_cpu():
+    h = bench.host_info()
+    assert h["nproc"] >= 1 and h["machine"]
