@@ -97,7 +97,18 @@ typedef struct {
                                 budget, else ceil(sqrt(K)) */
   int32_t tape_budget_mb;    /* kill-tape budget in MiB; 0 = 60% of free memory */
   int32_t record_entropy;    /* ucc_apply records Eq. 6 after every factor */
-  int32_t reserved[2];
+  int32_t batch_wait_ms;     /* ucc_batch_run: bound of one grid-barrier wait of
+                                its persistent launches, in ms; 0 = 2000.  Read
+                                from the first job. */
+  int32_t batch_test_skip_block; /* test only: block (1-based) of the batch's
+                                    persistent forward launch that leaves
+                                    before its first grid barrier, so that the
+                                    others' bounded waits run out and the call
+                                    returns UCC_ETIMEOUT; 0 = none */
+  int32_t batch_tiles;       /* ucc_batch_run: 32-entry tiles a warp takes per
+                                visit of a job (1, 2, 4 or 8); 0 = autotuned.
+                                Read from the first job. */
+  int32_t pad_;
 } ucc_options;
 
 /* Counters of the last apply / gradient call. */
@@ -131,6 +142,11 @@ typedef struct {
   double reverse_ms;        /* device time of the last reverse sweep */
   double forward_kernel_ms; /* device time of the forward factor launches alone */
   double reverse_kernel_ms; /* device time of the reverse factor launches alone */
+  int64_t batch_tiles;      /* ucc_batch_run: 32-entry tiles a warp takes per
+                               visit of a job (fixed by the autotuner) */
+  double cut_ms;            /* device time of the Methods-section cuts (selection,
+                               compaction, rehash) of the last forward pass */
+  double rebuild_ms;        /* device time of the other compactions and growths */
 } ucc_stats;
 
 /* Create a context: validate and upload the problem (h, g, the factor table
@@ -184,8 +200,17 @@ ucc_status ucc_get_entropy(ucc_ctx* ctx, double* S, int32_t n);
 ucc_status ucc_get_stats(const ucc_ctx* ctx, ucc_stats* out);
 
 /* Energies and gradients of n_jobs independent contexts (molecules or theta
- * vectors of uneven size) from one persistent launch per phase: E[j] and
- * grads[j][0..n_exc_j) (host pointers; grads may be NULL for energy only).
+ * vectors of uneven size): E[j] and grads[j][0..n_exc_j) (host pointers;
+ * grads may be NULL for energy only).  Every job whose table can be sized up
+ * front (three times its determinant sector, or four times its n_max when its
+ * Methods-section cut can fire; at most 2^26 entries) runs in one cooperative
+ * persistent launch per pass (forward, energy, reverse) inside a captured CUDA
+ * graph: each step applies one factor of every job, and each job's cut and
+ * compactions run on the device.  The forward launch is repeated only when
+ * jobs wait for more kill tape.  Probe width and tiles per warp are tuned on
+ * the first call for a batch shape.  The other jobs run one by one in the
+ * same call.  Grid barriers wait at most batch_wait_ms (first job's options);
+ * a wait that runs out returns UCC_ETIMEOUT and leaves the contexts usable.
  * All contexts must live on the same device and use the same stream as
  * jobs[0].  Synchronises. */
 ucc_status ucc_batch_run(int n_jobs, ucc_ctx* const* jobs, double eps, double* E, double* const* grads);

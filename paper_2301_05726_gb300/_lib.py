@@ -36,7 +36,8 @@ class Options(ctypes.Structure):
     _fields_ = [("n_max", ctypes.c_int64), ("n_cut", ctypes.c_int64), ("max_entries", ctypes.c_int64),
                 ("probe_width", ctypes.c_int32), ("checkpoint_stride", ctypes.c_int32),
                 ("tape_budget_mb", ctypes.c_int32), ("record_entropy", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("batch_wait_ms", ctypes.c_int32), ("batch_test_skip_block", ctypes.c_int32),
+                ("batch_tiles", ctypes.c_int32), ("pad_", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -46,7 +47,8 @@ class Stats(ctypes.Structure):
         "reverse_pairs", "recompute_scanned", "recompute_rotations", "recompute_created", "forward_launches",
         "reverse_launches", "probe_width", "reverse_scanned", "reverse_compactions")] + \
         [(n, ctypes.c_double) for n in ("apply_ms", "energy_ms", "reverse_ms", "forward_kernel_ms",
-                                        "reverse_kernel_ms")]
+                                        "reverse_kernel_ms")] + [("batch_tiles", ctypes.c_int64)] + \
+        [(n, ctypes.c_double) for n in ("cut_ms", "rebuild_ms")]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}

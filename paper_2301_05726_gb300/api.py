@@ -53,7 +53,8 @@ class UCCContext:
         self.handle = handle
         self._opt = dict(n_max=int(getattr(prob, "n_max", 0)), n_cut=int(getattr(prob, "n_cut", 0)),
                          max_entries=int(max_entries), probe_width=int(probe_width), checkpoint_stride=0,
-                         tape_budget_mb=0, record_entropy=0)
+                         tape_budget_mb=0, record_entropy=0, batch_wait_ms=0, batch_test_skip_block=0,
+                         batch_tiles=0)
         self.set_options()
 
     def close(self):
@@ -67,14 +68,16 @@ class UCCContext:
     def set_options(self, **changes):
         """Update run options (the rest keep their values): n_max, n_cut,
         max_entries, probe_width, checkpoint_stride, tape_budget_mb,
-        record_entropy.  The problem's own cut is the starting point."""
+        record_entropy, batch_wait_ms, batch_test_skip_block, batch_tiles.  The problem's
+        own cut is the starting point."""
         unknown = set(changes) - set(self._opt)
         if unknown:
             raise TypeError(f"unknown options {sorted(unknown)}")
         self._opt.update({k: int(v) for k, v in changes.items()})
         o = self._opt
         o = Options(o["n_max"], o["n_cut"], o["max_entries"], o["probe_width"], o["checkpoint_stride"],
-                    o["tape_budget_mb"], o["record_entropy"])
+                    o["tape_budget_mb"], o["record_entropy"], o["batch_wait_ms"], o["batch_test_skip_block"],
+                    o["batch_tiles"], 0)
         check(self.lib.ucc_set_options(self.handle, ctypes.byref(o)))
 
     def set_theta(self, theta):

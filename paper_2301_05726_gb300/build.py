@@ -18,7 +18,8 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libucc.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["ucc_api.cu", "k_apply.cu", "k_energy.cu", "k_adjoint.cu", "k_select.cu", "k_batch.cu", "ucc_static.cu"]
+SOURCES = ["ucc_api.cu", "k_apply.cu", "k_energy.cu", "k_adjoint.cu", "k_select.cu", "k_batch.cu", "k_persist.cu",
+           "ucc_static.cu"]
 HEADERS = ["ucc_internal.h", "ucc_device.cuh", "ucc_steps.cuh"]
 
 
@@ -41,7 +42,14 @@ def _stale(target, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
+# Per-file flags.  The persistent batched kernels read, after a grid barrier,
+# tables that other SMs rewrote earlier in the same launch: their global loads
+# are cached in L2 only (no stale L1 lines).
+FILE_FLAGS = {"k_persist.cu": ["-Xptxas", "-dlcm=cg"]}
+
+
 def _compile(src, extra):
+    extra = list(extra) + FILE_FLAGS.get(src, [])
     obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
     deps = [os.path.join(CSRC, src)] + [os.path.join(CSRC, h) for h in HEADERS] + \
         [os.path.join(ROOT, "include", "ucc.h")]

@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(kThreads) k_tape_reinsert(Table t, Tape tape, 
     const unsigned int born = rec.born;
     Lookup r = find1(t, key, 0u);
     if (r.state == ALIVE) {
-      raise_error(t.cnt, ERR_CONSISTENCY);
+      raise_consistency(t.cnt, SITE_TAPE_ALIVE);
     } else if (r.state == DEAD_OLD || r.state == DEAD_NOW) {
       t.amps[r.idx] = val;
       t.lam[r.idx] = 0.0;
@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(kThreads) k_tape_append(Table t, Tape tape, in
       if (!maybe[j]) continue;
       const Lookup r = find1(t, rec[j].key, 0u);
       if (r.state == ALIVE) {
-        raise_error(t.cnt, ERR_CONSISTENCY);
+        raise_consistency(t.cnt, SITE_BULK_ALIVE);
         add[j] = false;
       } else if (r.state == DEAD_OLD || r.state == DEAD_NOW) {
         t.amps[r.idx] = rec[j].val;
@@ -139,17 +139,19 @@ __global__ void __launch_bounds__(kThreads) k_link_tail(Table t) {
 template <int G>
 __global__ void __launch_bounds__(kStepThreads, 8) k_reverse(Table t, const Factor* __restrict__ factors, int k,
                                                              unsigned int stamp, double* grad) {
+  // The adjoint of a linked entry is loaded with its partner's filter word
+  // (staging it with every scanned entry costs more than it saves).
   __shared__ LinkScratch s_w[kStepThreads / 32];
   const Factor f = factors[k];
   const unsigned long long n = min(*((volatile unsigned long long*)&t.cnt->n_tail), t.cap_n);
   double acc = 0.0;
   unsigned int pairs = 0, kills = 0;
-  for_each_linked(
-      t, f, n, s_w[threadIdx.x >> 5], [&](unsigned long long i, bool act) { return act ? t.lam[i] : 0.0; },
+  for_each_linked<false>(
+      t, f, n, s_w[threadIdx.x >> 5], nullptr, [&](unsigned long long i, bool act) { return act ? t.lam[i] : 0.0; },
       [&](unsigned long long i, unsigned long long X, double cX, bool ex, double mu, bool act) {
         if (act) reverse_resolve(t, f, k, stamp, i, X, cX, mu, ex, absent_lookup(), acc, pairs, kills);
       },
-      [&](unsigned long long i, unsigned long long X, double cX, bool ex, bool act) {
+      [&](unsigned long long i, unsigned long long X, double cX, bool ex, double, bool act) {
         const double mu = act ? t.lam[i] : 0.0;
         Lookup r = findG<G>(t, X ^ (f.occ | f.vir), act, stamp);
         if (act) reverse_resolve(t, f, k, stamp, i, X, cX, mu, ex, r, acc, pairs, kills);

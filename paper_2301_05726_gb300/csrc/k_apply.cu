@@ -57,12 +57,12 @@ __global__ void __launch_bounds__(kStepThreads, 8) k_forward(Table t, const Fact
   if (!skip) {
     const Factor f = factors[k];
     const unsigned long long n = min(*((volatile unsigned long long*)&t.cnt->n_scan), t.cap_n);
-    for_each_linked(
-        t, f, n, s_w[threadIdx.x >> 5], [](unsigned long long, bool) { return 0.0; },
+    for_each_linked<false>(
+        t, f, n, s_w[threadIdx.x >> 5], nullptr, [](unsigned long long, bool) { return 0.0; },
         [&](unsigned long long i, unsigned long long X, double cX, bool ex, double, bool act) {
           if (act) forward_resolve<RECORD, true>(t, f, k, eps, stamp, tape, i, X, cX, ex, absent_lookup(), sc);
         },
-        [&](unsigned long long i, unsigned long long X, double cX, bool ex, bool act) {
+        [&](unsigned long long i, unsigned long long X, double cX, bool ex, double, bool act) {
           Lookup r = findG<G>(t, X ^ (f.occ | f.vir), act, stamp);
           if (act) forward_resolve<RECORD, true>(t, f, k, eps, stamp, tape, i, X, cX, ex, r, sc);
         });
@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(kThreads) k_rehash(Table t) {
       if (prev[u] == 0ull) {
         filter_add(t, key[u]);
       } else {
-        if (prev[u] == key[u]) raise_error(t.cnt, ERR_CONSISTENCY);
+        if (prev[u] == key[u]) raise_consistency(t.cnt, SITE_REHASH_DUP);
         s = claim_slot(t, key[u], h[u] + 1);
       }
       if (s != ~0ull) t.slots[s].idx = i;
@@ -376,10 +376,10 @@ __global__ void __launch_bounds__(kStepThreads) k_probe_bench(Table t, Factor f,
   const unsigned long long n = min(*((volatile unsigned long long*)&t.cnt->n_tail), t.cap_n);
   const unsigned long long m = f.occ | f.vir;
   unsigned long long acc = 0;
-  for_each_linked(
-      t, f, n, s_w[threadIdx.x >> 5], [](unsigned long long, bool) { return 0.0; },
+  for_each_linked<false>(
+      t, f, n, s_w[threadIdx.x >> 5], nullptr, [](unsigned long long, bool) { return 0.0; },
       [&](unsigned long long, unsigned long long, double, bool, double, bool) {},
-      [&](unsigned long long, unsigned long long X, double, bool, bool act) {
+      [&](unsigned long long, unsigned long long X, double, bool, double, bool act) {
         Lookup r = findG<G>(t, X ^ m, act, 0u);
         if (act) acc += r.idx + (unsigned long long)r.state;
       });

@@ -1,5 +1,6 @@
-// Batched (many-job) kernels: one launch advances every job of a batch by one
-// factor (forward or reverse), or evaluates every job's energy.
+// Batched (many-job) kernels of the energy: one launch evaluates every job's
+// sigma and energy sums, one initialises every job's adjoint.  (The factor
+// steps of a batch run in the persistent kernels of k_persist.cu.)
 //
 // Index space of a step: the jobs' stored entries laid end to end, each job's
 // range padded to a multiple of 32 so that a warp never straddles two jobs.
@@ -39,122 +40,23 @@ __device__ __forceinline__ void load_bases(const JobState* js, int n_jobs, const
   __syncthreads();
 }
 
-// Sizes of this step's job ranges.  mode 0: forward (n_scan of jobs still
-// applying factors, padded), 1: energy (n_tail of every job, unpadded, one warp
-// per entry), 2: reverse (n_tail of jobs still undoing factors, padded), 3: the
-// tape records of each job's current reverse factor (unpadded).
-__device__ void layout(const JobView* jobs, JobState* js, int n_jobs, BatchHeader* bh, int mode) {
+// Every job's stored entries laid end to end (unpadded: the energy kernel
+// takes one warp per entry), by one thread.
+__device__ void layout(const JobView* jobs, JobState* js, int n_jobs, BatchHeader* bh) {
   if (threadIdx.x != 0) return;
   unsigned long long total = 0;
   for (int j = 0; j < n_jobs; ++j) {
     const JobView& jv = jobs[j];
-    const Counters* c = jv.t.cnt;
-    unsigned long long n = 0, w = 0;
-    const int k = js[j].k;
-    if (mode == 0) {
-      if (k < jv.K && js[j].stop < 0) n = min(*((volatile const unsigned long long*)&c->n_scan), jv.t.cap_n);
-      w = (n + 31ull) & ~31ull;
-    } else if (mode == 1) {
-      n = min(*((volatile const unsigned long long*)&c->n_tail), jv.t.cap_n);
-      w = n;
-    } else if (mode == 2) {
-      if (k >= 0) n = min(*((volatile const unsigned long long*)&c->n_tail), jv.t.cap_n);
-      w = (n + 31ull) & ~31ull;
-    } else {
-      if (k >= 0) {
-        const unsigned long long hi = min(jv.tape.off[k + 1], jv.tape.cap);
-        const unsigned long long lo = min(jv.tape.off[k], hi);
-        n = hi - lo;
-      }
-      w = n;
-    }
+    const unsigned long long n = min(*((volatile const unsigned long long*)&jv.t.cnt->n_tail), jv.t.cap_n);
     js[j].base = total;
     js[j].n = n;
-    total += w;
+    total += n;
   }
   bh->total = total;
 }
 
-__global__ void k_batch_layout(const JobView* jobs, JobState* js, int n_jobs, BatchHeader* bh, int mode) {
-  layout(jobs, js, n_jobs, bh, mode);
-}
-
-__device__ __forceinline__ void flush_counts(Counters* c, StepCounts& sc) {
-  const unsigned int lane = threadIdx.x & 31u;
-  unsigned long long v[4] = {sc.rot, sc.cre, sc.dnew, sc.dold};
-  long long dd = sc.dead_delta;
-  for (int o = 16; o > 0; o >>= 1) {
-    for (int x = 0; x < 4; ++x) v[x] += __shfl_xor_sync(0xFFFFFFFFu, v[x], o);
-    dd += __shfl_xor_sync(0xFFFFFFFFu, dd, o);
-  }
-  if (lane == 0) {
-    if (v[0]) atomicAdd(&c->rotations, v[0]);
-    if (v[1]) atomicAdd(&c->created, v[1]);
-    if (v[2]) atomicAdd(&c->dropped_new, v[2]);
-    if (v[3]) atomicAdd(&c->dropped_old, v[3]);
-    if (dd) atomicAdd(&c->n_dead, (unsigned long long)dd);
-  }
-  sc = StepCounts();
-}
-
-template <bool RECORD>
-__global__ void __launch_bounds__(kThreads) k_forward_batch(const JobView* jobs, JobState* js, int n_jobs,
-                                                             BatchHeader* bh) {
-  __shared__ unsigned long long s_base[kMaxBatchJobs + 1];
-  load_bases(js, n_jobs, bh, s_base);
-  const unsigned long long total = s_base[n_jobs];
-  const unsigned int lane = threadIdx.x & 31u;
-  const unsigned long long warp = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const unsigned long long nwarps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
-  StepCounts sc;
-  int cur = -1;
-  for (unsigned long long g = warp * 32ull; g < total; g += nwarps * 32ull) {
-    const int j = job_of(s_base, n_jobs, g);  // warp-uniform
-    if (j != cur) {
-      if (cur >= 0) flush_counts(jobs[cur].t.cnt, sc);
-      cur = j;
-    }
-    const JobView& jv = jobs[j];
-    const int k = js[j].k;
-    const Factor f = jv.factors[k];
-    const unsigned long long i = g - s_base[j] + lane;
-    forward_entry<1, RECORD>(jv.t, f, k, jv.eps, (unsigned int)(k + 1), jv.tape, i, i < js[j].n, sc);
-  }
-  if (cur >= 0) flush_counts(jobs[cur].t.cnt, sc);
-  // Last block: each job's end-of-factor bookkeeping, then the next layout.
-  __shared__ bool last;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    last = atomicAdd(&bh->done, 1u) == gridDim.x - 1;
-  }
-  __syncthreads();
-  if (!last) return;
-  __threadfence();
-  for (int j = threadIdx.x; j < n_jobs; j += blockDim.x) {
-    if (js[j].n == 0) continue;  // not stepped this launch
-    const JobView& jv = jobs[j];
-    Counters* c = jv.t.cnt;
-    const int k = js[j].k;
-    const unsigned long long nt = ld_cg(&c->n_tail);
-    c->scanned += ld_cg(&c->n_scan);
-    c->n_scan = nt;
-    unsigned long long tn = 0;
-    if (RECORD) {
-      tn = ld_cg(&c->tape_n);
-      jv.tape.off[k + 1] = tn;
-    }
-    const unsigned long long slots = jv.t.slot_mask + 1ull;
-    const bool room = 2ull * nt <= jv.t.cap_n && 8ull * nt <= 3ull * slots && (!RECORD || tn + nt <= jv.tape.cap);
-    js[j].k = k + 1;
-    if (!room && k + 1 < jv.K) js[j].stop = k + 1;
-    js[j].n_tail = nt;
-    js[j].n_dead = ld_cg(&c->n_dead);
-    js[j].tape_n = tn;
-  }
-  __syncthreads();
-  layout(jobs, js, n_jobs, bh, 0);
-  if (threadIdx.x == 0) bh->done = 0u;
+__global__ void k_batch_layout(const JobView* jobs, JobState* js, int n_jobs, BatchHeader* bh) {
+  layout(jobs, js, n_jobs, bh);
 }
 
 // sigma[0, n) = 0 in every job before the lower-triangle pass.
@@ -240,101 +142,10 @@ __global__ void __launch_bounds__(kThreads) k_lambda_init_batch(const JobView* j
   }
 }
 
-// Tape re-insertion of every job's current reverse factor (layout mode 3).
-__global__ void __launch_bounds__(kThreads) k_tape_reinsert_batch(const JobView* jobs, JobState* js, int n_jobs,
-                                                                   BatchHeader* bh) {
-  __shared__ unsigned long long s_base[kMaxBatchJobs + 1];
-  load_bases(js, n_jobs, bh, s_base);
-  const unsigned long long total = s_base[n_jobs];
-  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-  for (unsigned long long g = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += stride) {
-    const int j = job_of(s_base, n_jobs, g);
-    const JobView& jv = jobs[j];
-    const int k = js[j].k;
-    const unsigned long long x = min(jv.tape.off[k], jv.tape.cap) + (g - s_base[j]);
-    const TapeRec rec = tape_at(jv.tape, x);
-    const unsigned long long key = rec.key;
-    Lookup r = find1(jv.t, key, 0u);
-    if (r.state == ALIVE) {
-      raise_error(jv.t.cnt, ERR_CONSISTENCY);
-    } else if (r.state == DEAD_OLD || r.state == DEAD_NOW) {
-      jv.t.amps[r.idx] = rec.val;
-      jv.t.lam[r.idx] = 0.0;
-      jv.t.born[r.idx] = rec.born;
-    } else {
-      insert_new(jv.t, key, rec.val, rec.born, r.slot, true, true);
-    }
-  }
-}
-
-__global__ void __launch_bounds__(kThreads) k_reverse_batch(const JobView* jobs, JobState* js, int n_jobs,
-                                                             BatchHeader* bh) {
-  __shared__ unsigned long long s_base[kMaxBatchJobs + 1];
-  load_bases(js, n_jobs, bh, s_base);
-  const unsigned long long total = s_base[n_jobs];
-  const unsigned int lane = threadIdx.x & 31u;
-  const unsigned long long warp = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const unsigned long long nwarps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
-  int cur = -1;
-  double acc = 0.0;
-  unsigned int pairs = 0, kills = 0;  // kills: not used by the batched sweep
-  auto flush = [&](int j) {
-    const double a = warp_sum(acc);
-    const unsigned long long p = warp_sum_u64(pairs);
-    if (lane == 0) {
-      if (a != 0.0) atomicAdd(&js[j].gacc, a);
-      if (p) atomicAdd(&jobs[j].t.cnt->rev_pairs, p);
-    }
-    acc = 0.0;
-    pairs = 0;
-  };
-  for (unsigned long long g = warp * 32ull; g < total; g += nwarps * 32ull) {
-    const int j = job_of(s_base, n_jobs, g);
-    if (j != cur) {
-      if (cur >= 0) flush(cur);
-      cur = j;
-    }
-    const JobView& jv = jobs[j];
-    const int k = js[j].k;
-    const Factor f = jv.factors[k];
-    const unsigned long long i = g - s_base[j] + lane;
-    reverse_entry<1>(jv.t, f, k, 0x80000000u | (unsigned int)k, i, i < js[j].n, acc, pairs, kills);
-  }
-  if (cur >= 0) flush(cur);
-  __shared__ bool last;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    last = atomicAdd(&bh->done, 1u) == gridDim.x - 1;
-  }
-  __syncthreads();
-  if (!last) return;
-  __threadfence();
-  for (int j = threadIdx.x; j < n_jobs; j += blockDim.x) {
-    const int k = js[j].k;
-    if (k < 0) continue;
-    jobs[j].grad[k] = 2.0 * ld_cg(&js[j].gacc);
-    js[j].gacc = 0.0;
-    js[j].k = k - 1;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) bh->done = 0u;
-}
-
 }  // namespace
 
-cudaError_t launch_batch_layout(const JobView* jobs, JobState* js, int n_jobs, BatchHeader* bh, int mode,
-                                cudaStream_t st) {
-  k_batch_layout<<<1, 32, 0, st>>>(jobs, js, n_jobs, bh, mode);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_forward_batch(const JobView* jobs, JobState* js, int n_jobs, BatchHeader* bh, int record,
-                                 int grid, cudaStream_t st) {
-  if (record)
-    k_forward_batch<true><<<grid, kThreads, 0, st>>>(jobs, js, n_jobs, bh);
-  else
-    k_forward_batch<false><<<grid, kThreads, 0, st>>>(jobs, js, n_jobs, bh);
+cudaError_t launch_batch_layout(const JobView* jobs, JobState* js, int n_jobs, BatchHeader* bh, cudaStream_t st) {
+  k_batch_layout<<<1, 32, 0, st>>>(jobs, js, n_jobs, bh);
   return cudaGetLastError();
 }
 
@@ -348,15 +159,6 @@ cudaError_t launch_sigma_batch(const JobView* jobs, JobState* js, int n_jobs, Ba
 cudaError_t launch_lambda_init_batch(const JobView* jobs, JobState* js, int n_jobs, BatchHeader* bh, int grid,
                                      cudaStream_t st) {
   k_lambda_init_batch<<<grid, kThreads, 0, st>>>(jobs, js, n_jobs, bh);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_reverse_batch(const JobView* jobs, JobState* js, int n_jobs, BatchHeader* bh, int grid,
-                                 cudaStream_t st) {
-  k_batch_layout<<<1, 32, 0, st>>>(jobs, js, n_jobs, bh, 3);
-  k_tape_reinsert_batch<<<grid, kThreads, 0, st>>>(jobs, js, n_jobs, bh);
-  k_batch_layout<<<1, 32, 0, st>>>(jobs, js, n_jobs, bh, 2);
-  k_reverse_batch<<<grid, kThreads, 0, st>>>(jobs, js, n_jobs, bh);
   return cudaGetLastError();
 }
 

@@ -5,9 +5,18 @@
 // Exact selection by radix passes over 11-bit digits, most significant first:
 // |c| as its IEEE-754 bit pattern (monotone in |c| for non-negative values)
 // from the top bin down, then, only if several entries share the threshold
-// value, the determinant key from the bottom bin up.  Each pass is one kernel:
-// every block histograms its share of the live entries in shared memory, and
-// the last block to finish picks the bin that holds the target rank.
+// value, the determinant key from the bottom bin up.  The first two digits of
+// |c| are histogrammed over the whole table (one kernel each: every block
+// histograms its share in shared memory, the last block to finish picks the
+// bin that holds the target rank); the entries left in the picked bin (a
+// relative window of about 2^-10 in |c|) are gathered into a small candidate
+// buffer, and one block resolves the remaining digits of |c| and, for ties,
+// of the key on that buffer.  When the bin holds more entries than the buffer
+// (many exactly equal amplitudes), that block reads the table instead.
+//
+// The cut itself is fused with the compaction that follows it: one pass
+// copies the kept entries into the spare arrays and records the dropped ones
+// on the kill tape, so dropped entries are neither tagged nor scanned again.
 
 #include "ucc_steps.cuh"
 
@@ -38,23 +47,24 @@ __device__ __forceinline__ unsigned long long high_mask(int pass) {
   return top >= 64 ? 0ull : (~0ull << top);
 }
 
-// The last block turns the global histogram into the next digit of the
-// threshold: phase 0 walks bins from the top (largest |c| first), phase 1 from
-// the bottom (smallest key first).
-__device__ void pick_bin(SelectState* sel, int phase, int pass, int nbins) {
-  __shared__ unsigned long long s_scan[kThreads];
-  const int per = (nbins + kThreads - 1) / kThreads;
+// Turn a histogram of nbins bins (hist_at(b)) into the next digit of the
+// threshold, NT threads of one block: phase 0 walks bins from the top (largest
+// |c| first), phase 1 from the bottom (smallest key first).
+template <int NT, class H>
+__device__ void pick_bin(SelectState* sel, int phase, int pass, int nbins, H hist_at) {
+  __shared__ unsigned long long s_scan[NT];
+  const int per = (nbins + NT - 1) / NT;
   unsigned long long local = 0;
   for (int j = 0; j < per; ++j) {
     const int o = threadIdx.x * per + j;  // visiting order
     if (o >= nbins) break;
     const int b = phase == 0 ? nbins - 1 - o : o;
-    local += ld_cg(&sel->hist[b]);
+    local += hist_at(b);
   }
   s_scan[threadIdx.x] = local;
   __syncthreads();
-  // inclusive scan (Hillis-Steele) over the 256 partial sums
-  for (int off = 1; off < kThreads; off <<= 1) {
+  // inclusive scan (Hillis-Steele) over the NT partial sums
+  for (int off = 1; off < NT; off <<= 1) {
     unsigned long long v = threadIdx.x >= off ? s_scan[threadIdx.x - off] : 0ull;
     __syncthreads();
     s_scan[threadIdx.x] += v;
@@ -69,7 +79,7 @@ __device__ void pick_bin(SelectState* sel, int phase, int pass, int nbins) {
       const int o = threadIdx.x * per + j;
       if (o >= nbins) break;
       const int b = phase == 0 ? nbins - 1 - o : o;
-      const unsigned long long cnt = ld_cg(&sel->hist[b]);
+      const unsigned long long cnt = hist_at(b);
       if (cum + cnt >= target) {
         const unsigned long long rest = target - cum;
         const int shift = digit_shift(pass);
@@ -91,18 +101,13 @@ __device__ void pick_bin(SelectState* sel, int phase, int pass, int nbins) {
     }
   }
   __syncthreads();
-  for (int b = threadIdx.x; b < nbins; b += blockDim.x) sel->hist[b] = 0;
 }
 
-// One radix pass: histogram of the pass's digit of |c| (phase 0) or of the
-// key among |c| == threshold entries (phase 1), restricted to entries whose
-// already-fixed digits match, then the pick in the last block.
-__global__ void __launch_bounds__(kThreads) k_select_pass(Table t, SelectState* sel, int phase, int pass) {
+// One of the two full-table radix passes over |c| (pass 0: bits 63..53, pass
+// 1: bits 52..42), restricted to live entries whose fixed digits match, then
+// the pick in the last block.
+__global__ void __launch_bounds__(kThreads) k_select_pass(Table t, SelectState* sel, int pass) {
   __shared__ unsigned int h[kBins];
-  __shared__ int s_skip;
-  if (threadIdx.x == 0) s_skip = (phase == 1 && !*((volatile int*)&sel->need_keys)) ? 1 : 0;
-  __syncthreads();
-  if (s_skip) return;  // uniform over the grid: no tie to break
   const int top = 64 - kDigit * pass;
   const int nbins = 1 << (top - digit_shift(pass));
   for (int b = threadIdx.x; b < nbins; b += blockDim.x) h[b] = 0;
@@ -110,90 +115,219 @@ __global__ void __launch_bounds__(kThreads) k_select_pass(Table t, SelectState* 
   const unsigned long long n = min(*((volatile unsigned long long*)&t.cnt->n_tail), t.cap_n);
   const unsigned long long hm = high_mask(pass);
   const unsigned long long T = sel->prefix;
-  const unsigned long long kp = sel->key_prefix;
   const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
   for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     const double a = t.amps[i];
     if (is_dead(a)) continue;
     const unsigned long long u = mag_bits(a);
-    if (phase == 0) {
-      if ((u & hm) != (T & hm)) continue;
-      atomicAdd(&h[digit_of(u, pass)], 1u);
-    } else {
-      if (u != T) continue;
-      const unsigned long long key = t.keys[i];
-      if ((key & hm) != (kp & hm)) continue;
-      atomicAdd(&h[digit_of(key, pass)], 1u);
-    }
+    if ((u & hm) != (T & hm)) continue;
+    atomicAdd(&h[digit_of(u, pass)], 1u);
   }
   __syncthreads();
   for (int b = threadIdx.x; b < nbins; b += blockDim.x)
     if (h[b]) atomicAdd(&sel->hist[b], (unsigned long long)h[b]);
   if (last_block_arrive(t.cnt)) {
-    pick_bin(sel, phase, pass, nbins);
+    pick_bin<kThreads>(sel, 0, pass, nbins, [&](int b) { return ld_cg(&sel->hist[b]); });
+    for (int b = threadIdx.x; b < nbins; b += blockDim.x) sel->hist[b] = 0;
     if (threadIdx.x == 0) t.cnt->done = 0u;
   }
 }
 
-// Drop every live entry outside the kept set; record drops on the tape.
-template <bool RECORD>
-__global__ void __launch_bounds__(kThreads) k_select_mark(Table t, SelectState* sel, unsigned int stamp, Tape tape,
-                                                          int k) {
+// The live entries whose top 22 bits of |c| equal the threshold's so far.
+__global__ void __launch_bounds__(kThreads) k_select_gather(Table t, SelectState* sel, SelectCand* cand) {
   const unsigned long long n = min(*((volatile unsigned long long*)&t.cnt->n_tail), t.cap_n);
-  const unsigned long long T = sel->prefix;
-  const bool keys = sel->need_keys != 0;
-  const unsigned long long Kt = sel->key_prefix;
+  const unsigned long long hm = high_mask(2);
+  const unsigned long long T = sel->prefix & hm;
   const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-  unsigned long long dropped = 0;
-  double dS = 0.0;
   for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     const double a = t.amps[i];
     if (is_dead(a)) continue;
     const unsigned long long u = mag_bits(a);
-    bool keep = u > T;
-    if (u == T) keep = !keys || t.keys[i] <= Kt;
-    if (keep) continue;
-    if (t.entropy) dS -= entropy_term(a);
-    if (RECORD) {
-      const unsigned long long ti = aggregated_add(&t.cnt->tape_n);
-      if (ti < tape.cap) {
-        TapeRec& rec = tape_at(tape, ti);
-        rec.key = t.keys[i];
-        rec.val = a;
-        rec.born = t.born[i];
+    if ((u & hm) != T) continue;
+    const unsigned long long j = aggregated_add(&sel->n_cand);
+    if (j < kSelectCandCap) {
+      cand[j].mag = u;
+      cand[j].key = t.keys[i];
+    }
+  }
+}
+
+constexpr int kFinishThreads = 1024;
+
+// The remaining digits of |c| (passes 2..5) and, when several entries share
+// the threshold value, of the key (passes 0..5), by one block over the
+// candidate buffer (or over the table when the buffer overflowed).
+__global__ void __launch_bounds__(kFinishThreads) k_select_finish(Table t, SelectState* sel,
+                                                                  const SelectCand* cand) {
+  __shared__ unsigned int h[kBins];
+  const unsigned long long nc = sel->n_cand;
+  const bool from_cand = nc <= kSelectCandCap;
+  const unsigned long long n = from_cand ? nc : min(*((volatile unsigned long long*)&t.cnt->n_tail), t.cap_n);
+  // entry x as (|c| bits, key), or false for a dropped table entry
+  auto entry = [&](unsigned long long x, unsigned long long& u, unsigned long long& key) {
+    if (from_cand) {
+      u = cand[x].mag;
+      key = cand[x].key;
+      return true;
+    }
+    const double a = t.amps[x];
+    if (is_dead(a)) return false;
+    u = mag_bits(a);
+    key = t.keys[x];
+    return true;
+  };
+  for (int phase = 0; phase < 2; ++phase) {
+    for (int pass = phase == 0 ? 2 : 0; pass < kPasses; ++pass) {
+      if (phase == 1 && !sel->need_keys) return;  // block-uniform
+      const int top = 64 - kDigit * pass;
+      const int nbins = 1 << (top - digit_shift(pass));
+      for (int b = threadIdx.x; b < nbins; b += blockDim.x) h[b] = 0;
+      __syncthreads();
+      const unsigned long long hm = high_mask(pass);
+      const unsigned long long T = sel->prefix, kp = sel->key_prefix;
+      for (unsigned long long x = threadIdx.x; x < n; x += blockDim.x) {
+        unsigned long long u, key;
+        if (!entry(x, u, key)) continue;
+        if (phase == 0) {
+          if ((u & hm) == (T & hm)) atomicAdd(&h[digit_of(u, pass)], 1u);
+        } else if (u == T && (key & hm) == (kp & hm)) {
+          atomicAdd(&h[digit_of(key, pass)], 1u);
+        }
+      }
+      __syncthreads();
+      pick_bin<kFinishThreads>(sel, phase, pass, nbins, [&](int b) { return (unsigned long long)h[b]; });
+    }
+  }
+}
+
+// Exclusive prefix over the block of two per-thread counts (each < 2^16),
+// packed as a + (b << 16), with one atomicAdd per count on the global
+// counters ca and cb: returns this thread's first position for each.
+__device__ __forceinline__ void block_reserve2(unsigned int a, unsigned int b, unsigned long long* ca,
+                                               unsigned long long* cb, unsigned long long& pa,
+                                               unsigned long long& pb) {
+  __shared__ unsigned int s_w[kThreads / 32];
+  __shared__ unsigned long long s_base[2];
+  const unsigned int lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
+  const unsigned int v = a | (b << 16);
+  unsigned int incl = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned int y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+    if ((int)lane >= o) incl += y;
+  }
+  if (lane == 31) s_w[w] = incl;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned int run = 0;
+    for (int x = 0; x < kThreads / 32; ++x) {
+      const unsigned int t = s_w[x];
+      s_w[x] = run;
+      run += t;
+    }
+    s_base[0] = (run & 0xFFFFu) ? atomicAdd(ca, (unsigned long long)(run & 0xFFFFu)) : 0ull;
+    s_base[1] = (run >> 16) ? atomicAdd(cb, (unsigned long long)(run >> 16)) : 0ull;
+  }
+  __syncthreads();
+  const unsigned int excl = s_w[w] + incl - v;
+  pa = s_base[0] + (excl & 0xFFFFu);
+  pb = s_base[1] + (excl >> 16);
+  __syncthreads();  // s_w and s_base are reused by the next call
+}
+
+// The cut fused with the compaction that follows it.  Each block takes tiles
+// of 4 x kThreads entries; a live entry above the threshold (|c| > T, or
+// |c| == T and key <= key threshold when ties are broken) goes to the spare
+// arrays, any other live entry is dropped: recorded on the tape with its value
+// and birth factor (RECORD), its Eq. 6 term subtracted (entropy runs).
+template <bool RECORD>
+__global__ void __launch_bounds__(kThreads) k_cut_compact(Table from, Table to, const SelectState* sel, Tape tape,
+                                                          int k) {
+  const unsigned long long n = min(*((volatile unsigned long long*)&from.cnt->n_tail), from.cap_n);
+  const unsigned long long T = sel->prefix;
+  const bool keys = sel->need_keys != 0;
+  const unsigned long long Kt = sel->key_prefix;
+  constexpr int kPer = 4;
+  const unsigned long long tile = (unsigned long long)kPer * kThreads;
+  unsigned long long dropped = 0;
+  double dS = 0.0;
+  for (unsigned long long base = (unsigned long long)blockIdx.x * tile; base < n;
+       base += (unsigned long long)gridDim.x * tile) {  // block-uniform
+    double a[kPer];
+    unsigned long long key[kPer];
+    int state[kPer];  // 0 none, 1 keep, 2 drop
+    unsigned int nk = 0, nd = 0;
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+      const unsigned long long i = base + (unsigned long long)u * kThreads + threadIdx.x;
+      a[u] = i < n ? from.amps[i] : dead_value(0u);
+    }
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+      state[u] = 0;
+      if (is_dead(a[u])) continue;
+      const unsigned long long i = base + (unsigned long long)u * kThreads + threadIdx.x;
+      key[u] = from.keys[i];
+      const unsigned long long m = mag_bits(a[u]);
+      const bool keep = m > T || (m == T && (!keys || key[u] <= Kt));
+      state[u] = keep ? 1 : 2;
+      nk += keep;
+      nd += !keep;
+    }
+    unsigned long long pk, pd;
+    block_reserve2(nk, RECORD ? nd : 0u, &from.cnt->new_n, &from.cnt->tape_n, pk, pd);
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+      if (state[u] == 0) continue;
+      const unsigned long long i = base + (unsigned long long)u * kThreads + threadIdx.x;
+      if (state[u] == 1) {
+        if (pk < to.cap_n) {
+          to.keys[pk] = key[u];
+          to.amps[pk] = a[u];
+          if (to.born) to.born[pk] = from.born[i];
+        } else {
+          raise_error(from.cnt, ERR_CAPACITY);
+        }
+        ++pk;
       } else {
-        raise_error(t.cnt, ERR_TAPE_FULL);
+        ++dropped;
+        if (from.entropy) dS -= entropy_term(a[u]);
+        if (RECORD) {
+          if (pd < tape.cap) {
+            TapeRec& rec = tape_at(tape, pd);
+            rec.key = key[u];
+            rec.val = a[u];
+            rec.born = from.born[i];
+          } else {
+            raise_error(from.cnt, ERR_TAPE_FULL);
+          }
+          ++pd;
+        }
       }
     }
-    t.amps[i] = dead_value(stamp);
-    ++dropped;
   }
   __shared__ unsigned long long s_d;
   if (threadIdx.x == 0) s_d = 0;
   __syncthreads();
   if (dropped) atomicAdd(&s_d, dropped);
-  __syncthreads();
-  if (threadIdx.x == 0 && s_d) {
-    atomicAdd(&t.cnt->n_dead, s_d);
-    atomicAdd(&sel->cut_total, s_d);
-  }
-  if (t.entropy) {
+  if (from.entropy) {
     const double b = block_sum(dS);
-    if (threadIdx.x == 0) t.partials[blockIdx.x] = b;
+    if (threadIdx.x == 0) from.partials[blockIdx.x] = b;
   }
-  const bool last = last_block_arrive(t.cnt);
-  if (last && t.entropy) {
+  __syncthreads();
+  if (threadIdx.x == 0 && s_d) atomicAdd(&const_cast<SelectState*>(sel)->cut_total, s_d);
+  const bool last = last_block_arrive(from.cnt);
+  if (last && from.entropy) {
     double s = 0.0;
-    for (unsigned int x = threadIdx.x; x < gridDim.x; x += blockDim.x) s += ld_cg(&t.partials[x]);
+    for (unsigned int x = threadIdx.x; x < gridDim.x; x += blockDim.x) s += ld_cg(&from.partials[x]);
     s = block_sum(s);
     if (threadIdx.x == 0) {
-      t.cnt->entropy += s;
-      t.entropy[k] = t.cnt->entropy;
+      from.cnt->entropy += s;
+      from.entropy[k] = from.cnt->entropy;
     }
   }
   if (last && threadIdx.x == 0) {
-    t.cnt->done = 0u;
-    if (RECORD) tape.off[k + 1] = ld_cg(&t.cnt->tape_n);
+    from.cnt->done = 0u;
+    if (RECORD) tape.off[k + 1] = ld_cg(&from.cnt->tape_n);
   }
 }
 
@@ -205,26 +339,30 @@ __global__ void k_select_init(SelectState* sel, unsigned long long n_cut) {
     sel->key_target = 0;
     sel->need_keys = 0;
     sel->count_eq = 0;
+    sel->n_cand = 0;
   }
   for (int b = threadIdx.x; b < kBins; b += blockDim.x) sel->hist[b] = 0;
 }
 
 }  // namespace
 
-cudaError_t launch_select_cut(const Table& t, SelectState* sel, unsigned long long n_cut, unsigned int stamp,
-                              int record, const Tape& tape, int k, int grid, cudaStream_t st, long long* launches) {
+cudaError_t launch_select_threshold(const Table& t, SelectState* sel, SelectCand* cand, unsigned long long n_cut,
+                                    int grid, cudaStream_t st, long long* launches) {
   k_select_init<<<1, kThreads, 0, st>>>(sel, n_cut);
-  *launches += 1;
-  for (int phase = 0; phase < 2; ++phase)
-    for (int pass = 0; pass < kPasses; ++pass) {
-      k_select_pass<<<grid, kThreads, 0, st>>>(t, sel, phase, pass);
-      *launches += 1;
-    }
+  k_select_pass<<<grid, kThreads, 0, st>>>(t, sel, 0);
+  k_select_pass<<<grid, kThreads, 0, st>>>(t, sel, 1);
+  k_select_gather<<<grid, kThreads, 0, st>>>(t, sel, cand);
+  k_select_finish<<<1, kFinishThreads, 0, st>>>(t, sel, cand);
+  *launches += 5;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cut_compact(const Table& from, const Table& to, const SelectState* sel, int record,
+                               const Tape& tape, int k, int grid, cudaStream_t st) {
   if (record)
-    k_select_mark<true><<<grid, kThreads, 0, st>>>(t, sel, stamp, tape, k);
+    k_cut_compact<true><<<grid, kThreads, 0, st>>>(from, to, sel, tape, k);
   else
-    k_select_mark<false><<<grid, kThreads, 0, st>>>(t, sel, stamp, tape, k);
-  *launches += 1;
+    k_cut_compact<false><<<grid, kThreads, 0, st>>>(from, to, sel, tape, k);
   return cudaGetLastError();
 }
 

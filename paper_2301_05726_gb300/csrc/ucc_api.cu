@@ -164,6 +164,7 @@ struct ucc_ctx {
   double* d_partials = nullptr;
   int partial_cap = 0;
   SelectState* d_sel = nullptr;
+  SelectCand* d_cand = nullptr;  // [kSelectCandCap] candidates of the cut's last selection passes
   double* d_entropy = nullptr;  // [K] Eq. 6 after each factor of the last apply
   bool entropy_on = false;
   bool have_entropy = false;
@@ -183,6 +184,7 @@ struct ucc_ctx {
   bool have_sigma = false;
   cudaEvent_t ev[6] = {};
   cudaEvent_t kev[2] = {};  // around each chunk of factor launches
+  cudaEvent_t rev_[2] = {};  // around each cut / rebuild
   ucc_stats stats{};
   int probe_width = 1;
   long long launches = 0;
@@ -249,7 +251,8 @@ ucc_status check_device_error(const Counters& h) {
   if (!err) return UCC_OK;
   std::string msg = "device error word:";
   if (err & ERR_PROBE_BOUND) msg += " probe-bound";
-  if (err & ERR_CONSISTENCY) msg += " consistency";
+  if (err & ERR_CONSISTENCY)
+    msg += " consistency (site " + std::to_string(h.err_site) + ", key " + std::to_string(h.err_key) + ")";
   if (err & ERR_TAPE_FULL) msg += " tape-full";
   if (err & ERR_CAPACITY) msg += " capacity";
   return fail((err & (ERR_CAPACITY | ERR_TAPE_FULL)) ? UCC_ECAPACITY : UCC_ECUDA, msg);
@@ -274,9 +277,12 @@ unsigned long long slots_for(unsigned long long cap_n) {
   return next_pow2(std::max<unsigned long long>(64, (cap_n * 4 + 2) / 3));
 }
 
-// Copy live entries into arrays of capacity new_cap (dropping dead entries) and
-// rebuild the hash.  Counters are updated on the device.
-ucc_status rebuild(ucc_ctx* c, TableSet& s, unsigned long long new_cap, bool with_lam = false) {
+// The spare arrays of table s, sized for new_cap entries and cleared, as the
+// target of a compaction; finish_rebuild hashes them and swaps them in.
+ucc_status prepare_spare(ucc_ctx* c, TableSet& s, unsigned long long new_cap, Table* out) {
+  if (new_cap >= kMaxEntries)
+    return fail(UCC_ECAPACITY, "the wavefunction needs more than 2^31 stored entries (" + std::to_string(new_cap) +
+                                   ")");
   unsigned long long ns = slots_for(new_cap);
   if (s.spare.cap_n != new_cap || s.spare.n_slots != ns) {
     s.spare.release();
@@ -286,8 +292,7 @@ ucc_status rebuild(ucc_ctx* c, TableSet& s, unsigned long long new_cap, bool wit
       return fail(UCC_ECAPACITY, "cannot allocate " + std::to_string(new_cap) + " entries: " + g_last_error);
     }
   }
-  Table from = c->table(s);
-  Table to = from;
+  Table to = c->table(s);
   to.keys = s.spare.keys;
   to.amps = s.spare.amps;
   to.born = s.spare.born;
@@ -302,16 +307,62 @@ ucc_status rebuild(ucc_ctx* c, TableSet& s, unsigned long long new_cap, bool wit
   CUDA_TRY(cudaMemsetAsync(&s.d_cnt->new_n, 0, sizeof(unsigned long long), c->stream));
   CUDA_TRY(cudaMemsetAsync(to.slots, 0, ns * sizeof(Slot), c->stream));
   CUDA_TRY(cudaMemsetAsync(to.filt, 0, ns / 4 * sizeof(unsigned int), c->stream));
-  int grid = c->full_grid();
-  CUDA_TRY(launch_compact(from, to, with_lam ? 2 : 1, grid, c->stream));
+  *out = to;
+  return UCC_OK;
+}
+
+// Hash the compacted spare arrays `to` and make them the current ones.
+ucc_status finish_rebuild(ucc_ctx* c, TableSet& s, const Table& to) {
+  const int grid = c->full_grid();
   CUDA_TRY(launch_rehash(to, grid, c->stream));
   CUDA_TRY(launch_finish_rebuild(to, c->stream));
-  c->launches += 3;
+  c->launches += 2;
   std::swap(s.cur, s.spare);
   // After growth the old, smaller arrays are not reused: free them now.
   if (s.spare.cap_n != s.cur.cap_n) s.spare.release();
   c->stats.rebuilds++;
   return UCC_OK;
+}
+
+// Copy live entries into arrays of capacity new_cap (dropping dead entries) and
+// rebuild the hash.  Counters are updated on the device.
+// Device time between the two events, added to *acc after the stream reaches
+// the second one.
+ucc_status add_elapsed(ucc_ctx* c, double* acc) {
+  float ms = 0.f;
+  CUDA_TRY(cudaEventSynchronize(c->rev_[1]));
+  CUDA_TRY(cudaEventElapsedTime(&ms, c->rev_[0], c->rev_[1]));
+  *acc += ms;
+  return UCC_OK;
+}
+
+ucc_status rebuild(ucc_ctx* c, TableSet& s, unsigned long long new_cap, bool with_lam = false) {
+  Table to;
+  CUDA_TRY(cudaEventRecord(c->rev_[0], c->stream));
+  UCC_TRY(prepare_spare(c, s, new_cap, &to));
+  CUDA_TRY(launch_compact(c->table(s), to, with_lam ? 2 : 1, c->full_grid(), c->stream));
+  c->launches++;
+  UCC_TRY(finish_rebuild(c, s, to));
+  CUDA_TRY(cudaEventRecord(c->rev_[1], c->stream));
+  return add_elapsed(c, &c->stats.rebuild_ms);
+}
+
+// The Methods-section cut after factor k: select the N_CUT-th entry, then one
+// pass keeps the entries above it in the spare arrays (dropping the ε-dropped
+// ones too) and records the cut ones on the tape, and the spare arrays are
+// hashed and swapped in.
+ucc_status cut_rebuild(ucc_ctx* c, TableSet& s, bool record, int k) {
+  const int grid = c->full_grid();
+  CUDA_TRY(cudaEventRecord(c->rev_[0], c->stream));
+  CUDA_TRY(launch_select_threshold(c->table(s), c->d_sel, c->d_cand, (unsigned long long)c->opt.n_cut, grid,
+                                   c->stream, &c->launches));
+  Table to;
+  UCC_TRY(prepare_spare(c, s, s.cur.cap_n, &to));
+  CUDA_TRY(launch_cut_compact(c->table(s), to, c->d_sel, record ? 1 : 0, c->tape(), k, grid, c->stream));
+  c->launches++;
+  UCC_TRY(finish_rebuild(c, s, to));
+  CUDA_TRY(cudaEventRecord(c->rev_[1], c->stream));
+  return add_elapsed(c, &c->stats.cut_ms);
 }
 
 // Grow the paged tape to hold `need` records (pages are added, never moved).
@@ -371,6 +422,7 @@ ucc_status reset_tape(ucc_ctx* c, TableSet& s, int k0) {
 // Load a snapshot into table s (its previous contents are discarded).
 ucc_status load_snapshot(ucc_ctx* c, TableSet& s, const Snapshot& snap) {
   const unsigned long long cap = std::max<unsigned long long>(4 * snap.n, 1 << 12);
+  if (cap >= kMaxEntries) return fail(UCC_ECAPACITY, "snapshot too large for one table");
   if (s.cur.cap_n < cap) UCC_TRY(s.cur.allocate(cap, slots_for(cap)));
   CUDA_TRY(cudaMemsetAsync(s.d_cnt, 0, sizeof(Counters), c->stream));
   CUDA_TRY(cudaMemsetAsync(s.cur.slots, 0, s.cur.n_slots * sizeof(Slot), c->stream));
@@ -468,7 +520,7 @@ ucc_status ensure_room(ucc_ctx* c, TableSet& s, bool record) {
   if (record) UCC_TRY(ensure_tape(c, h.tape_n + 2 * live + (1 << 12)));
   if (!room || sparse) {
     unsigned long long cap = s.cur.cap_n;
-    if (2 * live > cap || 8 * live > 3 * s.cur.n_slots) cap = std::max<unsigned long long>(4 * live, 1 << 12);
+    if (2 * live > cap || 8 * live > 3 * s.cur.n_slots) cap = std::max<unsigned long long>(5 * live / 2, 1 << 12);
     UCC_TRY(rebuild(c, s, cap));
     UCC_TRY(read_counters(c, s));
   }
@@ -518,8 +570,7 @@ ucc_status run_factors(ucc_ctx* c, TableSet& s, double eps, bool record, int k0,
       chunk = std::max(2, std::min(64, 2 * (resume - k)));
       if (h.cut_pending) {
         const unsigned long long before = h.n_tail - h.n_dead;
-        CUDA_TRY(launch_select_cut(c->table(s), c->d_sel, (unsigned long long)c->opt.n_cut, (unsigned int)resume,
-                                   record ? 1 : 0, c->tape(), resume - 1, c->full_grid(), c->stream, &c->launches));
+        UCC_TRY(cut_rebuild(c, s, record, resume - 1));
         UCC_TRY(read_counters(c, s));
         const unsigned long long after = s.h_cnt->n_tail - s.h_cnt->n_dead;
         if (after != (unsigned long long)c->opt.n_cut)
@@ -859,6 +910,7 @@ void destroy(ucc_ctx* c) {
   dfree(c->d_grad);
   dfree(c->d_partials);
   dfree(c->d_sel);
+  dfree(c->d_cand);
   release_tape(c);
   dfree(c->d_entropy);
   dfree(c->d_pages);
@@ -867,29 +919,67 @@ void destroy(ucc_ctx* c) {
     if (e) cudaEventDestroy(e);
   for (auto& e : c->kev)
     if (e) cudaEventDestroy(e);
+  for (auto& e : c->rev_)
+    if (e) cudaEventDestroy(e);
   delete c;
 }
 
-// The batched path: every job advances one factor per launch.
-ucc_status batch_on_stream(const std::vector<int>& idx, ucc_ctx* const* jobs, double eps, double* E,
-                           double* const* grads) {
+// Determinants in a job's sector (fixed alpha and beta electron counts).
+unsigned long long sector_size(const ucc_ctx* c) {
+  auto comb = [](int n, int k) {
+    unsigned long long r = 1;
+    for (int i = 1; i <= k; ++i) r = r * (unsigned long long)(n - k + i) / (unsigned long long)i;
+    return r;
+  };
+  return comb(c->n_spatial, c->n_alpha) * comb(c->n_spatial, c->n_beta);
+}
+
+// Entry capacity a job of the persistent batch is given up front: three times
+// its sector (a table holds at most the sector live plus a quarter dropped,
+// and a step may double what it holds), or four times N_MAX when its cut can
+// fire.  0 when the job cannot be sized (no cut and a sector too large).
+unsigned long long batch_capacity(const ucc_ctx* c) {
+  const unsigned long long sector = sector_size(c);
+  const unsigned long long n_max = c->opt.n_max > 0 ? (unsigned long long)c->opt.n_max : 0ull;
+  unsigned long long cap = (n_max > 0 && sector > n_max) ? 4 * n_max : 3 * sector;
+  cap = std::max<unsigned long long>(cap, 4096);
+  if (c->opt.max_entries > 0 && cap > 3ull * (unsigned long long)c->opt.max_entries) return 0;
+  if (cap > (1ull << 26)) return 0;  // larger jobs take the one-job path
+  return cap;
+}
+
+// A graph holding the one launch that `launch` enqueues on st, or nullptr when
+// the launch cannot be captured (the caller then launches it directly).
+template <class F>
+cudaGraphExec_t capture_one(cudaStream_t st, F launch) {
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ex = nullptr;
+  if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  const cudaError_t le = launch();
+  const cudaError_t ce = cudaStreamEndCapture(st, &g);
+  if (le == cudaSuccess && ce == cudaSuccess && g && cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) ex = nullptr;
+  if (g) cudaGraphDestroy(g);
+  cudaGetLastError();
+  return ex;
+}
+
+// Persistent-batch tuning: (probe width, tiles per warp visit) per batch shape,
+// chosen by timing the first steps of the forward pass with each candidate.
+std::mutex g_btune_mutex;
+std::map<std::pair<int, int>, std::pair<int, int>> g_btuned;
+
+// The batched path: one cooperative launch runs the whole forward pass of every
+// job, one launch the energy, one the whole reverse pass.
+ucc_status batch_persistent(const std::vector<int>& idx, ucc_ctx* const* jobs, double eps, double* E,
+                            double* const* grads) {
   const int n = (int)idx.size();
   ucc_ctx* c0 = jobs[idx[0]];
   cudaStream_t st = c0->stream;
   bool record = false;
   for (int x = 0; x < n; ++x) record |= grads && grads[idx[x]];
-  int maxK = 0;
-  for (int x = 0; x < n; ++x) {
-    ucc_ctx* c = jobs[idx[x]];
-    c->main = 0;
-    c->launches = 0;
-    c->stats = ucc_stats{};
-    c->cut_total = 0;
-    c->tape_budget = 0;  // batched jobs run without the cut: their tapes stay small
-    UCC_TRY(reset_table(c, c->ts[0]));
-    if (record) UCC_TRY(reset_tape(c, c->ts[0], 0));
-    maxK = std::max(maxK, c->K);
-  }
   JobView* d_jobs = nullptr;
   JobState* d_js = nullptr;
   BatchHeader* d_bh = nullptr;
@@ -898,6 +988,7 @@ ucc_status batch_on_stream(const std::vector<int>& idx, ucc_ctx* const* jobs, do
   UCC_TRY(dalloc(&d_bh, 1));
   std::vector<JobView> hv(n);
   std::vector<JobState> hs(n);
+  BatchHeader hb{};
   cudaGraphExec_t g_fwd = nullptr, g_rev = nullptr;
   auto release = [&]() {
     if (g_fwd) cudaGraphExecDestroy(g_fwd);
@@ -919,7 +1010,27 @@ ucc_status batch_on_stream(const std::vector<int>& idx, ucc_ctx* const* jobs, do
     v.grad = c->d_grad;
     v.eps = eps;
     v.K = c->K;
+    const Arrays& sp = c->ts[0].spare;
+    v.sp = SpareArrays{sp.keys, sp.amps, sp.born, sp.lam, sp.slots, sp.filt};
+    v.n_max = c->opt.n_max;
+    v.n_cut = c->opt.n_cut;
     return v;
+  };
+  // Bring each host-side table in line with the device view: the persistent
+  // kernels swap a job's two array sets.
+  auto sync_swaps = [&]() -> ucc_status {
+    std::vector<JobView> dv(n);
+    CUDA_TRY(cudaMemcpyAsync(dv.data(), d_jobs, n * sizeof(JobView), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    for (int x = 0; x < n; ++x) {
+      TableSet& ts = jobs[idx[x]]->ts[0];
+      if (dv[x].t.keys == ts.spare.keys) std::swap(ts.cur, ts.spare);
+      if (dv[x].t.keys != ts.cur.keys) return fail(UCC_ECUDA, "batched job arrays out of step");
+      // the kernels swap every array but sigma, which stays where it was
+      if (dv[x].t.sigma != ts.cur.sigma) std::swap(ts.cur.sigma, ts.spare.sigma);
+      hv[x] = dv[x];
+    }
+    return UCC_OK;
   };
   auto upload = [&]() -> ucc_status {
     for (int x = 0; x < n; ++x) hv[x] = view_of(x);
@@ -930,91 +1041,165 @@ ucc_status batch_on_stream(const std::vector<int>& idx, ucc_ctx* const* jobs, do
   };
   auto fetch = [&]() -> ucc_status {
     CUDA_TRY(cudaMemcpyAsync(hs.data(), d_js, n * sizeof(JobState), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(&hb, d_bh, sizeof(BatchHeader), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
     return UCC_OK;
   };
-  auto run = [&]() -> ucc_status {
-    const int grid = c0->full_grid();
+  // Header for a (re)launch: barrier words cleared, error cleared.
+  const unsigned long long wait_ns =
+      c0->opt.batch_wait_ms > 0 ? 1000000ull * (unsigned long long)c0->opt.batch_wait_ms : 2000000000ull;
+  auto reset_header = [&](int skip_block) -> ucc_status {
+    BatchHeader h{};
+    h.skip_block = skip_block;
+    h.wait_ns = wait_ns;
+    h.steps = hb.steps;
+    CUDA_TRY(cudaMemcpyAsync(d_bh, &h, sizeof(BatchHeader), cudaMemcpyHostToDevice, st));
+    return UCC_OK;
+  };
+  // Every job back to psi = {reference: 1.0} with its tables sized up front.
+  auto reset_all = [&]() -> ucc_status {
     for (int x = 0; x < n; ++x) {
+      ucc_ctx* c = jobs[idx[x]];
+      const unsigned long long cap = batch_capacity(c);
+      const unsigned long long ns = slots_for(cap);
+      TableSet& ts = c->ts[0];
+      if (ts.cur.cap_n != cap || ts.cur.n_slots != ns) UCC_TRY(ts.cur.allocate(cap, ns));
+      if (ts.spare.cap_n != cap || ts.spare.n_slots != ns) UCC_TRY(ts.spare.allocate(cap, ns));
+      c->main = 0;
+      UCC_TRY(reset_table(c, ts));
+      if (record) UCC_TRY(reset_tape(c, ts, 0));
       hs[x] = JobState{};
       hs[x].stop = -1;
     }
+    hb = BatchHeader{};
     UCC_TRY(upload());
-    CUDA_TRY(cudaMemsetAsync(d_bh, 0, sizeof(BatchHeader), st));
-    CUDA_TRY(launch_batch_layout(d_jobs, d_js, n, d_bh, 0, st));
-    // A chunk of steps reads all of its state from device memory, so one
-    // captured graph of it serves every chunk (forward: 32 steps; reverse:
-    // 32 steps of 4 launches; steps past a job's end are no-ops).
-    if (maxK >= 64) {
-      cudaGraph_t g = nullptr;
-      CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-      for (int s = 0; s < 32; ++s) launch_forward_batch(d_jobs, d_js, n, d_bh, record ? 1 : 0, grid, st);
-      CUDA_TRY(cudaStreamEndCapture(st, &g));
-      cudaError_t e = cudaGraphInstantiate(&g_fwd, g, 0);
-      cudaGraphDestroy(g);
-      CUDA_TRY(e);
-      if (record) {
-        CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-        for (int s = 0; s < 32; ++s) launch_reverse_batch(d_jobs, d_js, n, d_bh, grid, st);
-        CUDA_TRY(cudaStreamEndCapture(st, &g));
-        e = cudaGraphInstantiate(&g_rev, g, 0);
-        cudaGraphDestroy(g);
-        CUDA_TRY(e);
+    return reset_header(-1);
+  };
+  auto run = [&]() -> ucc_status {
+    for (int x = 0; x < n; ++x) {
+      ucc_ctx* c = jobs[idx[x]];
+      c->launches = 0;
+      c->stats = ucc_stats{};
+      c->cut_total = 0;
+      c->tape_budget = 0;
+      if (record) UCC_TRY(ensure_tape(c, 1));
+    }
+    // Probe width and tiles per warp visit: tuned once per batch shape.
+    int maxK = 0, max_so = 0;
+    for (int x = 0; x < n; ++x) {
+      maxK = std::max(maxK, jobs[idx[x]]->K);
+      max_so = std::max(max_so, jobs[idx[x]]->n_so);
+    }
+    int pw = c0->opt.probe_width > 0 ? c0->opt.probe_width : 0, tiles = c0->opt.batch_tiles;
+    if (pw == 8) pw = 4;
+    const std::pair<int, int> key((n + 15) / 16 * 16, max_so * 2 + (record ? 1 : 0));
+    if (!tiles || !pw) {
+      std::lock_guard<std::mutex> lock(g_btune_mutex);
+      auto it = g_btuned.find(key);
+      if (it != g_btuned.end()) {
+        if (!pw) pw = it->second.first;
+        if (!tiles) tiles = it->second.second;
       }
     }
-    // Forward: chunks of launches, then host action for jobs that need room.
-    CUDA_TRY(cudaEventRecord(c0->ev[0], st));
-    for (;;) {
-      if (g_fwd) {
-        CUDA_TRY(cudaGraphLaunch(g_fwd, st));
-      } else {
-        for (int s = 0; s < 32; ++s) CUDA_TRY(launch_forward_batch(d_jobs, d_js, n, d_bh, record ? 1 : 0, grid, st));
+    if (!tiles) {
+      // Coordinate search on the first 64 steps: tiles with one-lane probes,
+      // then the probe width with the best tile count.
+      auto trial = [&](int w, int tl, float* ms) -> ucc_status {
+        UCC_TRY(reset_all());
+        CUDA_TRY(cudaEventRecord(c0->kev[0], st));
+        CUDA_TRY(launch_persist_forward(d_jobs, d_js, n, d_bh, record ? 1 : 0, w, tl, 64, st));
+        CUDA_TRY(cudaEventRecord(c0->kev[1], st));
+        CUDA_TRY(cudaEventSynchronize(c0->kev[1]));
+        CUDA_TRY(cudaEventElapsedTime(ms, c0->kev[0], c0->kev[1]));
+        UCC_TRY(fetch());
+        if (hb.error) return fail(hb.error & 1 ? UCC_ETIMEOUT : UCC_ECAPACITY, "persistent batch trial failed");
+        for (int x = 0; x < n; ++x) jobs[idx[x]]->launches++;
+        return UCC_OK;
+      };
+      float best = 0.f;
+      int bw = pw ? pw : 1, bt = 1;
+      for (int tl : {1, 2, 4, 8}) {
+        float ms = 0.f;
+        UCC_TRY(trial(bw, tl, &ms));
+        if (tl == 1 || ms < best) {
+          best = ms;
+          bt = tl;
+        }
       }
-      for (int x = 0; x < n; ++x) jobs[idx[x]]->launches += 32;
+      if (!pw) {
+        for (int w : {2, 4}) {
+          float ms = 0.f;
+          UCC_TRY(trial(w, bt, &ms));
+          if (ms < best) {
+            best = ms;
+            bw = w;
+          }
+        }
+      }
+      pw = bw;
+      tiles = bt;
+      std::lock_guard<std::mutex> lock(g_btune_mutex);
+      g_btuned[key] = std::make_pair(pw, tiles);
+    }
+    if (!pw) pw = 1;
+    UCC_TRY(reset_all());
+    // The forward pass: one persistent launch (a captured graph), relaunched
+    // only when jobs wait for more tape.
+    g_fwd = capture_one(st, [&]() {
+      return launch_persist_forward(d_jobs, d_js, n, d_bh, record ? 1 : 0, pw, tiles, 1 << 30, st);
+    });
+    UCC_TRY(reset_header(c0->opt.batch_test_skip_block > 0 ? c0->opt.batch_test_skip_block - 1 : -1));
+    CUDA_TRY(cudaEventRecord(c0->ev[0], st));
+    for (int round = 0;; ++round) {
+      if (g_fwd)
+        CUDA_TRY(cudaGraphLaunch(g_fwd, st));
+      else
+        CUDA_TRY(launch_persist_forward(d_jobs, d_js, n, d_bh, record ? 1 : 0, pw, tiles, 1 << 30, st));
       UCC_TRY(fetch());
-      bool done = true, changed = false;
+      for (int x = 0; x < n; ++x) jobs[idx[x]]->launches++;
+      if (hb.error & 1) return fail(UCC_ETIMEOUT, "a grid barrier of the persistent batch timed out");
+      if (hb.error) return fail(UCC_ECAPACITY, "a batched job outgrew the table it was given");
+      bool waiting = false, done = true;
       for (int x = 0; x < n; ++x) {
         ucc_ctx* c = jobs[idx[x]];
         if (hs[x].k < c->K) done = false;
-        const bool sparse = hs[x].n_dead > 4096 && hs[x].n_dead * 4 > hs[x].n_tail;
-        if (hs[x].stop >= 0 || (sparse && hs[x].k < c->K)) {
-          UCC_TRY(ensure_room(c, c->ts[0], record));
+        if (hs[x].stop >= 0) {
+          waiting = true;
+          UCC_TRY(read_counters(c, c->ts[0]));
+          const Counters h = *c->ts[0].h_cnt;
+          UCC_TRY(ensure_tape(c, 2 * (h.tape_n + 2 * h.n_tail) + (1 << 12)));
           hs[x].stop = -1;
-          changed = true;
         }
       }
       if (done) break;
-      if (changed) {
-        UCC_TRY(upload());
-        CUDA_TRY(launch_batch_layout(d_jobs, d_js, n, d_bh, 0, st));
-      }
+      if (!waiting || round > 4096) return fail(UCC_ECUDA, "persistent batch made no progress");
+      UCC_TRY(sync_swaps());
+      for (int x = 0; x < n; ++x) hv[x].tape = jobs[idx[x]]->tape();
+      CUDA_TRY(cudaMemcpyAsync(d_jobs, hv.data(), n * sizeof(JobView), cudaMemcpyHostToDevice, st));
+      CUDA_TRY(cudaMemcpyAsync(d_js, hs.data(), n * sizeof(JobState), cudaMemcpyHostToDevice, st));
+      UCC_TRY(reset_header(-1));
     }
     CUDA_TRY(cudaEventRecord(c0->ev[1], st));
+    UCC_TRY(sync_swaps());
     for (int x = 0; x < n; ++x) {
       ucc_ctx* c = jobs[idx[x]];
       UCC_TRY(read_counters(c, c->ts[0]));
-      if (record) {
-        // The batched reverse re-inserts tapes without host checks: make room
-        // for the whole (small) tape now, before sigma and lambda exist.
-        const Counters h = *c->ts[0].h_cnt;
-        const unsigned long long need = h.n_tail + h.tape_n;
-        if (need > c->ts[0].cur.cap_n || 4ull * need > 3ull * c->ts[0].cur.n_slots) {
-          UCC_TRY(rebuild(c, c->ts[0], std::max<unsigned long long>(c->ts[0].cur.cap_n,
-                                                                    2 * (h.n_tail - h.n_dead + h.tape_n) + 64)));
-          UCC_TRY(read_counters(c, c->ts[0]));
-        }
-      }
+      c->cut_total = hs[x].cut;
       fill_forward_stats(c, *c->ts[0].h_cnt);
       c->stats.tape_entries = (long long)c->ts[0].h_cnt->tape_n;
+      c->stats.forward_launches = 1;
+      c->stats.probe_width = pw;
+      c->stats.capacity_entries = (long long)c->ts[0].cur.cap_n;
+      c->stats.hash_slots = (long long)c->ts[0].cur.n_slots;
     }
     // Energy of every job in one launch.
     for (int x = 0; x < n; ++x) hs[x].e_num = hs[x].norm2 = hs[x].gacc = 0.0;
-    UCC_TRY(upload());
+    CUDA_TRY(cudaMemcpyAsync(d_js, hs.data(), n * sizeof(JobState), cudaMemcpyHostToDevice, st));
     for (int x = 0; x < n; ++x)
       CUDA_TRY(cudaMemsetAsync(&jobs[idx[x]]->ts[0].d_cnt->sig_probes, 0, 2 * sizeof(unsigned long long), st));
-    CUDA_TRY(launch_batch_layout(d_jobs, d_js, n, d_bh, 1, st));
+    CUDA_TRY(launch_batch_layout(d_jobs, d_js, n, d_bh, st));
     CUDA_TRY(cudaEventRecord(c0->ev[2], st));
-    CUDA_TRY(launch_sigma_batch(d_jobs, d_js, n, d_bh, grid, st));
+    CUDA_TRY(launch_sigma_batch(d_jobs, d_js, n, d_bh, c0->full_grid(), st));
     CUDA_TRY(cudaEventRecord(c0->ev[3], st));
     UCC_TRY(fetch());
     for (int x = 0; x < n; ++x) {
@@ -1023,22 +1208,31 @@ ucc_status batch_on_stream(const std::vector<int>& idx, ucc_ctx* const* jobs, do
       c->launches += 3;
     }
     if (record) {
-      CUDA_TRY(launch_lambda_init_batch(d_jobs, d_js, n, d_bh, grid, st));
-      for (int x = 0; x < n; ++x) hs[x].k = jobs[idx[x]]->K - 1;
-      CUDA_TRY(cudaMemcpyAsync(d_js, hs.data(), n * sizeof(JobState), cudaMemcpyHostToDevice, st));
-      CUDA_TRY(cudaEventRecord(c0->ev[4], st));
-      if (g_rev) {
-        for (int s = 0; s < maxK; s += 32) CUDA_TRY(cudaGraphLaunch(g_rev, st));
-      } else {
-        for (int s = 0; s < maxK; ++s) CUDA_TRY(launch_reverse_batch(d_jobs, d_js, n, d_bh, grid, st));
+      CUDA_TRY(launch_lambda_init_batch(d_jobs, d_js, n, d_bh, c0->full_grid(), st));
+      for (int x = 0; x < n; ++x) {
+        hs[x].k = jobs[idx[x]]->K - 1;
+        hs[x].gacc = 0.0;
       }
+      CUDA_TRY(cudaMemcpyAsync(d_js, hs.data(), n * sizeof(JobState), cudaMemcpyHostToDevice, st));
+      g_rev = capture_one(st, [&]() { return launch_persist_reverse(d_jobs, d_js, n, d_bh, pw, tiles, st); });
+      UCC_TRY(reset_header(-1));
+      CUDA_TRY(cudaEventRecord(c0->ev[4], st));
+      if (g_rev)
+        CUDA_TRY(cudaGraphLaunch(g_rev, st));
+      else
+        CUDA_TRY(launch_persist_reverse(d_jobs, d_js, n, d_bh, pw, tiles, st));
       CUDA_TRY(cudaEventRecord(c0->ev[5], st));
       UCC_TRY(fetch());
+      if (hb.error & 1) return fail(UCC_ETIMEOUT, "a grid barrier of the persistent batch timed out");
+      if (hb.error) return fail(UCC_ECAPACITY, "a batched job outgrew the table it was given");
+      UCC_TRY(sync_swaps());
       for (int x = 0; x < n; ++x) {
         ucc_ctx* c = jobs[idx[x]];
         if (hs[x].k != -1) return fail(UCC_ECUDA, "batched reverse sweep did not finish");
-        if (c->K) CUDA_TRY(cudaMemcpyAsync(grads[idx[x]], c->d_grad, c->K * sizeof(double), cudaMemcpyDeviceToHost, st));
-        c->launches += 1 + 4LL * maxK;
+        if (c->K && grads[idx[x]])
+          CUDA_TRY(cudaMemcpyAsync(grads[idx[x]], c->d_grad, c->K * sizeof(double), cudaMemcpyDeviceToHost, st));
+        c->launches += 2;
+        c->stats.reverse_launches = 1;
       }
     }
     float ms = 0.f;
@@ -1048,6 +1242,7 @@ ucc_status batch_on_stream(const std::vector<int>& idx, ucc_ctx* const* jobs, do
       c->stats.sigma_probes = (long long)c->ts[0].h_cnt->sig_probes;
       c->stats.sigma_hits = (long long)c->ts[0].h_cnt->sig_hits;
       c->stats.reverse_pairs = (long long)c->ts[0].h_cnt->rev_pairs;
+      c->stats.reverse_scanned = (long long)c->ts[0].h_cnt->rev_scanned;
       c->stats.kernel_launches = c->launches;
       c->have_psi = !record;
       c->have_sigma = !record;
@@ -1060,9 +1255,17 @@ ucc_status batch_on_stream(const std::vector<int>& idx, ucc_ctx* const* jobs, do
       CUDA_TRY(cudaEventElapsedTime(&ms, c0->ev[4], c0->ev[5]));
       c0->stats.reverse_ms = ms;
     }
+    c0->stats.probe_width = pw;
+    for (int x = 0; x < n; ++x) jobs[idx[x]]->stats.batch_tiles = tiles;
     return UCC_OK;
   };
   ucc_status s = run();
+  if (s != UCC_OK) {
+    // leave the host view consistent with the device arrays
+    std::string msg = g_last_error;
+    sync_swaps();
+    g_last_error = msg;
+  }
   release();
   return s;
 }
@@ -1083,7 +1286,7 @@ ucc_status batch_together(const std::vector<int>& idx, ucc_ctx* const* jobs, dou
   cudaEventRecord(e_in, caller);
   cudaStreamWaitEvent(bs, e_in, 0);
   for (int j : idx) jobs[j]->stream = bs;
-  ucc_status s = batch_on_stream(idx, jobs, eps, E, grads);
+  ucc_status s = batch_persistent(idx, jobs, eps, E, grads);
   for (int j : idx) jobs[j]->stream = caller;
   cudaEventRecord(e_out, bs);
   cudaStreamWaitEvent(caller, e_out, 0);
@@ -1133,6 +1336,7 @@ ucc_status ucc_create(const ucc_hamiltonian* ham, const ucc_ansatz* an, void* cu
   if ((s = c->ts[0].init()) != UCC_OK) return bail(s);
   if ((s = c->ts[1].init()) != UCC_OK) return bail(s);
   if ((s = dalloc(&c->d_sel, 1)) != UCC_OK) return bail(s);
+  if ((s = dalloc(&c->d_cand, kSelectCandCap)) != UCC_OK) return bail(s);
   if ((s = dalloc(&c->t_off, (size_t)c->K + 1)) != UCC_OK) return bail(s);
   if ((s = dalloc(&c->d_pages, kTapeMaxPages)) != UCC_OK) return bail(s);
   if ((s = dalloc(&c->d_entropy, std::max(1, c->K))) != UCC_OK) return bail(s);
@@ -1140,6 +1344,8 @@ ucc_status ucc_create(const ucc_hamiltonian* ham, const ucc_ansatz* an, void* cu
   for (auto& e : c->ev)
     if (cudaEventCreate(&e) != cudaSuccess) return bail(fail(UCC_ECUDA, "event creation failed"));
   for (auto& e : c->kev)
+    if (cudaEventCreate(&e) != cudaSuccess) return bail(fail(UCC_ECUDA, "event creation failed"));
+  for (auto& e : c->rev_)
     if (cudaEventCreate(&e) != cudaSuccess) return bail(fail(UCC_ECUDA, "event creation failed"));
   if (cudaMemcpyAsync(c->d_h, ham->h, n * n * sizeof(double), cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
       cudaMemcpyAsync(c->d_g, ham->g, n * n * n * n * sizeof(double), cudaMemcpyHostToDevice, c->stream) !=
@@ -1174,6 +1380,9 @@ ucc_status ucc_set_options(ucc_ctx* c, const ucc_options* opt) {
   if (o.n_max > 0 && (o.n_cut <= 0 || o.n_cut > o.n_max)) return fail(UCC_EINVAL, "need 0 < n_cut <= n_max");
   if (o.probe_width != 0 && o.probe_width != 1 && o.probe_width != 2 && o.probe_width != 4 && o.probe_width != 8)
     return fail(UCC_EINVAL, "probe_width must be 0, 1, 2, 4 or 8");
+  if (o.batch_wait_ms < 0 || o.batch_test_skip_block < 0) return fail(UCC_EINVAL, "negative option");
+  if (o.batch_tiles != 0 && o.batch_tiles != 1 && o.batch_tiles != 2 && o.batch_tiles != 4 && o.batch_tiles != 8)
+    return fail(UCC_EINVAL, "batch_tiles must be 0, 1, 2, 4 or 8");
   c->opt = o;
   return UCC_OK;
 }
@@ -1274,11 +1483,12 @@ ucc_status ucc_batch_run(int n_jobs, ucc_ctx* const* jobs, double eps, double* E
       return fail(UCC_EINVAL, "batched jobs must share one device and one stream");
   }
   CUDA_TRY(cudaSetDevice(jobs[0]->device));
-  // Jobs with the N_MAX/N_CUT cut need segment checkpoints: they run one by one.
+  // Jobs whose table cannot be sized up front (no cut and a large sector)
+  // run one by one; the rest share the persistent launches.
   std::vector<int> together;
   for (int j = 0; j < n_jobs; ++j) {
     ucc_ctx* c = jobs[j];
-    if (c->opt.n_max > 0 || together.size() >= (size_t)kMaxBatchJobs) {
+    if (batch_capacity(c) == 0 || together.size() >= (size_t)kMaxBatchJobs) {
       if (grads && grads[j]) {
         UCC_TRY(run_gradient(c, eps, &E[j], grads[j], 0));
       } else {

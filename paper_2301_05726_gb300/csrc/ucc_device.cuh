@@ -80,6 +80,10 @@ __device__ __forceinline__ unsigned int dead_stamp(double v) {
 }
 
 __device__ __forceinline__ void raise_error(Counters* c, int bit) { atomicOr(&c->error, bit); }
+__device__ __forceinline__ void raise_consistency(Counters* c, int site, unsigned long long key = 0ull) {
+  atomicOr(&c->error, ERR_CONSISTENCY);
+  if (atomicCAS(&c->err_site, 0, site) == 0) c->err_key = key;
+}
 
 // Result of looking a key up.
 enum Found : int { ABSENT = 0, ALIVE = 1, DEAD_NOW = 2, DEAD_OLD = 3 };
@@ -213,7 +217,7 @@ __device__ __forceinline__ Lookup findG(const Table& t, unsigned long long key, 
 // Only one lane ever inserts a given key during a step, so a lost CAS means
 // another key took the slot and the probe moves on.
 __device__ __forceinline__ unsigned long long claim_slot(const Table& t, unsigned long long key,
-                                                         unsigned long long start) {
+                                                         unsigned long long start, int site = SITE_DUP_CLAIM) {
   unsigned long long h = start & t.slot_mask;
   for (int step = 0; step < MAX_PROBE; ++step) {
     unsigned long long prev = atomicCAS(&t.slots[h].key, 0ull, key);
@@ -222,7 +226,7 @@ __device__ __forceinline__ unsigned long long claim_slot(const Table& t, unsigne
       return h;
     }
     if (prev == key) {
-      raise_error(t.cnt, ERR_CONSISTENCY);
+      raise_consistency(t.cnt, site, key);
       return h;
     }
     h = (h + 1) & t.slot_mask;
@@ -243,8 +247,9 @@ __device__ __forceinline__ unsigned long long aggregated_add(unsigned long long*
 
 // Append (key, amp) as a new entry and point a slot at it.
 __device__ __forceinline__ bool insert_new(const Table& t, unsigned long long key, double amp, unsigned int born,
-                                           unsigned long long start_slot, bool with_born, bool with_lam) {
-  unsigned long long s = claim_slot(t, key, start_slot);
+                                           unsigned long long start_slot, bool with_born, bool with_lam,
+                                           int site = SITE_DUP_CLAIM) {
+  unsigned long long s = claim_slot(t, key, start_slot, site);
   unsigned long long idx = aggregated_add(&t.cnt->n_tail);
   if (idx >= t.cap_n || s == ~0ull) {
     raise_error(t.cnt, ERR_CAPACITY);

@@ -47,8 +47,23 @@ struct Counters {
   int stop_k;                 // first factor skipped: no room, or a cut is due (-1: none)
   int error;                  // device error word (bit flags below)
   int cut_pending;            // more than n_max live entries after factor stop_k - 1
+  int err_site;               // where the first consistency error was raised (ErrSite)
+  unsigned long long err_key; // the key involved in it
   double e_num, norm2;        // <psi|H|psi>, <psi|psi> of the last energy pass
   double entropy;             // running Eq. 6 entropy of the stored state (when recorded)
+};
+
+// Where a consistency error was raised (Counters::err_site, first one wins).
+enum ErrSite : int {
+  SITE_PAIR_OWNER = 1,    // a factor step found the excited member's partner dropped in the same step
+  SITE_DUP_CLAIM = 2,     // a slot claim met its own key already hashed
+  SITE_REHASH_DUP = 3,    // a rehash met a key twice
+  SITE_TAPE_ALIVE = 4,    // a kill-tape record's key was live when re-inserted
+  SITE_BULK_ALIVE = 5,    // the same, bulk re-insertion
+  SITE_BATCH_ALIVE = 6,   // the same, persistent batched reverse
+  SITE_CREATE_DUP = 7,    // a created partner's key was already hashed
+  SITE_REINSERT_DUP = 8,  // a re-inserted record's key was already hashed
+  SITE_REBUILD_DUP = 9    // a compaction kept a key twice
 };
 
 enum DeviceError : int {
@@ -110,11 +125,31 @@ struct SelectState {
   unsigned long long prefix, target;          // |c| bits of the threshold, rank left inside it
   unsigned long long key_prefix, key_target;  // key tie-break among |c| == threshold
   unsigned long long count_eq, cut_total;
+  unsigned long long n_cand;                  // entries gathered into the candidate buffer
   int need_keys, pad;
   unsigned long long hist[2048];
 };
 
-// One job of a batch, as the batched kernels see it (uploaded by the host).
+// A candidate of the selection's last passes: |c| as its IEEE bit pattern and the key.
+struct SelectCand {
+  unsigned long long mag, key;
+};
+constexpr unsigned long long kSelectCandCap = 1ull << 16;  // candidates the buffer holds
+
+// A second set of table arrays of a job (same sizes as its current ones): the
+// target of the job's compactions and cuts inside the persistent batched
+// kernels, which swap the two sets on the device.
+struct SpareArrays {
+  unsigned long long* keys;
+  double* amps;
+  unsigned int* born;
+  double* lam;
+  Slot* slots;
+  unsigned int* filt;
+};
+
+// One job of a batch, as the batched kernels see it (uploaded by the host;
+// the persistent kernels swap t's arrays with sp's on the device).
 struct JobView {
   Table t;
   const Factor* factors;
@@ -124,6 +159,8 @@ struct JobView {
   double eps;
   int K;
   int pad;
+  SpareArrays sp;
+  long long n_max, n_cut;  // the Methods-section cut of this job (n_max 0: none)
 };
 
 // Per-job progress, written by the batched kernels and read back by the host.
@@ -134,15 +171,30 @@ struct JobState {
   unsigned long long n;       // entries of the job this step covers
   unsigned long long n_tail, n_dead, tape_n;  // mirror of the job's counters after the step
   double e_num, norm2, gacc;  // energy sums; gradient accumulator of the current factor
+  unsigned long long rbase, rn;  // reverse: this step's tape records of the job in the record index space
+  long long cut;              // entries the job's cuts removed
+  int swapped;                // the job's current arrays are its spare set (odd number of swaps)
+  int pad2;
 };
 
 struct BatchHeader {
   unsigned long long total;   // size of the batch index space of the next step
   unsigned int done;          // last-block arrival counter
   int pad;
+  unsigned long long rtotal;  // reverse: size of the tape-record index space of the next step
+  unsigned int bar_count, bar_gen;  // grid barrier of the persistent kernels
+  int active;                 // jobs still stepping after the last layout
+  int error;                  // persistent kernels: 1 = a grid barrier timed out, 2 = a job ran out of room
+  int skip_block;             // test hook: this block leaves before the first grid barrier (-1: none)
+  int steps;                  // steps the persistent kernel ran (all launches of the call)
+  unsigned long long wait_ns; // bound of one grid-barrier wait
 };
 
 constexpr int kMaxBatchJobs = 1024;
+
+// Largest entry capacity of one table (the factor steps' queues index entries
+// in 31 bits): 2^31 entries, about 120 GB of table.
+constexpr unsigned long long kMaxEntries = 1ull << 31;
 
 constexpr unsigned int BORN_INITIAL = 0xFFFFFFFFu;  // the reference determinant
 
@@ -151,8 +203,14 @@ cudaError_t launch_reset(const Table& t, unsigned long long hf, cudaStream_t st)
 cudaError_t launch_forward(const Table& t, const Factor* factors, int k, double eps, unsigned int stamp,
                            int record, const Tape& tape, unsigned long long n_max, int probe_width, int grid,
                            cudaStream_t st);
-cudaError_t launch_select_cut(const Table& t, SelectState* sel, unsigned long long n_cut, unsigned int stamp,
-                              int record, const Tape& tape, int k, int grid, cudaStream_t st, long long* launches);
+// The N_CUT-th entry by (|c| descending, key ascending) into sel: prefix (its |c| bits), need_keys and
+// key_prefix (the largest kept key among entries with that |c|).
+cudaError_t launch_select_threshold(const Table& t, SelectState* sel, SelectCand* cand, unsigned long long n_cut,
+                                    int grid, cudaStream_t st, long long* launches);
+// Copy the entries the threshold keeps into `to` (live entries only, unordered, counted in new_n) and
+// record the ones it drops on the tape as factor k's (record) or account their entropy.
+cudaError_t launch_cut_compact(const Table& from, const Table& to, const SelectState* sel, int record,
+                               const Tape& tape, int k, int grid, cudaStream_t st);
 cudaError_t launch_compact(const Table& from, const Table& to, int with_born, int grid, cudaStream_t st);
 cudaError_t launch_rehash(const Table& t, int grid, cudaStream_t st);
 cudaError_t launch_finish_rebuild(const Table& t, cudaStream_t st);
@@ -170,19 +228,23 @@ cudaError_t launch_transfer_lambda(const Table& dst, const Table& src, int grid,
 cudaError_t launch_probe_bench(const Table& t, const Factor& f, int probe_width, unsigned long long* sink, int grid,
                                cudaStream_t st);
 int sigma_smem_bytes(int n_so);
-// Batched (many-job) launches; mode 0 lays out the forward index space
-// (n_scan of jobs still applying factors), 1 the energy space (n_tail of every
-// job), 2 the reverse space (n_tail of jobs still undoing factors).
-cudaError_t launch_batch_layout(const JobView* jobs, JobState* js, int n_jobs, BatchHeader* bh, int mode,
-                                cudaStream_t st);
-cudaError_t launch_forward_batch(const JobView* jobs, JobState* js, int n_jobs, BatchHeader* bh, int record,
-                                 int grid, cudaStream_t st);
+// Batched (many-job) energy: the layout of every job's stored entries, then
+// sigma and the energy sums of every job in one launch.
+cudaError_t launch_batch_layout(const JobView* jobs, JobState* js, int n_jobs, BatchHeader* bh, cudaStream_t st);
 cudaError_t launch_sigma_batch(const JobView* jobs, JobState* js, int n_jobs, BatchHeader* bh, int grid,
                                cudaStream_t st);
 cudaError_t launch_lambda_init_batch(const JobView* jobs, JobState* js, int n_jobs, BatchHeader* bh, int grid,
                                      cudaStream_t st);
-cudaError_t launch_reverse_batch(const JobView* jobs, JobState* js, int n_jobs, BatchHeader* bh, int grid,
-                                 cudaStream_t st);
+// Persistent batched passes: one cooperative launch runs every job's factor
+// steps (forward: up to max_steps steps, or until no job can step) with
+// bounded grid barriers.  probe_width 1/2/4/8, tiles = 32-entry tiles a warp
+// takes per visit of a job (1, 2, 4 or 8).  Returns the launch's error.
+cudaError_t launch_persist_forward(JobView* jobs, JobState* js, int n_jobs, BatchHeader* bh, int record,
+                                   int probe_width, int tiles, int max_steps, cudaStream_t st);
+cudaError_t launch_persist_reverse(JobView* jobs, JobState* js, int n_jobs, BatchHeader* bh, int probe_width,
+                                   int tiles, cudaStream_t st);
+// The persistent kernels' grid (blocks resident at once) on the current device.
+int persist_grid(int record, int probe_width, int reverse);
 // Message returned by ucc_last_error() on the calling thread.
 void set_last_error(const char* msg);
 

@@ -120,7 +120,7 @@ __device__ __forceinline__ void forward_resolve(const Table& t, const Factor& f,
   const bool partner_live = (r.state == ALIVE);
   if (!ex && (partner_live || r.state == DEAD_NOW)) return;  // E's thread owns the pair
   if (ex && r.state == DEAD_NOW) {
-    raise_error(t.cnt, ERR_CONSISTENCY);
+    raise_consistency(t.cnt, SITE_PAIR_OWNER);
     return;
   }
   const unsigned long long E = ex ? X : Y;
@@ -195,7 +195,7 @@ __device__ __forceinline__ void forward_resolve(const Table& t, const Factor& f,
     if (DEFER)
       append_unlinked(t, Y, nY, (unsigned int)k, RECORD);
     else
-      insert_new(t, Y, nY, (unsigned int)k, r.slot, RECORD, false);
+      insert_new(t, Y, nY, (unsigned int)k, r.slot, RECORD, false, SITE_CREATE_DUP);
     ++sc.cre;
   }
 }
@@ -316,31 +316,42 @@ __device__ __forceinline__ void reverse_entry(const Table& t, const Factor& f, i
 // does not matter: ownership and the dropped-entry stamps decide everything
 // from the state at the start of the step.
 //
-// The keys and amplitudes of a warp's next round of kScanTiles tiles are
+// The keys and amplitudes of a warp's next round of kScanTiles tiles (and,
+// with AUX, a third per-entry array: the adjoint in the reverse sweep) are
 // copied into shared memory (cp.async, two buffers per warp) while it works on
-// the current one, so the scan's load latency overlaps the pair work.
+// the current one, so the scan's load latency overlaps the pair work and a
+// linked entry's own values never need a load of their own.
 constexpr int kScanTiles = 2;
 constexpr int kRound = 32 * kScanTiles;
 constexpr int kQueue = 64;
-constexpr unsigned long long kExBit = 1ull << 63;
+// Queue entries keep the entry index in 31 bits and the excited-member flag in
+// the top bit: the host keeps every table below kMaxEntries entries.
+constexpr unsigned int kExBit = 1u << 31;
+static_assert(kMaxEntries <= (1ull << 31), "queue indices are 31-bit");
 
-struct LinkQueue {
-  unsigned long long i[kQueue];  // entry index, kExBit set for the excited member
+template <bool AUX>
+struct LinkQueueT {
+  unsigned int i[kQueue];  // entry index, kExBit set for the excited member
   unsigned long long X[kQueue];
   double c[kQueue];
+  double m[AUX ? kQueue : 1];
 };
 
-struct __align__(16) ScanStage {
+template <bool AUX>
+struct __align__(16) ScanStageT {
   unsigned long long X[kRound];
   double c[kRound];
+  double m[AUX ? kRound : 2];
 };
 
 // Per-warp shared memory of for_each_linked.
-struct LinkScratch {
-  ScanStage stage[2];
-  LinkQueue linked;  // linked entries, before the filter test
-  LinkQueue probe;   // linked entries whose partner may be stored
+template <bool AUX>
+struct LinkScratchT {
+  ScanStageT<AUX> stage[2];
+  LinkQueueT<AUX> linked;  // linked entries, before the filter test
+  LinkQueueT<AUX> probe;   // linked entries whose partner may be stored
 };
+using LinkScratch = LinkScratchT<false>;
 
 // Threads per block of the kernels built on for_each_linked: with four warps
 // per block, the eight blocks an SM holds at 64 registers per thread also fit
@@ -355,16 +366,18 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_all_but_last() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
 // The staged scan copies 16-byte pieces starting at even entries, so keys and
-// amps must start on a 16-byte boundary (device allocations do).
+// amps (and lam) must start on a 16-byte boundary (device allocations do).
 inline bool scan_aligned(const Table& t) {
-  return ((reinterpret_cast<uintptr_t>(t.keys) | reinterpret_cast<uintptr_t>(t.amps)) & 15u) == 0u;
+  return ((reinterpret_cast<uintptr_t>(t.keys) | reinterpret_cast<uintptr_t>(t.amps) |
+           reinterpret_cast<uintptr_t>(t.lam)) & 15u) == 0u;
 }
 
-// Copy entries [base, min(base + kRound, n)) of keys and amps into a stage:
-// 16-byte pieces of two entries; the piece holding entry n - 1 alone copies 8
-// bytes (the rest zero-filled) and pieces past n are not issued.
-__device__ __forceinline__ void stage_round(const Table& t, ScanStage& st, unsigned long long base,
-                                            unsigned long long n, unsigned int lane) {
+// Copy entries [base, min(base + kRound, n)) of keys and amps (and aux) into a
+// stage: 16-byte pieces of two entries; the piece holding entry n - 1 alone
+// copies 8 bytes (the rest zero-filled) and pieces past n are not issued.
+template <bool AUX>
+__device__ __forceinline__ void stage_round(const Table& t, const double* aux, ScanStageT<AUX>& st,
+                                            unsigned long long base, unsigned long long n, unsigned int lane) {
 #pragma unroll
   for (int h = 0; h < kRound / 64; ++h) {
     const int e = 2 * (int)(lane + 32u * h);  // first entry of the piece, relative to base
@@ -373,6 +386,7 @@ __device__ __forceinline__ void stage_round(const Table& t, ScanStage& st, unsig
       const int bytes = g + 1ull < n ? 16 : 8;
       cp_async16(&st.X[e], t.keys + g, bytes);
       cp_async16(&st.c[e], t.amps + g, bytes);
+      if (AUX) cp_async16(&st.m[e], aux + g, bytes);
     }
   }
 }
@@ -387,58 +401,64 @@ __device__ __forceinline__ Lookup absent_lookup() {
   return r;
 }
 
-// Append (i, X, c, ex) of the active lanes (ballot m) to queue q at qn.
-__device__ __forceinline__ void enqueue(LinkQueue& q, int qn, unsigned int m, unsigned int below_me, bool act,
-                                        unsigned long long i, unsigned long long X, double c, bool ex) {
+// Append (i, X, c, ex, m) of the active lanes (ballot mk) to queue q at qn.
+template <bool AUX>
+__device__ __forceinline__ void enqueue(LinkQueueT<AUX>& q, int qn, unsigned int mk, unsigned int below_me, bool act,
+                                        unsigned long long i, unsigned long long X, double c, bool ex, double m) {
   if (act) {
-    const int p = qn + __popc(m & below_me);
-    q.i[p] = i | (ex ? kExBit : 0ull);
+    const int p = qn + __popc(mk & below_me);
+    q.i[p] = (unsigned int)i | (ex ? kExBit : 0u);
     q.X[p] = X;
     q.c[p] = c;
+    if (AUX) q.m[p] = m;
   }
 }
 
 // Pop the last 32 entries of a queue holding qn >= 32 into the lanes and call
-// f(i, X, c, ex, true).
-template <class F>
-__device__ __forceinline__ void drain32(LinkQueue& q, int& qn, unsigned int lane, F& f) {
+// f(i, X, c, ex, m, true).
+template <bool AUX, class F>
+__device__ __forceinline__ void drain32(LinkQueueT<AUX>& q, int& qn, unsigned int lane, F& f) {
   __syncwarp();
   const int p = qn - 32 + (int)lane;
-  const unsigned long long qi = q.i[p];
+  const unsigned int qi = q.i[p];
   const unsigned long long qX = q.X[p];
   const double qc = q.c[p];
+  const double qm = AUX ? q.m[p] : 0.0;
   __syncwarp();
   qn -= 32;
-  f(qi & ~kExBit, qX, qc, (qi & kExBit) != 0ull, true);
+  f((unsigned long long)(qi & ~kExBit), qX, qc, (qi & kExBit) != 0u, qm, true);
 }
 
 // The qn < 32 entries left in a queue (lanes past qn inactive); empties it.
-template <class F>
-__device__ __forceinline__ void drain_rest(LinkQueue& q, int& qn, unsigned int lane, F& f) {
+template <bool AUX, class F>
+__device__ __forceinline__ void drain_rest(LinkQueueT<AUX>& q, int& qn, unsigned int lane, F& f) {
   __syncwarp();
   const bool a = (int)lane < qn;
-  unsigned long long qi = 0ull, qX = 0ull;
-  double qc = 0.0;
+  unsigned int qi = 0u;
+  unsigned long long qX = 0ull;
+  double qc = 0.0, qm = 0.0;
   if (a) {
     qi = q.i[lane];
     qX = q.X[lane];
     qc = q.c[lane];
+    if (AUX) qm = q.m[lane];
   }
   __syncwarp();
   qn = 0;
-  f(qi & ~kExBit, qX, qc, (qi & kExBit) != 0ull, a);
+  f((unsigned long long)(qi & ~kExBit), qX, qc, (qi & kExBit) != 0u, qm, a);
 }
 
 // Scan entries [0, n) in warp-strided rounds of kRound entries and resolve
-// every live linked entry: lone(i, X, cX, ex, aux, active) when the filter
-// proves its partner absent, probe(i, X, cX, ex, active) otherwise.  aux =
-// pre(i, active) is loaded together with the filter word, so a lone entry
-// that needs one more value of its own (the adjoint, in the reverse sweep)
-// waits for a single round trip.  Every lane of the warp calls this; lone and
-// probe are called by all lanes together.
-template <class Pre, class Lone, class Probe>
+// every live linked entry: lone(i, X, cX, ex, m, active) when the filter
+// proves its partner absent, probe(i, X, cX, ex, m, active) otherwise, where m
+// is the entry's value in aux (AUX: staged with the scan) or, without AUX,
+// pre(i, active) for lone entries (loaded together with the filter word, so a
+// lone entry waits for a single round trip) and 0 for probed ones.  Every lane
+// of the warp calls this; lone and probe are called by all lanes together.
+template <bool AUX, class Pre, class Lone, class Probe>
 __device__ __forceinline__ void for_each_linked(const Table& t, const Factor& f, unsigned long long n,
-                                                LinkScratch& w, Pre pre, Lone lone, Probe probe) {
+                                                LinkScratchT<AUX>& w, const double* aux, Pre pre, Lone lone,
+                                                Probe probe) {
   const unsigned int lane = threadIdx.x & 31u;
   const unsigned int below_me = (1u << lane) - 1u;
   const unsigned long long warp = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -448,8 +468,8 @@ __device__ __forceinline__ void for_each_linked(const Table& t, const Factor& f,
   int nl = 0, np = 0;  // warp-uniform lengths of the linked and probe queues
   // Up to 32 linked entries: the partner's filter bit sends each lane to lone
   // at once or onto the probe queue.
-  auto split = [&](unsigned long long i, unsigned long long X, double c, bool ex, bool act) {
-    const double aux = pre(i, act);
+  auto split = [&](unsigned long long i, unsigned long long X, double c, bool ex, double mu, bool act) {
+    if (!AUX) mu = pre(i, act);
     bool maybe = act;
     if (act && t.filt) {
       const unsigned long long h = (X ^ m) * kFilterMul;
@@ -457,21 +477,21 @@ __device__ __forceinline__ void for_each_linked(const Table& t, const Factor& f,
     }
     const bool pr = act && maybe;
     const unsigned int mp = __ballot_sync(0xFFFFFFFFu, pr);
-    enqueue(w.probe, np, mp, below_me, pr, i, X, c, ex);
+    enqueue<AUX>(w.probe, np, mp, below_me, pr, i, X, c, ex, mu);
     np += __popc(mp);
-    lone(i, X, c, ex, aux, act && !maybe);
-    if (np >= 32) drain32(w.probe, np, lane, probe);
+    lone(i, X, c, ex, mu, act && !maybe);
+    if (np >= 32) drain32<AUX>(w.probe, np, lane, probe);
   };
   unsigned long long base = warp * (unsigned long long)kRound;
-  if (base < n) stage_round(t, w.stage[0], base, n, lane);
+  if (base < n) stage_round<AUX>(t, aux, w.stage[0], base, n, lane);
   cp_async_commit();
   for (int r = 0; base < n; base += step, ++r) {
     // Next round's copy into the other buffer (its last reader was round r - 1).
-    if (base + step < n) stage_round(t, w.stage[(r + 1) & 1], base + step, n, lane);
+    if (base + step < n) stage_round<AUX>(t, aux, w.stage[(r + 1) & 1], base + step, n, lane);
     cp_async_commit();
     cp_async_wait_all_but_last();  // this round's copy has landed (this lane's pieces)
     __syncwarp();                  // ... and every other lane's
-    const ScanStage& st = w.stage[r & 1];
+    const ScanStageT<AUX>& st = w.stage[r & 1];
     // Not unrolled: the body inlines the resolve paths (instruction cache).
 #pragma unroll 1
     for (int u = 0; u < kScanTiles; ++u) {
@@ -479,7 +499,7 @@ __device__ __forceinline__ void for_each_linked(const Table& t, const Factor& f,
       const unsigned long long i = base + (unsigned long long)e;
       bool act = false, ex = false;
       unsigned long long X = 0ull;
-      double cX = 0.0;
+      double cX = 0.0, mu = 0.0;
       if (i < n) {
         X = st.X[e];
         // occ and vir are disjoint: E holds exactly occ of the factor's
@@ -489,18 +509,19 @@ __device__ __forceinline__ void for_each_linked(const Table& t, const Factor& f,
         if (ex || tX == f.vir) {
           cX = st.c[e];
           act = !is_dead(cX);
+          if (AUX) mu = st.m[e];
         }
       }
       const unsigned int ml = __ballot_sync(0xFFFFFFFFu, act);
-      enqueue(w.linked, nl, ml, below_me, act, i, X, cX, ex);
+      enqueue<AUX>(w.linked, nl, ml, below_me, act, i, X, cX, ex, mu);
       nl += __popc(ml);
-      if (nl >= 32) drain32(w.linked, nl, lane, split);
+      if (nl >= 32) drain32<AUX>(w.linked, nl, lane, split);
     }
     __syncwarp();  // every lane is done with this buffer before it is refilled
   }
   asm volatile("cp.async.wait_all;\n" ::: "memory");  // nothing left in flight
-  if (nl > 0) drain_rest(w.linked, nl, lane, split);
-  if (np > 0) drain_rest(w.probe, np, lane, probe);
+  if (nl > 0) drain_rest<AUX>(w.linked, nl, lane, split);
+  if (np > 0) drain_rest<AUX>(w.probe, np, lane, probe);
 }
 
 constexpr int kMaxSpin = 32;                          // spin-orbitals of one spin

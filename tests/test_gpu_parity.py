@@ -411,3 +411,24 @@ def test_one_tape_vs_sqrt_k_checkpoints_64so(torch_cuda):
     drift = np.max(np.abs(g1 - g2))
     print(f"one tape vs sqrt(K) checkpoints: max |dg| = {drift:.3e} (|g|max = {np.max(np.abs(g1)):.3e})")
     assert drift <= 1e-10
+
+
+def test_truncation_with_many_exact_ties(torch_cuda):
+    # Zero angles after the first eight factors: every partner they create has
+    # amplitude exactly 0 (eps = 0 keeps it), so each cut's threshold is 0 with
+    # about 1e5 exactly tied entries, more than the selection's candidate buffer
+    # holds: the tie-break by smaller key runs on the table itself.
+    prob = synth.config_problem(2).prefix(300)
+    th = prob.theta.copy()
+    th[8:] = 0.0
+    prob = prob.with_theta(th)
+    n_max, n_cut = 100_000, 70_000
+    ok, oa, oc = oracle_for(prob).apply(n_max=n_max, n_cut=n_cut)
+    assert oc["cut"] > 4 * n_cut and np.sum(oa == 0.0) > 0.9 * len(oa)
+    ctx = ctx_for(prob)
+    ctx.set_options(n_max=n_max, n_cut=n_cut)
+    ctx.apply()
+    gk, ga = ctx.wavefunction()
+    assert_same_state(gk, ga, ok, oa)
+    st = ctx.stats()
+    assert st["cut"] == oc["cut"] and st["rotations"] == oc["rotations"]
