@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--no-n1", action="store_true", help="skip the 40-spin-orbital adjoint/batched vs plain leg")
     ap.add_argument("--n1-fd-components", type=int, default=2)
     ap.add_argument("--n1-batch", type=int, default=2, help="theta vectors in the 40-spin-orbital batched leg")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 256-job batched leg")
     return ap.parse_args()
 
 
@@ -370,6 +371,65 @@ def n1_leg(args):
     return out
 
 
+def batch_leg(args):
+    """The 256-job workload (16-36 spin-orbitals, 4-12 electrons, theta ~ N(0, 0.02), eps = 1e-8), each
+    job with the paper's production cut (N_MAX = 8,000, N_CUT = 5,000): energies and adjoint gradients
+    of all jobs through one ucc_batch_run call (persistent launches), and the same for a sample of jobs
+    against the one-job path."""
+    import torch
+    from paper_2301_05726_gb300 import synth
+    from paper_2301_05726_gb300.api import UCCContext, batch_run
+
+    def jobs(ids):
+        out = []
+        for j in ids:
+            p = synth.batch_job_problem(j)
+            p.n_max, p.n_cut = BATCH_N_MAX, BATCH_N_CUT
+            out.append(p)
+        return out
+
+    probs = jobs(range(256))
+    ctxs = [UCCContext(p) for p in probs]
+    batch_run(ctxs, 1e-8, with_grad=True)  # warm-up (tunes probe width and tiles once)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    E, _ = batch_run(ctxs, 1e-8, with_grad=True)
+    torch.cuda.synchronize()
+    tb = time.perf_counter() - t0
+    st = [c.stats() for c in ctxs]
+    rot = sum(x["rotations"] for x in st)
+    out = {"workload": "256 jobs, 16-36 so, 4-12 e, eps 1e-8, cut n_max=8000 n_cut=5000",
+           "factors": sum(p.n_exc for p in probs), "seconds": tb, "evals_per_s": len(probs) / tb,
+           "det_rotations_per_s": rot / tb, "probe_width": st[0]["probe_width"], "tiles": st[0]["batch_tiles"],
+           "phase_ms": {"forward": st[0]["apply_ms"], "energy": st[0]["energy_ms"], "reverse": st[0]["reverse_ms"]},
+           "jobs_cut": sum(x["cut"] > 0 for x in st)}
+    for c in ctxs:
+        c.close()
+    # a sample of jobs: the batch vs one job at a time (the one-job path, host-driven cuts)
+    sample = list(range(0, 256, 32))
+    sp = jobs(sample)
+    sc = [UCCContext(p) for p in sp]
+    batch_run(sc, 1e-8, with_grad=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    batch_run(sc, 1e-8, with_grad=True)
+    torch.cuda.synchronize()
+    t_b = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    for c in sc:
+        c.gradient(eps=1e-8)
+    torch.cuda.synchronize()
+    t_s = time.perf_counter() - t0
+    for c in sc:
+        c.close()
+    out["sample_vs_one_by_one"] = {"jobs": sample, "batched_s": t_b, "one_by_one_s": t_s, "speedup": t_s / t_b}
+    return out
+
+
+# The paper's production truncation (Methods section), carried by every job of the batched workload.
+BATCH_N_MAX, BATCH_N_CUT = 8000, 5000
+
+
 def run_ours(args, prob):
     import numpy as np
     import torch
@@ -457,6 +517,9 @@ def run_ours(args, prob):
     n1 = None
     if rank == 0 and not args.no_n1:
         n1 = n1_leg(args)
+    batched = None
+    if rank == 0 and not args.no_batch:
+        batched = batch_leg(args)
 
     if rank != 0:
         if world > 1:
@@ -494,6 +557,7 @@ def run_ours(args, prob):
                      "cuts": tot["cut_ms"] / n_steps, "other_rebuilds": tot["rebuild_ms"] / n_steps},
         "vs_plain": plain,
         "n1_40so": n1,
+        "batched": batched,
         "e2e": {"value": rot_all / (e2e_ms / 1e3), "unit": UNIT, "steps": len(e2e_times),
                 "h2d_bytes_per_step": FACTOR_BYTES * prob.n_exc, "d2h_bytes_per_step": 8 * prob.n_exc + 8},
         "gpu_launches": int(tot["kernel_launches"]),

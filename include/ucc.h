@@ -5,7 +5,7 @@
  * wavefunction circuit simulator of Mullinax & Tubman (arXiv 2301.05726):
  * the factorised unitary-coupled-cluster state of Eq. 3,
  *     |psi> = U_K ... U_2 U_1 |Psi_0>,   U_k = exp(theta_k (tau_k - tau_k^+))
- * (Eqs. 4-5), held as a sparse map from 64-bit determinant bit strings to
+ * (Eqs. 4-5), held as a sparse map from determinant bit strings to
  * FP64 amplitudes, with amplitudes below eps discarded after every factor
  * (Methods section), the energy <psi|H|psi>/<psi|psi> of the molecular
  * Hamiltonian built from one- and two-electron integrals (Methods section),
@@ -13,8 +13,10 @@
  *
  * Conventions shared by every call:
  *   - spin-orbital p = 2*spatial + spin (0 = alpha, 1 = beta); bit p of a
- *     determinant key is the Jordan-Wigner qubit of spin-orbital p; at most
- *     64 spin-orbitals (the paper's 32-orbital restriction, Methods section);
+ *     determinant key is the Jordan-Wigner qubit of spin-orbital p; a key is
+ *     one 64-bit word up to 64 spin-orbitals (the paper's 32-orbital
+ *     restriction, Methods section) and two words, low word first, up to 128
+ *     (the larger spaces the paper's Conclusion points to);
  *   - the reference |Psi_0> occupies spatial orbitals 0..n_alpha-1 (alpha)
  *     and 0..n_beta-1 (beta);
  *   - excitation row k = (i, j, a, b) is tau_k = a+_a a+_b a_j a_i; a single
@@ -151,7 +153,7 @@ typedef struct {
 
 /* Create a context: validate and upload the problem (h, g, the factor table
  * with host-evaluated cos/sin).  The stream is stored and used by every later
- * call on this context.  Returns UCC_EINVAL for n_spatial > 32 or < 1,
+ * call on this context.  Returns UCC_EINVAL for n_spatial > 64 or < 1,
  * electron counts out of range, a malformed or spin-violating excitation row,
  * or a NaN/inf theta. */
 ucc_status ucc_create(const ucc_hamiltonian* ham, const ucc_ansatz* ansatz, void* cuda_stream, ucc_ctx** out);
@@ -182,10 +184,11 @@ ucc_status ucc_energy(ucc_ctx* ctx, double* E, double* norm2);
 ucc_status ucc_gradient(ucc_ctx* ctx, double eps, double* E, double* grad, int on_device);
 
 /* Copy the live determinants of the held state (unordered) into caller
- * buffers of capacity cap: keys, amps, and optionally sigma = P_S H psi from
- * the last energy evaluation (NULL to skip).  Host or device pointers
- * (on_device).  *n receives the count; UCC_ECAPACITY (and *n set) if cap is
- * too small.  Synchronises. */
+ * buffers of capacity cap: keys (one uint64 per determinant up to 64
+ * spin-orbitals, two -- low word first -- above, so 2*cap words), amps, and
+ * optionally sigma = P_S H psi from the last energy evaluation (NULL to
+ * skip).  Host or device pointers (on_device).  *n receives the count;
+ * UCC_ECAPACITY (and *n set) if cap is too small.  Synchronises. */
 ucc_status ucc_get_wavefunction(ucc_ctx* ctx, size_t cap, size_t* n, uint64_t* keys, double* amps, double* sigma,
                                 int on_device);
 
@@ -202,8 +205,9 @@ ucc_status ucc_get_stats(const ucc_ctx* ctx, ucc_stats* out);
 /* Energies and gradients of n_jobs independent contexts (molecules or theta
  * vectors of uneven size): E[j] and grads[j][0..n_exc_j) (host pointers;
  * grads may be NULL for energy only).  Every job whose table can be sized up
- * front (three times its determinant sector, or four times its n_max when its
- * Methods-section cut can fire; at most 2^26 entries) runs in one cooperative
+ * front (three times its determinant sector, or three times its n_max when
+ * its Methods-section cut can fire; at most 2^22 entries; keys of one word)
+ * runs in one cooperative
  * persistent launch per pass (forward, energy, reverse) inside a captured CUDA
  * graph: each step applies one factor of every job, and each job's cut and
  * compactions run on the device.  The forward launch is repeated only when

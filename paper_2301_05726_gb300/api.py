@@ -40,6 +40,7 @@ class UCCContext:
         self.lib = _lib.load()
         self.prob = prob
         self.K = int(prob.exc.shape[0])
+        self.key_words = 2 if 2 * int(prob.n_spatial) > 64 else 1  # uint64 words per determinant key
         self._h = np.ascontiguousarray(prob.h, dtype=np.float64)
         self._g = np.ascontiguousarray(prob.g, dtype=np.float64)
         self._exc = np.ascontiguousarray(prob.exc, dtype=np.int32).reshape(-1)
@@ -114,19 +115,24 @@ class UCCContext:
         return E.value, g
 
     def wavefunction(self, with_sigma=False):
-        """(keys, amps[, sigma]) of the held state, sorted by key (host)."""
+        """(keys, amps[, sigma]) of the held state, sorted by key (host).  Above
+        64 spin-orbitals keys is an (n, 2) array of (low, high) words."""
         n = ctypes.c_size_t()
         st = self.lib.ucc_get_wavefunction(self.handle, 0, ctypes.byref(n), None, None, None, 0)
         if st not in (_lib.UCC_OK, _lib.UCC_ECAPACITY):
             check(st)
         cap = n.value
-        keys = np.zeros(cap, dtype=np.uint64)
+        keys = np.zeros(cap * self.key_words, dtype=np.uint64)
         amps = np.zeros(cap, dtype=np.float64)
         sig = np.zeros(cap, dtype=np.float64) if with_sigma else None
         check(self.lib.ucc_get_wavefunction(self.handle, cap, ctypes.byref(n), keys.ctypes.data_as(ctypes.c_void_p),
                                             amps.ctypes.data_as(ctypes.c_void_p),
                                             sig.ctypes.data_as(ctypes.c_void_p) if with_sigma else None, 0))
-        order = np.argsort(keys, kind="stable")
+        if self.key_words == 2:
+            keys = keys.reshape(cap, 2)
+            order = np.lexsort((keys[:, 0], keys[:, 1]))
+        else:
+            order = np.argsort(keys, kind="stable")
         if with_sigma:
             return keys[order], amps[order], sig[order]
         return keys[order], amps[order]

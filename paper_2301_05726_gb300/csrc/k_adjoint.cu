@@ -27,13 +27,14 @@ constexpr unsigned long long kBulkRecords = 1024;
 
 // Re-insert the entries factor k dropped, with their values just before the
 // drop, a zero adjoint, and their original birth factor.
-__global__ void __launch_bounds__(kThreads) k_tape_reinsert(Table t, Tape tape, int k) {
+template <class KT>
+__global__ void __launch_bounds__(kThreads) k_tape_reinsert(TableT<KT> t, TapeT<KT> tape, int k) {
   const unsigned long long hi = min(tape.off[k + 1], tape.cap);
   const unsigned long long lo = min(tape.off[k], hi);
   const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
   for (unsigned long long x = lo + (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; x < hi; x += stride) {
-    const TapeRec rec = tape_at(tape, x);
-    const unsigned long long key = rec.key;
+    const TapeRecT<KT> rec = tape_at(tape, x);
+    const KT key = rec.key;
     const double val = rec.val;
     const unsigned int born = rec.born;
     Lookup r = find1(t, key, 0u);
@@ -58,11 +59,13 @@ __global__ void __launch_bounds__(kThreads) k_tape_reinsert(Table t, Tape tape, 
 // slot, one reservation per warp and round; k_link_tail then hashes the
 // appended range.  This replaces a per-record chain of filter load, slot
 // claim and tail reservation.
-__global__ void k_mark_tail(Table t) {
+template <class KT>
+__global__ void k_mark_tail(TableT<KT> t) {
   if (threadIdx.x == 0) t.cnt->link_from = *((volatile unsigned long long*)&t.cnt->n_tail);
 }
 
-__global__ void __launch_bounds__(kThreads) k_tape_append(Table t, Tape tape, int k) {
+template <class KT>
+__global__ void __launch_bounds__(kThreads) k_tape_append(TableT<KT> t, TapeT<KT> tape, int k) {
   const unsigned long long hi = min(tape.off[k + 1], tape.cap);
   const unsigned long long lo = min(tape.off[k], hi);
   const unsigned int lane = threadIdx.x & 31u;
@@ -71,7 +74,7 @@ __global__ void __launch_bounds__(kThreads) k_tape_append(Table t, Tape tape, in
   const unsigned long long nwarps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
   unsigned long long revived = 0;
   for (unsigned long long base = lo + warp * 128ull; base < hi; base += nwarps * 128ull) {  // warp-uniform
-    TapeRec rec[4];
+    TapeRecT<KT> rec[4];
     bool add[4], maybe[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -128,7 +131,8 @@ __global__ void __launch_bounds__(kThreads) k_tape_append(Table t, Tape tape, in
 }
 
 // Hash slots for the entries appended since k_mark_tail.
-__global__ void __launch_bounds__(kThreads) k_link_tail(Table t) {
+template <class KT>
+__global__ void __launch_bounds__(kThreads) k_link_tail(TableT<KT> t) {
   const unsigned long long lo = *((volatile unsigned long long*)&t.cnt->link_from);
   const unsigned long long hi = min(*((volatile unsigned long long*)&t.cnt->n_tail), t.cap_n);
   const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
@@ -136,22 +140,22 @@ __global__ void __launch_bounds__(kThreads) k_link_tail(Table t) {
     link_appended(t, t.keys[j], j);
 }
 
-template <int G>
-__global__ void __launch_bounds__(kStepThreads, 8) k_reverse(Table t, const Factor* __restrict__ factors, int k,
-                                                             unsigned int stamp, double* grad) {
+template <class KT, int G>
+__global__ void __launch_bounds__(kStepThreads, 8) k_reverse(TableT<KT> t, const FactorT<KT>* __restrict__ factors,
+                                                             int k, unsigned int stamp, double* grad) {
   // The adjoint of a linked entry is loaded with its partner's filter word
   // (staging it with every scanned entry costs more than it saves).
-  __shared__ LinkScratch s_w[kStepThreads / 32];
-  const Factor f = factors[k];
+  __shared__ LinkScratch<KT> s_w[kStepThreads / 32];
+  const FactorT<KT> f = factors[k];
   const unsigned long long n = min(*((volatile unsigned long long*)&t.cnt->n_tail), t.cap_n);
   double acc = 0.0;
   unsigned int pairs = 0, kills = 0;
   for_each_linked<false>(
       t, f, n, s_w[threadIdx.x >> 5], nullptr, [&](unsigned long long i, bool act) { return act ? t.lam[i] : 0.0; },
-      [&](unsigned long long i, unsigned long long X, double cX, bool ex, double mu, bool act) {
+      [&](unsigned long long i, KT X, double cX, bool ex, double mu, bool act) {
         if (act) reverse_resolve(t, f, k, stamp, i, X, cX, mu, ex, absent_lookup(), acc, pairs, kills);
       },
-      [&](unsigned long long i, unsigned long long X, double cX, bool ex, double, bool act) {
+      [&](unsigned long long i, KT X, double cX, bool ex, double, bool act) {
         const double mu = act ? t.lam[i] : 0.0;
         Lookup r = findG<G>(t, X ^ (f.occ | f.vir), act, stamp);
         if (act) reverse_resolve(t, f, k, stamp, i, X, cX, mu, ex, r, acc, pairs, kills);
@@ -184,38 +188,52 @@ __global__ void __launch_bounds__(kStepThreads, 8) k_reverse(Table t, const Fact
 
 }  // namespace
 
-cudaError_t launch_tape_reinsert(const Table& t, const Tape& tape, int k, unsigned long long records, int grid,
-                                 cudaStream_t st, long long* launches) {
+template <class KT>
+cudaError_t launch_tape_reinsert(const TableT<KT>& t, const TapeT<KT>& tape, int k, unsigned long long records,
+                                 int grid, cudaStream_t st, long long* launches) {
   if (records < kBulkRecords) {
-    k_tape_reinsert<<<grid, kThreads, 0, st>>>(t, tape, k);
+    k_tape_reinsert<KT><<<grid, kThreads, 0, st>>>(t, tape, k);
     *launches += 1;
   } else {
-    k_mark_tail<<<1, 32, 0, st>>>(t);
-    k_tape_append<<<grid, kThreads, 0, st>>>(t, tape, k);
-    k_link_tail<<<grid, kThreads, 0, st>>>(t);
+    k_mark_tail<KT><<<1, 32, 0, st>>>(t);
+    k_tape_append<KT><<<grid, kThreads, 0, st>>>(t, tape, k);
+    k_link_tail<KT><<<grid, kThreads, 0, st>>>(t);
     *launches += 3;
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_reverse(const Table& t, const Factor* factors, int k, unsigned int stamp, double* grad,
+template <class KT>
+cudaError_t launch_reverse(const TableT<KT>& t, const FactorT<KT>* factors, int k, unsigned int stamp, double* grad,
                            int probe_width, int grid, cudaStream_t st) {
   if (!scan_aligned(t)) return cudaErrorMisalignedAddress;
   switch (probe_width) {
     case 2:
-      k_reverse<2><<<one_wave<k_reverse<2>, kStepThreads>(grid), kStepThreads, 0, st>>>(t, factors, k, stamp, grad);
+      k_reverse<KT, 2><<<one_wave<k_reverse<KT, 2>, kStepThreads>(grid), kStepThreads, 0, st>>>(t, factors, k, stamp,
+                                                                                                 grad);
       break;
     case 4:
-      k_reverse<4><<<one_wave<k_reverse<4>, kStepThreads>(grid), kStepThreads, 0, st>>>(t, factors, k, stamp, grad);
+      k_reverse<KT, 4><<<one_wave<k_reverse<KT, 4>, kStepThreads>(grid), kStepThreads, 0, st>>>(t, factors, k, stamp,
+                                                                                                 grad);
       break;
     case 8:
-      k_reverse<8><<<one_wave<k_reverse<8>, kStepThreads>(grid), kStepThreads, 0, st>>>(t, factors, k, stamp, grad);
+      k_reverse<KT, 8><<<one_wave<k_reverse<KT, 8>, kStepThreads>(grid), kStepThreads, 0, st>>>(t, factors, k, stamp,
+                                                                                                 grad);
       break;
     default:
-      k_reverse<1><<<one_wave<k_reverse<1>, kStepThreads>(grid), kStepThreads, 0, st>>>(t, factors, k, stamp, grad);
+      k_reverse<KT, 1><<<one_wave<k_reverse<KT, 1>, kStepThreads>(grid), kStepThreads, 0, st>>>(t, factors, k, stamp,
+                                                                                                 grad);
       break;
   }
   return cudaGetLastError();
 }
+
+#define UCC_ADJOINT_INSTANTIATE(KT)                                                                               \
+  template cudaError_t launch_tape_reinsert<KT>(const TableT<KT>&, const TapeT<KT>&, int, unsigned long long, int, \
+                                                cudaStream_t, long long*);                                       \
+  template cudaError_t launch_reverse<KT>(const TableT<KT>&, const FactorT<KT>*, int, unsigned int, double*, int,  \
+                                          int, cudaStream_t);
+UCC_ADJOINT_INSTANTIATE(unsigned long long)
+UCC_ADJOINT_INSTANTIATE(Key128)
 
 }  // namespace ucc

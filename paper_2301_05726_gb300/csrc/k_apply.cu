@@ -44,25 +44,25 @@ __device__ __forceinline__ void block_add_counts(Counters* c, unsigned long long
 // start of the step, otherwise by the thread of D.  Entries dropped during
 // this step carry this step's stamp, so a D-thread can tell "E was live when
 // the step began" (live or DEAD_NOW) from "E absent" (ABSENT or DEAD_OLD).
-template <int G, bool RECORD>
-__global__ void __launch_bounds__(kStepThreads, 8) k_forward(Table t, const Factor* __restrict__ factors, int k,
-                                                             double eps, unsigned int stamp, Tape tape,
+template <class KT, int G, bool RECORD>
+__global__ void __launch_bounds__(kStepThreads, 8) k_forward(TableT<KT> t, const FactorT<KT>* __restrict__ factors,
+                                                             int k, double eps, unsigned int stamp, TapeT<KT> tape,
                                                              unsigned long long n_max) {
   __shared__ int s_skip;
-  __shared__ LinkScratch s_w[kStepThreads / 32];
+  __shared__ LinkScratch<KT> s_w[kStepThreads / 32];
   if (threadIdx.x == 0) s_skip = *((volatile int*)&t.cnt->stop_k) >= 0;
   __syncthreads();
   const bool skip = s_skip != 0;
   StepCounts sc;
   if (!skip) {
-    const Factor f = factors[k];
+    const FactorT<KT> f = factors[k];
     const unsigned long long n = min(*((volatile unsigned long long*)&t.cnt->n_scan), t.cap_n);
     for_each_linked<false>(
         t, f, n, s_w[threadIdx.x >> 5], nullptr, [](unsigned long long, bool) { return 0.0; },
-        [&](unsigned long long i, unsigned long long X, double cX, bool ex, double, bool act) {
+        [&](unsigned long long i, KT X, double cX, bool ex, double, bool act) {
           if (act) forward_resolve<RECORD, true>(t, f, k, eps, stamp, tape, i, X, cX, ex, absent_lookup(), sc);
         },
-        [&](unsigned long long i, unsigned long long X, double cX, bool ex, double, bool act) {
+        [&](unsigned long long i, KT X, double cX, bool ex, double, bool act) {
           Lookup r = findG<G>(t, X ^ (f.occ | f.vir), act, stamp);
           if (act) forward_resolve<RECORD, true>(t, f, k, eps, stamp, tape, i, X, cX, ex, r, sc);
         });
@@ -111,7 +111,8 @@ __global__ void __launch_bounds__(kStepThreads, 8) k_forward(Table t, const Fact
 
 // Hash slots for the entries factor k's step appended (k_forward defers
 // them); skipped with the step itself when an earlier factor stopped the chunk.
-__global__ void __launch_bounds__(kThreads) k_link(Table t, int k) {
+template <class KT>
+__global__ void __launch_bounds__(kThreads) k_link(TableT<KT> t, int k) {
   const int stop = *((volatile int*)&t.cnt->stop_k);
   if (stop >= 0 && stop <= k) return;
   const unsigned long long lo = *((volatile unsigned long long*)&t.cnt->link_from);
@@ -125,7 +126,8 @@ __global__ void __launch_bounds__(kThreads) k_link(Table t, int k) {
 // with_born: 0 keys and amplitudes, 1 also born, 2 also born and lam.
 // Each warp takes four tiles of 32 entries per round: their amplitudes are
 // loaded together and one reservation per round places the live ones.
-__global__ void __launch_bounds__(kThreads) k_compact(Table from, Table to, int with_born) {
+template <class KT>
+__global__ void __launch_bounds__(kThreads) k_compact(TableT<KT> from, TableT<KT> to, int with_born) {
   const unsigned long long n = min(*((volatile unsigned long long*)&from.cnt->n_tail), from.cap_n);
   const unsigned int lane = threadIdx.x & 31u;
   const unsigned int below_me = (1u << lane) - 1u;
@@ -174,30 +176,33 @@ __global__ void __launch_bounds__(kThreads) k_compact(Table from, Table to, int 
 // Four entries per thread and round: their keys are loaded and their home
 // slots claimed together (the home slot is usually free), and only the
 // entries whose home slot was taken probe on.
-__global__ void __launch_bounds__(kThreads) k_rehash(Table t) {
+template <class KT>
+__global__ void __launch_bounds__(kThreads) k_rehash(TableT<KT> t) {
+  using K = KeyOps<KT>;
   const unsigned long long n = min(*((volatile unsigned long long*)&t.cnt->new_n), t.cap_n);
   const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
   for (unsigned long long i0 = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += 4 * stride) {
-    unsigned long long key[4], h[4], prev[4];
+    KT key[4], prev[4];
+    unsigned long long h[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const unsigned long long i = i0 + u * stride;
-      key[u] = i < n ? t.keys[i] : 0ull;
+      key[u] = i < n ? t.keys[i] : K::zero();
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       h[u] = home_slot(t, key[u]);
-      prev[u] = key[u] ? atomicCAS(&t.slots[h[u]].key, 0ull, key[u]) : 1ull;
+      prev[u] = !K::is_zero(key[u]) ? key_cas(&t.slots[h[u]].key, K::zero(), key[u]) : K::bit(0);
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      if (!key[u]) continue;
+      if (K::is_zero(key[u])) continue;
       const unsigned long long i = i0 + u * stride;
       unsigned long long s = h[u];
-      if (prev[u] == 0ull) {
+      if (K::is_zero(prev[u])) {
         filter_add(t, key[u]);
       } else {
-        if (prev[u] == key[u]) raise_consistency(t.cnt, SITE_REHASH_DUP);
+        if (prev[u] == key[u]) raise_consistency(t.cnt, SITE_REHASH_DUP, K::lo(key[u]));
         s = claim_slot(t, key[u], h[u] + 1);
       }
       if (s != ~0ull) t.slots[s].idx = i;
@@ -205,7 +210,8 @@ __global__ void __launch_bounds__(kThreads) k_rehash(Table t) {
   }
 }
 
-__global__ void k_finish_rebuild(Table t) {
+template <class KT>
+__global__ void k_finish_rebuild(TableT<KT> t) {
   Counters* c = t.cnt;
   const unsigned long long n = min(*((volatile unsigned long long*)&c->new_n), t.cap_n);
   c->n_tail = n;
@@ -217,8 +223,9 @@ __global__ void k_finish_rebuild(Table t) {
 }
 
 // Gather live entries into caller buffers (unordered).
-__global__ void __launch_bounds__(kThreads) k_export(Table t, unsigned long long cap, unsigned long long* keys,
-                                                      double* amps, double* sigma) {
+template <class KT>
+__global__ void __launch_bounds__(kThreads) k_export(TableT<KT> t, unsigned long long cap, KT* keys, double* amps,
+                                                      double* sigma) {
   const unsigned long long n = min(*((volatile unsigned long long*)&t.cnt->n_tail), t.cap_n);
   const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
   for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
@@ -234,7 +241,8 @@ __global__ void __launch_bounds__(kThreads) k_export(Table t, unsigned long long
 }
 
 // psi = {HF: 1.0}; the slots are already zero.
-__global__ void k_reset(Table t, unsigned long long hf) {
+template <class KT>
+__global__ void k_reset(TableT<KT> t, KT hf) {
   Counters* c = t.cnt;
   t.keys[0] = hf;
   t.amps[0] = 1.0;
@@ -250,65 +258,84 @@ __global__ void k_reset(Table t, unsigned long long hf) {
 
 }  // namespace
 
-cudaError_t launch_reset(const Table& t, unsigned long long hf, cudaStream_t st) {
-  k_reset<<<1, 1, 0, st>>>(t, hf);
+template <class KT>
+cudaError_t launch_reset(const TableT<KT>& t, KT hf, cudaStream_t st) {
+  k_reset<KT><<<1, 1, 0, st>>>(t, hf);
   return cudaGetLastError();
 }
 
-template <bool RECORD>
-static cudaError_t forward_g(const Table& t, const Factor* factors, int k, double eps, unsigned int stamp,
-                             const Tape& tape, unsigned long long n_max, int pw, int grid, cudaStream_t st) {
+template <class KT, bool RECORD>
+static cudaError_t forward_g(const TableT<KT>& t, const FactorT<KT>* factors, int k, double eps, unsigned int stamp,
+                             const TapeT<KT>& tape, unsigned long long n_max, int pw, int grid, cudaStream_t st) {
   switch (pw) {
     case 2:
-      k_forward<2, RECORD><<<one_wave<k_forward<2, RECORD>, kStepThreads>(grid), kStepThreads, 0, st>>>(
+      k_forward<KT, 2, RECORD><<<one_wave<k_forward<KT, 2, RECORD>, kStepThreads>(grid), kStepThreads, 0, st>>>(
           t, factors, k, eps, stamp, tape, n_max);
       break;
     case 4:
-      k_forward<4, RECORD><<<one_wave<k_forward<4, RECORD>, kStepThreads>(grid), kStepThreads, 0, st>>>(
+      k_forward<KT, 4, RECORD><<<one_wave<k_forward<KT, 4, RECORD>, kStepThreads>(grid), kStepThreads, 0, st>>>(
           t, factors, k, eps, stamp, tape, n_max);
       break;
     case 8:
-      k_forward<8, RECORD><<<one_wave<k_forward<8, RECORD>, kStepThreads>(grid), kStepThreads, 0, st>>>(
+      k_forward<KT, 8, RECORD><<<one_wave<k_forward<KT, 8, RECORD>, kStepThreads>(grid), kStepThreads, 0, st>>>(
           t, factors, k, eps, stamp, tape, n_max);
       break;
     default:
-      k_forward<1, RECORD><<<one_wave<k_forward<1, RECORD>, kStepThreads>(grid), kStepThreads, 0, st>>>(
+      k_forward<KT, 1, RECORD><<<one_wave<k_forward<KT, 1, RECORD>, kStepThreads>(grid), kStepThreads, 0, st>>>(
           t, factors, k, eps, stamp, tape, n_max);
       break;
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_forward(const Table& t, const Factor* factors, int k, double eps, unsigned int stamp, int record,
-                           const Tape& tape, unsigned long long n_max, int probe_width, int grid, cudaStream_t st) {
+template <class KT>
+cudaError_t launch_forward(const TableT<KT>& t, const FactorT<KT>* factors, int k, double eps, unsigned int stamp,
+                           int record, const TapeT<KT>& tape, unsigned long long n_max, int probe_width, int grid,
+                           cudaStream_t st) {
   if (!scan_aligned(t)) return cudaErrorMisalignedAddress;
-  const cudaError_t e = record ? forward_g<true>(t, factors, k, eps, stamp, tape, n_max, probe_width, grid, st)
-                               : forward_g<false>(t, factors, k, eps, stamp, tape, n_max, probe_width, grid, st);
+  const cudaError_t e = record ? forward_g<KT, true>(t, factors, k, eps, stamp, tape, n_max, probe_width, grid, st)
+                               : forward_g<KT, false>(t, factors, k, eps, stamp, tape, n_max, probe_width, grid, st);
   if (e != cudaSuccess) return e;
-  k_link<<<one_wave<k_link, kThreads>(grid), kThreads, 0, st>>>(t, k);
+  k_link<KT><<<one_wave<k_link<KT>, kThreads>(grid), kThreads, 0, st>>>(t, k);
   return cudaGetLastError();
 }
 
-cudaError_t launch_compact(const Table& from, const Table& to, int with_born, int grid, cudaStream_t st) {
-  k_compact<<<grid, kThreads, 0, st>>>(from, to, with_born);
+template <class KT>
+cudaError_t launch_compact(const TableT<KT>& from, const TableT<KT>& to, int with_born, int grid, cudaStream_t st) {
+  k_compact<KT><<<grid, kThreads, 0, st>>>(from, to, with_born);
   return cudaGetLastError();
 }
 
-cudaError_t launch_rehash(const Table& t, int grid, cudaStream_t st) {
-  k_rehash<<<grid, kThreads, 0, st>>>(t);
+template <class KT>
+cudaError_t launch_rehash(const TableT<KT>& t, int grid, cudaStream_t st) {
+  k_rehash<KT><<<grid, kThreads, 0, st>>>(t);
   return cudaGetLastError();
 }
 
-cudaError_t launch_finish_rebuild(const Table& t, cudaStream_t st) {
-  k_finish_rebuild<<<1, 1, 0, st>>>(t);
+template <class KT>
+cudaError_t launch_finish_rebuild(const TableT<KT>& t, cudaStream_t st) {
+  k_finish_rebuild<KT><<<1, 1, 0, st>>>(t);
   return cudaGetLastError();
 }
 
-cudaError_t launch_export(const Table& t, unsigned long long cap, unsigned long long* keys, double* amps,
-                          double* sigma, int grid, cudaStream_t st) {
-  k_export<<<grid, kThreads, 0, st>>>(t, cap, keys, amps, sigma);
+template <class KT>
+cudaError_t launch_export(const TableT<KT>& t, unsigned long long cap, KT* keys, double* amps, double* sigma,
+                          int grid, cudaStream_t st) {
+  k_export<KT><<<grid, kThreads, 0, st>>>(t, cap, keys, amps, sigma);
   return cudaGetLastError();
 }
+
+#define UCC_APPLY_INSTANTIATE(KT)                                                                                  \
+  template cudaError_t launch_reset<KT>(const TableT<KT>&, KT, cudaStream_t);                                      \
+  template cudaError_t launch_forward<KT>(const TableT<KT>&, const FactorT<KT>*, int, double, unsigned int, int,   \
+                                          const TapeT<KT>&, unsigned long long, int, int, cudaStream_t);           \
+  template cudaError_t launch_compact<KT>(const TableT<KT>&, const TableT<KT>&, int, int, cudaStream_t);           \
+  template cudaError_t launch_rehash<KT>(const TableT<KT>&, int, cudaStream_t);                                    \
+  template cudaError_t launch_finish_rebuild<KT>(const TableT<KT>&, cudaStream_t);                                 \
+  template cudaError_t launch_export<KT>(const TableT<KT>&, unsigned long long, KT*, double*, double*, int,        \
+                                         cudaStream_t);
+UCC_APPLY_INSTANTIATE(unsigned long long)
+UCC_APPLY_INSTANTIATE(Key128)
 
 }  // namespace ucc
 
@@ -317,7 +344,8 @@ namespace ucc {
 namespace {
 
 // Load a snapshot (live keys and amplitudes, unordered) as entries [0, n).
-__global__ void __launch_bounds__(256) k_restore(Table t, const unsigned long long* keys, const double* amps,
+template <class KT>
+__global__ void __launch_bounds__(256) k_restore(TableT<KT> t, const KT* keys, const double* amps,
                                                   unsigned long long n) {
   const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
   for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n && i < t.cap_n;
@@ -339,7 +367,8 @@ __global__ void __launch_bounds__(256) k_restore(Table t, const unsigned long lo
 
 // Copy the adjoint vector of `src` onto the live entries of `dst` by key
 // (zero where src has no live entry).
-__global__ void __launch_bounds__(256) k_transfer_lambda(Table dst, Table src) {
+template <class KT>
+__global__ void __launch_bounds__(256) k_transfer_lambda(TableT<KT> dst, TableT<KT> src) {
   const unsigned long long n = min(*((volatile unsigned long long*)&dst.cnt->n_tail), dst.cap_n);
   const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
   for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
@@ -351,16 +380,26 @@ __global__ void __launch_bounds__(256) k_transfer_lambda(Table dst, Table src) {
 
 }  // namespace
 
-cudaError_t launch_restore(const Table& t, const unsigned long long* keys, const double* amps, unsigned long long n,
-                           int grid, cudaStream_t st) {
-  k_restore<<<grid, 256, 0, st>>>(t, keys, amps, n);
+template <class KT>
+cudaError_t launch_restore(const TableT<KT>& t, const KT* keys, const double* amps, unsigned long long n, int grid,
+                           cudaStream_t st) {
+  k_restore<KT><<<grid, 256, 0, st>>>(t, keys, amps, n);
   return cudaGetLastError();
 }
 
-cudaError_t launch_transfer_lambda(const Table& dst, const Table& src, int grid, cudaStream_t st) {
-  k_transfer_lambda<<<grid, 256, 0, st>>>(dst, src);
+template <class KT>
+cudaError_t launch_transfer_lambda(const TableT<KT>& dst, const TableT<KT>& src, int grid, cudaStream_t st) {
+  k_transfer_lambda<KT><<<grid, 256, 0, st>>>(dst, src);
   return cudaGetLastError();
 }
+
+template cudaError_t launch_restore<unsigned long long>(const Table&, const unsigned long long*, const double*,
+                                                        unsigned long long, int, cudaStream_t);
+template cudaError_t launch_restore<Key128>(const TableT<Key128>&, const Key128*, const double*, unsigned long long,
+                                            int, cudaStream_t);
+template cudaError_t launch_transfer_lambda<unsigned long long>(const Table&, const Table&, int, cudaStream_t);
+template cudaError_t launch_transfer_lambda<Key128>(const TableT<Key128>&, const TableT<Key128>&, int,
+                                                    cudaStream_t);
 
 }  // namespace ucc
 
@@ -370,16 +409,16 @@ namespace {
 
 // Read-only replay of factor f's partner lookups on the live table with
 // G-lane probes (the autotuner times it); the result only feeds a checksum.
-template <int G>
-__global__ void __launch_bounds__(kStepThreads) k_probe_bench(Table t, Factor f, unsigned long long* sink) {
-  __shared__ LinkScratch s_w[kStepThreads / 32];
+template <class KT, int G>
+__global__ void __launch_bounds__(kStepThreads) k_probe_bench(TableT<KT> t, FactorT<KT> f, unsigned long long* sink) {
+  __shared__ LinkScratch<KT> s_w[kStepThreads / 32];
   const unsigned long long n = min(*((volatile unsigned long long*)&t.cnt->n_tail), t.cap_n);
-  const unsigned long long m = f.occ | f.vir;
+  const KT m = f.occ | f.vir;
   unsigned long long acc = 0;
   for_each_linked<false>(
       t, f, n, s_w[threadIdx.x >> 5], nullptr, [](unsigned long long, bool) { return 0.0; },
-      [&](unsigned long long, unsigned long long, double, bool, double, bool) {},
-      [&](unsigned long long, unsigned long long X, double, bool, double, bool act) {
+      [&](unsigned long long, KT, double, bool, double, bool) {},
+      [&](unsigned long long, KT X, double, bool, double, bool act) {
         Lookup r = findG<G>(t, X ^ m, act, 0u);
         if (act) acc += r.idx + (unsigned long long)r.state;
       });
@@ -389,24 +428,30 @@ __global__ void __launch_bounds__(kStepThreads) k_probe_bench(Table t, Factor f,
 
 }  // namespace
 
-cudaError_t launch_probe_bench(const Table& t, const Factor& f, int probe_width, unsigned long long* sink, int grid,
-                               cudaStream_t st) {
+template <class KT>
+cudaError_t launch_probe_bench(const TableT<KT>& t, const FactorT<KT>& f, int probe_width, unsigned long long* sink,
+                               int grid, cudaStream_t st) {
   if (!scan_aligned(t)) return cudaErrorMisalignedAddress;
   switch (probe_width) {
     case 2:
-      k_probe_bench<2><<<grid, kStepThreads, 0, st>>>(t, f, sink);
+      k_probe_bench<KT, 2><<<grid, kStepThreads, 0, st>>>(t, f, sink);
       break;
     case 4:
-      k_probe_bench<4><<<grid, kStepThreads, 0, st>>>(t, f, sink);
+      k_probe_bench<KT, 4><<<grid, kStepThreads, 0, st>>>(t, f, sink);
       break;
     case 8:
-      k_probe_bench<8><<<grid, kStepThreads, 0, st>>>(t, f, sink);
+      k_probe_bench<KT, 8><<<grid, kStepThreads, 0, st>>>(t, f, sink);
       break;
     default:
-      k_probe_bench<1><<<grid, kStepThreads, 0, st>>>(t, f, sink);
+      k_probe_bench<KT, 1><<<grid, kStepThreads, 0, st>>>(t, f, sink);
       break;
   }
   return cudaGetLastError();
 }
+
+template cudaError_t launch_probe_bench<unsigned long long>(const Table&, const Factor&, int, unsigned long long*, int,
+                                                            cudaStream_t);
+template cudaError_t launch_probe_bench<Key128>(const TableT<Key128>&, const FactorT<Key128>&, int,
+                                                unsigned long long*, int, cudaStream_t);
 
 }  // namespace ucc

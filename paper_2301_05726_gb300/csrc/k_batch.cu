@@ -78,11 +78,11 @@ __global__ void __launch_bounds__(kThreads) k_sigma_zero_batch(const JobView* jo
 __global__ void __launch_bounds__(kSigmaWarps * 32) k_sigma_batch(const JobView* jobs, JobState* js,
                                                                    int n_jobs, BatchHeader* bh) {
   __shared__ unsigned long long s_base[kMaxBatchJobs + 1];
-  __shared__ LowerLists lists[kSigmaWarps];
+  __shared__ LowerLists<unsigned long long> lists[kSigmaWarps];
   load_bases(js, n_jobs, bh, s_base);
   const unsigned long long total = s_base[n_jobs];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  LowerLists& L = lists[w];
+  LowerLists<unsigned long long>& L = lists[w];
   const unsigned long long gw = (unsigned long long)blockIdx.x * kSigmaWarps + w;
   const unsigned long long nw = (unsigned long long)gridDim.x * kSigmaWarps;
   int cur = -1;

@@ -21,21 +21,28 @@ namespace ucc {
 
 namespace {
 
-constexpr int kWarps = 8;
-constexpr int kThreads = kWarps * 32;
+// Warps per block of the energy kernel: the warps' connection lists fill the
+// static shared memory (two-word keys have four times the pair lists).
+template <class KT>
+__host__ __device__ constexpr int sigma_warps() {
+  return sizeof(KT) == 8 ? 8 : 2;
+}
 // sigma[0, n_tail) = 0 before the lower-triangle pass accumulates into it.
-__global__ void __launch_bounds__(256) k_sigma_zero(Table t) {
+template <class KT>
+__global__ void __launch_bounds__(256) k_sigma_zero(TableT<KT> t) {
   const unsigned long long n = min(*((volatile unsigned long long*)&t.cnt->n_tail), t.cap_n);
   const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
   for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
     t.sigma[i] = 0.0;
 }
 
-__global__ void __launch_bounds__(kThreads, 4) k_sigma(Table t, Integrals in) {
-  __shared__ LowerLists lists[kWarps];
+template <class KT>
+__global__ void __launch_bounds__(sigma_warps<KT>() * 32) k_sigma(TableT<KT> t, Integrals in) {
+  constexpr int kWarps = sigma_warps<KT>();
+  __shared__ LowerLists<KT> lists[kWarps];
   const int w = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
-  LowerLists& L = lists[w];
+  LowerLists<KT>& L = lists[w];
   const unsigned long long n = min(*((volatile unsigned long long*)&t.cnt->n_tail), t.cap_n);
   const unsigned long long gw = (unsigned long long)blockIdx.x * kWarps + w;
   const unsigned long long nw = (unsigned long long)gridDim.x * kWarps;
@@ -44,7 +51,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_sigma(Table t, Integrals in) {
   for (unsigned long long e = gw; e < n; e += nw) {
     const double cI = t.amps[e];
     if (is_dead(cI)) continue;  // warp-uniform
-    const unsigned long long I = t.keys[e];
+    const KT I = t.keys[e];
     double d;
     double part = sigma_lower(t, in, L, I, cI, lane, d, probes, hits);
     d = warp_sum(d);
@@ -93,7 +100,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_sigma(Table t, Integrals in) {
 }
 
 // mu_K = (sigma - E psi) / <psi|psi> on the live entries; 0 on dropped ones.
-__global__ void __launch_bounds__(256) k_lambda_init(Table t) {
+template <class KT>
+__global__ void __launch_bounds__(256) k_lambda_init(TableT<KT> t) {
   const unsigned long long n = min(*((volatile unsigned long long*)&t.cnt->n_tail), t.cap_n);
   const double norm2 = *((volatile double*)&t.cnt->norm2);
   const double E = *((volatile double*)&t.cnt->e_num) / norm2;
@@ -106,17 +114,22 @@ __global__ void __launch_bounds__(256) k_lambda_init(Table t) {
 
 }  // namespace
 
-int sigma_smem_bytes(int) { return (int)sizeof(LowerLists) * kWarps; }
-
-cudaError_t launch_sigma(const Table& t, const Integrals& in, int grid, cudaStream_t st) {
-  k_sigma_zero<<<grid, 256, 0, st>>>(t);
-  k_sigma<<<grid, kThreads, 0, st>>>(t, in);
+template <class KT>
+cudaError_t launch_sigma(const TableT<KT>& t, const Integrals& in, int grid, cudaStream_t st) {
+  k_sigma_zero<KT><<<grid, 256, 0, st>>>(t);
+  k_sigma<KT><<<grid, sigma_warps<KT>() * 32, 0, st>>>(t, in);
   return cudaGetLastError();
 }
 
-cudaError_t launch_lambda_init(const Table& t, int grid, cudaStream_t st) {
-  k_lambda_init<<<grid, 256, 0, st>>>(t);
+template <class KT>
+cudaError_t launch_lambda_init(const TableT<KT>& t, int grid, cudaStream_t st) {
+  k_lambda_init<KT><<<grid, 256, 0, st>>>(t);
   return cudaGetLastError();
 }
+
+template cudaError_t launch_sigma<unsigned long long>(const Table&, const Integrals&, int, cudaStream_t);
+template cudaError_t launch_sigma<Key128>(const TableT<Key128>&, const Integrals&, int, cudaStream_t);
+template cudaError_t launch_lambda_init<unsigned long long>(const Table&, int, cudaStream_t);
+template cudaError_t launch_lambda_init<Key128>(const TableT<Key128>&, int, cudaStream_t);
 
 }  // namespace ucc

@@ -350,44 +350,57 @@ __device__ void block_rebuild(JobView* jobs, int j, const Table& t, unsigned lon
     s_tape = record ? ldv(&t.cnt->tape_n) : 0ull;
   }
   __syncthreads();
-  for (unsigned long long base = 0; base < nt; base += blockDim.x) {
-    const unsigned long long i = base + threadIdx.x;
+  // Four entries per thread and round (one prefix over the block per round):
+  // entry base + u * blockDim.x + threadIdx.x for u < 4.
+  constexpr int kPer = 4;
+  for (unsigned long long base = 0; base < nt; base += kPer * (unsigned long long)blockDim.x) {
     unsigned int kp = 0, dp = 0;
-    double a = 0.0;
-    unsigned long long key = 0;
-    if (i < nt) {
-      a = t.amps[i];
-      if (!is_dead(a)) {
-        key = t.keys[i];
-        if (keep(a, key))
-          kp = 1;
-        else
-          dp = 1;
+    double a[kPer];
+    unsigned long long key[kPer];
+    int st[kPer];  // 0 none, 1 keep, 2 drop
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+      const unsigned long long i = base + (unsigned long long)u * blockDim.x + threadIdx.x;
+      st[u] = 0;
+      a[u] = 0.0;
+      key[u] = 0ull;
+      if (i < nt) {
+        a[u] = t.amps[i];
+        if (!is_dead(a[u])) {
+          key[u] = t.keys[i];
+          st[u] = keep(a[u], key[u]) ? 1 : 2;
+          kp += st[u] == 1;
+          dp += st[u] == 2;
+        }
       }
     }
     unsigned int tk, td;
-    const unsigned int pk = block_prefix(kp, &tk);
-    const unsigned int pd = block_prefix(dp, &td);
-    if (kp) {
-      const unsigned long long at = s_kept + pk;
-      if (at < t.cap_n) {
-        sp.keys[at] = key;
-        sp.amps[at] = a;
-        sp.born[at] = t.born[i];
-        if (with_lam) sp.lam[at] = t.lam[i];
-      } else {
-        raise_error(t.cnt, ERR_CAPACITY);
-      }
-    }
-    if (dp && record) {
-      const unsigned long long at = s_tape + pd;
-      if (at < jv.tape.cap) {
-        TapeRec& rec = tape_at(jv.tape, at);
-        rec.key = key;
-        rec.val = a;
-        rec.born = t.born[i];
-      } else {
-        raise_error(t.cnt, ERR_TAPE_FULL);
+    unsigned int pk = block_prefix(kp, &tk);
+    unsigned int pd = block_prefix(dp, &td);
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+      if (st[u] == 0) continue;
+      const unsigned long long i = base + (unsigned long long)u * blockDim.x + threadIdx.x;
+      if (st[u] == 1) {
+        const unsigned long long at = s_kept + pk++;
+        if (at < t.cap_n) {
+          sp.keys[at] = key[u];
+          sp.amps[at] = a[u];
+          sp.born[at] = t.born[i];
+          if (with_lam) sp.lam[at] = t.lam[i];
+        } else {
+          raise_error(t.cnt, ERR_CAPACITY);
+        }
+      } else if (record) {
+        const unsigned long long at = s_tape + pd++;
+        if (at < jv.tape.cap) {
+          TapeRec& rec = tape_at(jv.tape, at);
+          rec.key = key[u];
+          rec.val = a[u];
+          rec.born = t.born[i];
+        } else {
+          raise_error(t.cnt, ERR_TAPE_FULL);
+        }
       }
     }
     __syncthreads();
@@ -400,11 +413,10 @@ __device__ void block_rebuild(JobView* jobs, int j, const Table& t, unsigned lon
   }
   // clear the spare slots and filter, then hash the kept entries into them
   const unsigned long long ns = t.slot_mask + 1ull;
-  for (unsigned long long x = threadIdx.x; x < ns; x += blockDim.x) {
-    sp.slots[x].key = 0ull;
-    sp.slots[x].idx = 0ull;
-  }
-  for (unsigned long long x = threadIdx.x; x < ns / 4; x += blockDim.x) sp.filt[x] = 0u;
+  uint4* const slot16 = reinterpret_cast<uint4*>(sp.slots);  // one 16-byte store per slot
+  for (unsigned long long x = threadIdx.x; x < ns; x += blockDim.x) slot16[x] = make_uint4(0u, 0u, 0u, 0u);
+  uint4* const filt16 = reinterpret_cast<uint4*>(sp.filt);  // four filter words per store (ns / 4 is a multiple of 4)
+  for (unsigned long long x = threadIdx.x; x < ns / 16; x += blockDim.x) filt16[x] = make_uint4(0u, 0u, 0u, 0u);
   __syncthreads();
   Table tt = t;
   tt.keys = sp.keys;
@@ -525,7 +537,10 @@ __global__ void __launch_bounds__(kPThreads) k_persist_forward(JobView* jobs, Jo
           js[j].cut += (long long)s_drop;
           if (RECORD) jv.tape.off[k + 1] = ldv(&c->tape_n);
         }
-      } else if (s_dead > 1024 && 4ull * s_dead > nt) {
+      } else if (s_dead > 0 &&
+                 (4ull * s_dead > nt || 2ull * nt > t.cap_n || 8ull * nt > 3ull * (t.slot_mask + 1ull))) {
+        // compact when a quarter of the stored entries are dropped ones, or
+        // when the next step would not have room
         block_rebuild(
             jobs, j, t, nt, [](double, unsigned long long) { return true; }, false, false, k, &s_kept, &s_drop);
       }

@@ -51,7 +51,8 @@ __device__ __forceinline__ unsigned long long high_mask(int pass) {
 // threshold, NT threads of one block: phase 0 walks bins from the top (largest
 // |c| first), phase 1 from the bottom (smallest key first).
 template <int NT, class H>
-__device__ void pick_bin(SelectState* sel, int phase, int pass, int nbins, H hist_at) {
+__device__ void pick_bin(SelectState* sel, int phase, int pass, int nbins, H hist_at,
+                         unsigned long long* key_word = nullptr) {
   __shared__ unsigned long long s_scan[NT];
   const int per = (nbins + NT - 1) / NT;
   unsigned long long local = 0;
@@ -92,7 +93,7 @@ __device__ void pick_bin(SelectState* sel, int phase, int pass, int nbins, H his
             sel->key_target = rest;
           }
         } else {
-          sel->key_prefix |= (unsigned long long)b << shift;
+          *(key_word ? key_word : &sel->key_prefix) |= (unsigned long long)b << shift;
           sel->key_target = rest;
         }
         break;
@@ -106,7 +107,8 @@ __device__ void pick_bin(SelectState* sel, int phase, int pass, int nbins, H his
 // One of the two full-table radix passes over |c| (pass 0: bits 63..53, pass
 // 1: bits 52..42), restricted to live entries whose fixed digits match, then
 // the pick in the last block.
-__global__ void __launch_bounds__(kThreads) k_select_pass(Table t, SelectState* sel, int pass) {
+template <class KT>
+__global__ void __launch_bounds__(kThreads) k_select_pass(TableT<KT> t, SelectState* sel, int pass) {
   __shared__ unsigned int h[kBins];
   const int top = 64 - kDigit * pass;
   const int nbins = 1 << (top - digit_shift(pass));
@@ -134,7 +136,8 @@ __global__ void __launch_bounds__(kThreads) k_select_pass(Table t, SelectState* 
 }
 
 // The live entries whose top 22 bits of |c| equal the threshold's so far.
-__global__ void __launch_bounds__(kThreads) k_select_gather(Table t, SelectState* sel, SelectCand* cand) {
+template <class KT>
+__global__ void __launch_bounds__(kThreads) k_select_gather(TableT<KT> t, SelectState* sel, SelectCandT<KT>* cand) {
   const unsigned long long n = min(*((volatile unsigned long long*)&t.cnt->n_tail), t.cap_n);
   const unsigned long long hm = high_mask(2);
   const unsigned long long T = sel->prefix & hm;
@@ -155,16 +158,20 @@ __global__ void __launch_bounds__(kThreads) k_select_gather(Table t, SelectState
 constexpr int kFinishThreads = 1024;
 
 // The remaining digits of |c| (passes 2..5) and, when several entries share
-// the threshold value, of the key (passes 0..5), by one block over the
-// candidate buffer (or over the table when the buffer overflowed).
-__global__ void __launch_bounds__(kFinishThreads) k_select_finish(Table t, SelectState* sel,
-                                                                  const SelectCand* cand) {
+// the threshold value, of the key (its high word first for two-word keys,
+// each word in passes 0..5), by one block over the candidate buffer (or over
+// the table when the buffer overflowed).
+template <class KT>
+__global__ void __launch_bounds__(kFinishThreads) k_select_finish(TableT<KT> t, SelectState* sel,
+                                                                  const SelectCandT<KT>* cand) {
+  using K = KeyOps<KT>;
   __shared__ unsigned int h[kBins];
+  __shared__ unsigned long long s_mhi, s_mlo;  // key bits fixed so far (masks), high and low word
   const unsigned long long nc = sel->n_cand;
   const bool from_cand = nc <= kSelectCandCap;
   const unsigned long long n = from_cand ? nc : min(*((volatile unsigned long long*)&t.cnt->n_tail), t.cap_n);
   // entry x as (|c| bits, key), or false for a dropped table entry
-  auto entry = [&](unsigned long long x, unsigned long long& u, unsigned long long& key) {
+  auto entry = [&](unsigned long long x, unsigned long long& u, KT& key) {
     if (from_cand) {
       u = cand[x].mag;
       key = cand[x].key;
@@ -176,27 +183,60 @@ __global__ void __launch_bounds__(kFinishThreads) k_select_finish(Table t, Selec
     key = t.keys[x];
     return true;
   };
-  for (int phase = 0; phase < 2; ++phase) {
-    for (int pass = phase == 0 ? 2 : 0; pass < kPasses; ++pass) {
-      if (phase == 1 && !sel->need_keys) return;  // block-uniform
-      const int top = 64 - kDigit * pass;
-      const int nbins = 1 << (top - digit_shift(pass));
-      for (int b = threadIdx.x; b < nbins; b += blockDim.x) h[b] = 0;
-      __syncthreads();
-      const unsigned long long hm = high_mask(pass);
-      const unsigned long long T = sel->prefix, kp = sel->key_prefix;
-      for (unsigned long long x = threadIdx.x; x < n; x += blockDim.x) {
-        unsigned long long u, key;
-        if (!entry(x, u, key)) continue;
-        if (phase == 0) {
-          if ((u & hm) == (T & hm)) atomicAdd(&h[digit_of(u, pass)], 1u);
-        } else if (u == T && (key & hm) == (kp & hm)) {
-          atomicAdd(&h[digit_of(key, pass)], 1u);
-        }
-      }
-      __syncthreads();
-      pick_bin<kFinishThreads>(sel, phase, pass, nbins, [&](int b) { return (unsigned long long)h[b]; });
+  // |c| digits
+  for (int pass = 2; pass < kPasses; ++pass) {
+    const int top = 64 - kDigit * pass;
+    const int nbins = 1 << (top - digit_shift(pass));
+    for (int b = threadIdx.x; b < nbins; b += blockDim.x) h[b] = 0;
+    __syncthreads();
+    const unsigned long long hm = high_mask(pass);
+    const unsigned long long T = sel->prefix;
+    for (unsigned long long x = threadIdx.x; x < n; x += blockDim.x) {
+      unsigned long long u;
+      KT key;
+      if (!entry(x, u, key)) continue;
+      if ((u & hm) == (T & hm)) atomicAdd(&h[digit_of(u, pass)], 1u);
     }
+    __syncthreads();
+    pick_bin<kFinishThreads>(sel, 0, pass, nbins, [&](int b) { return (unsigned long long)h[b]; });
+  }
+  if (!sel->need_keys) return;  // block-uniform
+  // key digits among the entries with |c| == T, smallest key first
+  if (threadIdx.x == 0) {
+    s_mhi = 0ull;
+    s_mlo = 0ull;
+    sel->key_prefix = 0ull;
+    sel->key_prefix_hi = 0ull;
+  }
+  __syncthreads();
+  for (int wp = 0; wp < K::kWords * kPasses; ++wp) {
+    const bool hi_word = K::kWords == 2 && wp < kPasses;
+    const int pass = wp % kPasses;
+    const int top = 64 - kDigit * pass;
+    const int nbins = 1 << (top - digit_shift(pass));
+    for (int b = threadIdx.x; b < nbins; b += blockDim.x) h[b] = 0;
+    __syncthreads();
+    const unsigned long long T = sel->prefix, phi = sel->key_prefix_hi, plo = sel->key_prefix;
+    const unsigned long long mhi = s_mhi, mlo = s_mlo;
+    for (unsigned long long x = threadIdx.x; x < n; x += blockDim.x) {
+      unsigned long long u;
+      KT key;
+      if (!entry(x, u, key)) continue;
+      if (u != T || (K::hi(key) & mhi) != phi || (K::lo(key) & mlo) != plo) continue;
+      atomicAdd(&h[digit_of(hi_word ? K::hi(key) : K::lo(key), pass)], 1u);
+    }
+    __syncthreads();
+    pick_bin<kFinishThreads>(sel, 1, pass, nbins, [&](int b) { return (unsigned long long)h[b]; },
+                             hi_word ? &sel->key_prefix_hi : &sel->key_prefix);
+    if (threadIdx.x == 0) {
+      const int shift = digit_shift(pass);
+      const unsigned long long dm = (unsigned long long)(nbins - 1) << shift;
+      if (hi_word)
+        s_mhi |= dm;
+      else
+        s_mlo |= dm;
+    }
+    __syncthreads();
   }
 }
 
@@ -239,13 +279,13 @@ __device__ __forceinline__ void block_reserve2(unsigned int a, unsigned int b, u
 // |c| == T and key <= key threshold when ties are broken) goes to the spare
 // arrays, any other live entry is dropped: recorded on the tape with its value
 // and birth factor (RECORD), its Eq. 6 term subtracted (entropy runs).
-template <bool RECORD>
-__global__ void __launch_bounds__(kThreads) k_cut_compact(Table from, Table to, const SelectState* sel, Tape tape,
-                                                          int k) {
+template <class KT, bool RECORD>
+__global__ void __launch_bounds__(kThreads) k_cut_compact(TableT<KT> from, TableT<KT> to, const SelectState* sel,
+                                                          TapeT<KT> tape, int k) {
   const unsigned long long n = min(*((volatile unsigned long long*)&from.cnt->n_tail), from.cap_n);
   const unsigned long long T = sel->prefix;
   const bool keys = sel->need_keys != 0;
-  const unsigned long long Kt = sel->key_prefix;
+  const KT Kt = KeyOps<KT>::from_words(sel->key_prefix, sel->key_prefix_hi);
   constexpr int kPer = 4;
   const unsigned long long tile = (unsigned long long)kPer * kThreads;
   unsigned long long dropped = 0;
@@ -253,7 +293,7 @@ __global__ void __launch_bounds__(kThreads) k_cut_compact(Table from, Table to, 
   for (unsigned long long base = (unsigned long long)blockIdx.x * tile; base < n;
        base += (unsigned long long)gridDim.x * tile) {  // block-uniform
     double a[kPer];
-    unsigned long long key[kPer];
+    KT key[kPer];
     int state[kPer];  // 0 none, 1 keep, 2 drop
     unsigned int nk = 0, nd = 0;
 #pragma unroll
@@ -268,7 +308,7 @@ __global__ void __launch_bounds__(kThreads) k_cut_compact(Table from, Table to, 
       const unsigned long long i = base + (unsigned long long)u * kThreads + threadIdx.x;
       key[u] = from.keys[i];
       const unsigned long long m = mag_bits(a[u]);
-      const bool keep = m > T || (m == T && (!keys || key[u] <= Kt));
+      const bool keep = m > T || (m == T && (!keys || !key_less(Kt, key[u])));
       state[u] = keep ? 1 : 2;
       nk += keep;
       nd += !keep;
@@ -293,7 +333,7 @@ __global__ void __launch_bounds__(kThreads) k_cut_compact(Table from, Table to, 
         if (from.entropy) dS -= entropy_term(a[u]);
         if (RECORD) {
           if (pd < tape.cap) {
-            TapeRec& rec = tape_at(tape, pd);
+            TapeRecT<KT>& rec = tape_at(tape, pd);
             rec.key = key[u];
             rec.val = a[u];
             rec.born = from.born[i];
@@ -336,6 +376,7 @@ __global__ void k_select_init(SelectState* sel, unsigned long long n_cut) {
     sel->prefix = 0;
     sel->target = n_cut;
     sel->key_prefix = 0;
+    sel->key_prefix_hi = 0;
     sel->key_target = 0;
     sel->need_keys = 0;
     sel->count_eq = 0;
@@ -346,24 +387,34 @@ __global__ void k_select_init(SelectState* sel, unsigned long long n_cut) {
 
 }  // namespace
 
-cudaError_t launch_select_threshold(const Table& t, SelectState* sel, SelectCand* cand, unsigned long long n_cut,
-                                    int grid, cudaStream_t st, long long* launches) {
+template <class KT>
+cudaError_t launch_select_threshold(const TableT<KT>& t, SelectState* sel, SelectCandT<KT>* cand,
+                                    unsigned long long n_cut, int grid, cudaStream_t st, long long* launches) {
   k_select_init<<<1, kThreads, 0, st>>>(sel, n_cut);
-  k_select_pass<<<grid, kThreads, 0, st>>>(t, sel, 0);
-  k_select_pass<<<grid, kThreads, 0, st>>>(t, sel, 1);
-  k_select_gather<<<grid, kThreads, 0, st>>>(t, sel, cand);
-  k_select_finish<<<1, kFinishThreads, 0, st>>>(t, sel, cand);
+  k_select_pass<KT><<<grid, kThreads, 0, st>>>(t, sel, 0);
+  k_select_pass<KT><<<grid, kThreads, 0, st>>>(t, sel, 1);
+  k_select_gather<KT><<<grid, kThreads, 0, st>>>(t, sel, cand);
+  k_select_finish<KT><<<1, kFinishThreads, 0, st>>>(t, sel, cand);
   *launches += 5;
   return cudaGetLastError();
 }
 
-cudaError_t launch_cut_compact(const Table& from, const Table& to, const SelectState* sel, int record,
-                               const Tape& tape, int k, int grid, cudaStream_t st) {
+template <class KT>
+cudaError_t launch_cut_compact(const TableT<KT>& from, const TableT<KT>& to, const SelectState* sel, int record,
+                               const TapeT<KT>& tape, int k, int grid, cudaStream_t st) {
   if (record)
-    k_cut_compact<true><<<grid, kThreads, 0, st>>>(from, to, sel, tape, k);
+    k_cut_compact<KT, true><<<grid, kThreads, 0, st>>>(from, to, sel, tape, k);
   else
-    k_cut_compact<false><<<grid, kThreads, 0, st>>>(from, to, sel, tape, k);
+    k_cut_compact<KT, false><<<grid, kThreads, 0, st>>>(from, to, sel, tape, k);
   return cudaGetLastError();
 }
+
+#define UCC_SELECT_INSTANTIATE(KT)                                                                                \
+  template cudaError_t launch_select_threshold<KT>(const TableT<KT>&, SelectState*, SelectCandT<KT>*,             \
+                                                   unsigned long long, int, cudaStream_t, long long*);           \
+  template cudaError_t launch_cut_compact<KT>(const TableT<KT>&, const TableT<KT>&, const SelectState*, int,      \
+                                              const TapeT<KT>&, int, int, cudaStream_t);
+UCC_SELECT_INSTANTIATE(unsigned long long)
+UCC_SELECT_INSTANTIATE(Key128)
 
 }  // namespace ucc

@@ -73,8 +73,11 @@ unsigned long long next_pow2(unsigned long long x) {
 }
 
 // One set of table arrays; a rebuild writes into a second set and swaps.
+// Keys take kw 64-bit words each and slots kw 16-byte units (kw = 2 above 64
+// spin-orbitals); the kernels see them through TableT<KT>.
 struct Arrays {
   unsigned long long cap_n = 0, n_slots = 0;
+  int kw = 1;
   unsigned long long* keys = nullptr;
   double* amps = nullptr;
   unsigned int* born = nullptr;
@@ -94,12 +97,12 @@ struct Arrays {
   }
   ucc_status allocate(unsigned long long cn, unsigned long long ns) {
     release();
-    UCC_TRY(dalloc(&keys, cn));
+    UCC_TRY(dalloc(&keys, cn * kw));
     UCC_TRY(dalloc(&amps, cn));
     UCC_TRY(dalloc(&born, cn));
     UCC_TRY(dalloc(&lam, cn));
     UCC_TRY(dalloc(&sigma, cn));
-    UCC_TRY(dalloc(&slots, ns));
+    UCC_TRY(dalloc(&slots, ns * kw));
     UCC_TRY(dalloc(&filt, ns / 4));
     cap_n = cn;
     n_slots = ns;
@@ -131,7 +134,8 @@ struct TableSet {
   }
 };
 
-// psi (live keys and amplitudes) at the start of a gradient segment.
+// psi (live keys and amplitudes) at the start of a gradient segment; keys of
+// kw words each.
 struct Snapshot {
   unsigned long long n = 0;
   unsigned long long* keys = nullptr;
@@ -154,17 +158,20 @@ struct ucc_ctx {
   int K = 0;
   std::vector<int> rows;         // K x 4
   std::vector<double> theta;     // K
-  std::vector<Factor> factors;   // host copy
+  bool wide = false;             // more than 64 spin-orbitals: two-word keys
+  int kw = 1;                    // key words
+  std::vector<Factor> factors;   // host copy (one-word keys)
+  std::vector<FactorT<Key128>> factors_w;  // host copy (two-word keys)
   ucc_options opt{};
 
-  Factor* d_factors = nullptr;
+  void* d_factors = nullptr;     // FactorT<KT>[K]
   double* d_h = nullptr;
   double* d_g = nullptr;
   double* d_grad = nullptr;
   double* d_partials = nullptr;
   int partial_cap = 0;
   SelectState* d_sel = nullptr;
-  SelectCand* d_cand = nullptr;  // [kSelectCandCap] candidates of the cut's last selection passes
+  void* d_cand = nullptr;  // SelectCandT<KT>[kSelectCandCap]: candidates of the cut's last selection passes
   double* d_entropy = nullptr;  // [K] Eq. 6 after each factor of the last apply
   bool entropy_on = false;
   bool have_entropy = false;
@@ -172,8 +179,8 @@ struct ucc_ctx {
   int main = 0;
   std::vector<Snapshot> snaps;
   // kill tape (paged) of the segment being reversed
-  std::vector<TapeRec*> t_pages;
-  TapeRec** d_pages = nullptr;          // [kTapeMaxPages]
+  std::vector<void*> t_pages;
+  void** d_pages = nullptr;             // [kTapeMaxPages] TapeRecT<KT> pages
   unsigned long long* t_off = nullptr;  // K + 1
   unsigned long long tape_cap = 0;
   unsigned long long tape_budget = 0;   // bytes the tape may take in this call
@@ -190,14 +197,15 @@ struct ucc_ctx {
   long long launches = 0;
   long long cut_total = 0;
 
-  Table table(const TableSet& s) const {
-    Table t;
-    t.keys = s.cur.keys;
+  template <class KT>
+  TableT<KT> table(const TableSet& s) const {
+    TableT<KT> t;
+    t.keys = reinterpret_cast<KT*>(s.cur.keys);
     t.amps = s.cur.amps;
     t.born = s.cur.born;
     t.lam = s.cur.lam;
     t.sigma = s.cur.sigma;
-    t.slots = s.cur.slots;
+    t.slots = reinterpret_cast<SlotT<KT>*>(s.cur.slots);
     t.slot_mask = s.cur.n_slots - 1;
     t.slot_shift = 64 - __builtin_ctzll(s.cur.n_slots);
     t.filt = s.cur.filt;
@@ -208,13 +216,23 @@ struct ucc_ctx {
     t.entropy = entropy_on ? d_entropy : nullptr;
     return t;
   }
-  Tape tape() const {
-    Tape tp;
-    tp.pages = d_pages;
+  template <class KT>
+  TapeT<KT> tape() const {
+    TapeT<KT> tp;
+    tp.pages = reinterpret_cast<TapeRecT<KT>* const*>(d_pages);
     tp.off = t_off;
     tp.cap = tape_cap;
     return tp;
   }
+  template <class KT>
+  FactorT<KT>* dfactors() const {
+    return static_cast<FactorT<KT>*>(d_factors);
+  }
+  template <class KT>
+  SelectCandT<KT>* dcand() const {
+    return static_cast<SelectCandT<KT>*>(d_cand);
+  }
+  size_t tape_rec_bytes() const { return wide ? sizeof(TapeRecT<Key128>) : sizeof(TapeRec); }
   int full_grid(int per_sm = 8) const { return std::max(1, num_sms * per_sm); }
 };
 
@@ -224,19 +242,20 @@ namespace {
 // E that it excites: the four operators count occupied modes below i, j, b, a
 // in the running determinant; relative to E those counts shift by the index
 // comparisons below, so parity = popc(E & pmask) + pconst (mod 2).
-Factor make_factor(int i, int j, int a, int b, double th) {
-  auto below = [](int p) { return p <= 0 ? 0ull : ((1ull << p) - 1ull); };
-  Factor f{};
+template <class KT>
+FactorT<KT> make_factor(int i, int j, int a, int b, double th) {
+  using K = KeyOps<KT>;
+  FactorT<KT> f{};
   if (j < 0) {
-    f.occ = 1ull << i;
-    f.vir = 1ull << a;
-    f.pmask = below(i) ^ below(a);
+    f.occ = K::bit(i);
+    f.vir = K::bit(a);
+    f.pmask = K::below(i) ^ K::below(a);
     f.pconst = (i < a) ? 1 : 0;
     f.is_double = 0;
   } else {
-    f.occ = (1ull << i) | (1ull << j);
-    f.vir = (1ull << a) | (1ull << b);
-    f.pmask = below(i) ^ below(j) ^ below(a) ^ below(b);
+    f.occ = K::bit(i) | K::bit(j);
+    f.vir = K::bit(a) | K::bit(b);
+    f.pmask = K::below(i) ^ K::below(j) ^ K::below(a) ^ K::below(b);
     f.pconst = ((i < j) + (i < b) + (j < b) + (i < a) + (j < a) + (b < a)) & 1;
     f.is_double = 1;
   }
@@ -279,7 +298,8 @@ unsigned long long slots_for(unsigned long long cap_n) {
 
 // The spare arrays of table s, sized for new_cap entries and cleared, as the
 // target of a compaction; finish_rebuild hashes them and swaps them in.
-ucc_status prepare_spare(ucc_ctx* c, TableSet& s, unsigned long long new_cap, Table* out) {
+template <class KT>
+ucc_status prepare_spare(ucc_ctx* c, TableSet& s, unsigned long long new_cap, TableT<KT>* out) {
   if (new_cap >= kMaxEntries)
     return fail(UCC_ECAPACITY, "the wavefunction needs more than 2^31 stored entries (" + std::to_string(new_cap) +
                                    ")");
@@ -292,27 +312,28 @@ ucc_status prepare_spare(ucc_ctx* c, TableSet& s, unsigned long long new_cap, Ta
       return fail(UCC_ECAPACITY, "cannot allocate " + std::to_string(new_cap) + " entries: " + g_last_error);
     }
   }
-  Table to = c->table(s);
-  to.keys = s.spare.keys;
+  TableT<KT> to = c->template table<KT>(s);
+  to.keys = reinterpret_cast<KT*>(s.spare.keys);
   to.amps = s.spare.amps;
   to.born = s.spare.born;
   to.lam = s.spare.lam;
   to.sigma = s.spare.sigma;
-  to.slots = s.spare.slots;
+  to.slots = reinterpret_cast<SlotT<KT>*>(s.spare.slots);
   to.slot_mask = ns - 1;
   to.slot_shift = 64 - __builtin_ctzll(ns);
   to.filt = s.spare.filt;
   to.filt_shift = 32 - (__builtin_ctzll(ns) - 2);
   to.cap_n = new_cap;
   CUDA_TRY(cudaMemsetAsync(&s.d_cnt->new_n, 0, sizeof(unsigned long long), c->stream));
-  CUDA_TRY(cudaMemsetAsync(to.slots, 0, ns * sizeof(Slot), c->stream));
+  CUDA_TRY(cudaMemsetAsync(to.slots, 0, ns * sizeof(SlotT<KT>), c->stream));
   CUDA_TRY(cudaMemsetAsync(to.filt, 0, ns / 4 * sizeof(unsigned int), c->stream));
   *out = to;
   return UCC_OK;
 }
 
 // Hash the compacted spare arrays `to` and make them the current ones.
-ucc_status finish_rebuild(ucc_ctx* c, TableSet& s, const Table& to) {
+template <class KT>
+ucc_status finish_rebuild(ucc_ctx* c, TableSet& s, const TableT<KT>& to) {
   const int grid = c->full_grid();
   CUDA_TRY(launch_rehash(to, grid, c->stream));
   CUDA_TRY(launch_finish_rebuild(to, c->stream));
@@ -336,11 +357,12 @@ ucc_status add_elapsed(ucc_ctx* c, double* acc) {
   return UCC_OK;
 }
 
+template <class KT>
 ucc_status rebuild(ucc_ctx* c, TableSet& s, unsigned long long new_cap, bool with_lam = false) {
-  Table to;
+  TableT<KT> to;
   CUDA_TRY(cudaEventRecord(c->rev_[0], c->stream));
   UCC_TRY(prepare_spare(c, s, new_cap, &to));
-  CUDA_TRY(launch_compact(c->table(s), to, with_lam ? 2 : 1, c->full_grid(), c->stream));
+  CUDA_TRY(launch_compact(c->template table<KT>(s), to, with_lam ? 2 : 1, c->full_grid(), c->stream));
   c->launches++;
   UCC_TRY(finish_rebuild(c, s, to));
   CUDA_TRY(cudaEventRecord(c->rev_[1], c->stream));
@@ -351,14 +373,16 @@ ucc_status rebuild(ucc_ctx* c, TableSet& s, unsigned long long new_cap, bool wit
 // pass keeps the entries above it in the spare arrays (dropping the ε-dropped
 // ones too) and records the cut ones on the tape, and the spare arrays are
 // hashed and swapped in.
+template <class KT>
 ucc_status cut_rebuild(ucc_ctx* c, TableSet& s, bool record, int k) {
   const int grid = c->full_grid();
   CUDA_TRY(cudaEventRecord(c->rev_[0], c->stream));
-  CUDA_TRY(launch_select_threshold(c->table(s), c->d_sel, c->d_cand, (unsigned long long)c->opt.n_cut, grid,
-                                   c->stream, &c->launches));
-  Table to;
+  CUDA_TRY(launch_select_threshold(c->template table<KT>(s), c->d_sel, c->template dcand<KT>(),
+                                   (unsigned long long)c->opt.n_cut, grid, c->stream, &c->launches));
+  TableT<KT> to;
   UCC_TRY(prepare_spare(c, s, s.cur.cap_n, &to));
-  CUDA_TRY(launch_cut_compact(c->table(s), to, c->d_sel, record ? 1 : 0, c->tape(), k, grid, c->stream));
+  CUDA_TRY(launch_cut_compact(c->template table<KT>(s), to, c->d_sel, record ? 1 : 0, c->template tape<KT>(), k,
+                              grid, c->stream));
   c->launches++;
   UCC_TRY(finish_rebuild(c, s, to));
   CUDA_TRY(cudaEventRecord(c->rev_[1], c->stream));
@@ -371,17 +395,18 @@ ucc_status cut_rebuild(ucc_ctx* c, TableSet& s, bool record, int k) {
 ucc_status ensure_tape(ucc_ctx* c, unsigned long long need) {
   while (c->tape_cap < need) {
     if ((int)c->t_pages.size() >= kTapeMaxPages) return fail(UCC_ECAPACITY, "kill tape page table full");
-    const unsigned long long bytes = (c->tape_cap + kTapePageRecs) * sizeof(TapeRec);
+    const unsigned long long bytes = (c->tape_cap + kTapePageRecs) * c->tape_rec_bytes();
     if (c->tape_budget && bytes > c->tape_budget) {
       c->tape_over_budget = true;
       return fail(UCC_ECAPACITY, "kill tape over its memory budget");
     }
-    TapeRec* page = nullptr;
-    UCC_TRY(dalloc(&page, kTapePageRecs));
-    CUDA_TRY(cudaMemcpyAsync(c->d_pages + c->t_pages.size(), &page, sizeof(TapeRec*), cudaMemcpyHostToDevice,
+    unsigned char* page = nullptr;
+    UCC_TRY(dalloc(&page, kTapePageRecs * c->tape_rec_bytes()));
+    void* pv = page;
+    CUDA_TRY(cudaMemcpyAsync(c->d_pages + c->t_pages.size(), &pv, sizeof(void*), cudaMemcpyHostToDevice,
                              c->stream));
     CUDA_TRY(cudaStreamSynchronize(c->stream));
-    c->t_pages.push_back(page);
+    c->t_pages.push_back(pv);
     c->tape_cap += kTapePageRecs;
   }
   return UCC_OK;
@@ -393,20 +418,22 @@ void release_tape(ucc_ctx* c) {
   c->tape_cap = 0;
 }
 
-unsigned long long reference_key(const ucc_ctx* c) {
-  unsigned long long hf = 0;
-  for (int s = 0; s < c->n_alpha; ++s) hf |= 1ull << (2 * s);
-  for (int s = 0; s < c->n_beta; ++s) hf |= 1ull << (2 * s + 1);
+template <class KT>
+KT reference_key(const ucc_ctx* c) {
+  KT hf = KeyOps<KT>::zero();
+  for (int s = 0; s < c->n_alpha; ++s) hf = hf | KeyOps<KT>::bit(2 * s);
+  for (int s = 0; s < c->n_beta; ++s) hf = hf | KeyOps<KT>::bit(2 * s + 1);
   return hf;
 }
 
 // psi = {reference: 1.0} in table s.
+template <class KT>
 ucc_status reset_table(ucc_ctx* c, TableSet& s) {
   if (s.cur.cap_n == 0) UCC_TRY(s.cur.allocate(1 << 12, slots_for(1 << 12)));
   CUDA_TRY(cudaMemsetAsync(s.d_cnt, 0, sizeof(Counters), c->stream));
-  CUDA_TRY(cudaMemsetAsync(s.cur.slots, 0, s.cur.n_slots * sizeof(Slot), c->stream));
+  CUDA_TRY(cudaMemsetAsync(s.cur.slots, 0, s.cur.n_slots * sizeof(SlotT<KT>), c->stream));
   CUDA_TRY(cudaMemsetAsync(s.cur.filt, 0, s.cur.n_slots / 4 * sizeof(unsigned int), c->stream));
-  CUDA_TRY(launch_reset(c->table(s), reference_key(c), c->stream));
+  CUDA_TRY(launch_reset(c->template table<KT>(s), reference_key<KT>(c), c->stream));
   c->launches++;
   return UCC_OK;
 }
@@ -420,34 +447,50 @@ ucc_status reset_tape(ucc_ctx* c, TableSet& s, int k0) {
 }
 
 // Load a snapshot into table s (its previous contents are discarded).
+template <class KT>
 ucc_status load_snapshot(ucc_ctx* c, TableSet& s, const Snapshot& snap) {
   const unsigned long long cap = std::max<unsigned long long>(4 * snap.n, 1 << 12);
   if (cap >= kMaxEntries) return fail(UCC_ECAPACITY, "snapshot too large for one table");
   if (s.cur.cap_n < cap) UCC_TRY(s.cur.allocate(cap, slots_for(cap)));
   CUDA_TRY(cudaMemsetAsync(s.d_cnt, 0, sizeof(Counters), c->stream));
-  CUDA_TRY(cudaMemsetAsync(s.cur.slots, 0, s.cur.n_slots * sizeof(Slot), c->stream));
+  CUDA_TRY(cudaMemsetAsync(s.cur.slots, 0, s.cur.n_slots * sizeof(SlotT<KT>), c->stream));
   CUDA_TRY(cudaMemsetAsync(s.cur.filt, 0, s.cur.n_slots / 4 * sizeof(unsigned int), c->stream));
   const int grid = c->full_grid();
-  CUDA_TRY(launch_restore(c->table(s), snap.keys, snap.amps, snap.n, grid, c->stream));
-  CUDA_TRY(launch_rehash(c->table(s), grid, c->stream));
+  CUDA_TRY(launch_restore(c->template table<KT>(s), reinterpret_cast<const KT*>(snap.keys), snap.amps, snap.n, grid,
+                          c->stream));
+  CUDA_TRY(launch_rehash(c->template table<KT>(s), grid, c->stream));
   c->launches += 2;
   return read_counters(c, s);
 }
 
 // Copy the live entries of table s into a new snapshot.
+template <class KT>
 ucc_status take_snapshot(ucc_ctx* c, TableSet& s, Snapshot* out) {
   UCC_TRY(read_counters(c, s));
   const unsigned long long live = s.h_cnt->n_tail - s.h_cnt->n_dead;
   out->release();
-  UCC_TRY(dalloc(&out->keys, live));
+  UCC_TRY(dalloc(&out->keys, live * c->kw));
   UCC_TRY(dalloc(&out->amps, live));
   out->n = live;
   CUDA_TRY(cudaMemsetAsync(&s.d_cnt->new_n, 0, sizeof(unsigned long long), c->stream));
-  CUDA_TRY(launch_export(c->table(s), live, out->keys, out->amps, nullptr, c->full_grid(), c->stream));
+  CUDA_TRY(launch_export(c->template table<KT>(s), live, reinterpret_cast<KT*>(out->keys), out->amps, nullptr,
+                         c->full_grid(), c->stream));
   c->launches++;
   UCC_TRY(read_counters(c, s));
   if (s.h_cnt->new_n != live) return fail(UCC_ECUDA, "snapshot count mismatch");
   return UCC_OK;
+}
+
+// Host copy of factor k in the context's key width.
+template <class KT>
+FactorT<KT> host_factor(const ucc_ctx* c, int k);
+template <>
+Factor host_factor<unsigned long long>(const ucc_ctx* c, int k) {
+  return c->factors[k];
+}
+template <>
+FactorT<Key128> host_factor<Key128>(const ucc_ctx* c, int k) {
+  return c->factors_w[k];
 }
 
 int pick_probe_width(ucc_ctx* c) {
@@ -463,6 +506,7 @@ int pick_probe_width(ucc_ctx* c) {
 std::mutex g_tune_mutex;
 std::map<std::pair<int, int>, int> g_tuned;
 
+template <class KT>
 ucc_status autotune(ucc_ctx* c, TableSet& s, int k, unsigned long long n) {
   if (c->opt.probe_width != 0 || n < (1ull << 16) || k >= c->K) return UCC_OK;
   int bucket = 0;
@@ -485,7 +529,8 @@ ucc_status autotune(ucc_ctx* c, TableSet& s, int k, unsigned long long n) {
   for (int rep = 0; rep < 2 && st == UCC_OK; ++rep)
     for (int w : widths) {
       if (cudaEventRecord(c->kev[0], c->stream) != cudaSuccess ||
-          launch_probe_bench(c->table(s), c->factors[k], w, sink, c->full_grid(), c->stream) != cudaSuccess ||
+          launch_probe_bench(c->template table<KT>(s), host_factor<KT>(c, k), w, sink, c->full_grid(), c->stream) !=
+              cudaSuccess ||
           cudaEventRecord(c->kev[1], c->stream) != cudaSuccess || cudaEventSynchronize(c->kev[1]) != cudaSuccess) {
         st = fail(UCC_ECUDA, "probe-width autotuning failed");
         break;
@@ -509,6 +554,7 @@ ucc_status autotune(ucc_ctx* c, TableSet& s, int k, unsigned long long n) {
 // Make room for the next factor: it may append one entry per stored entry
 // (and, in gradient runs, drop as many onto the tape).  Compacts when a
 // quarter of the stored entries are dropped ones.
+template <class KT>
 ucc_status ensure_room(ucc_ctx* c, TableSet& s, bool record) {
   UCC_TRY(read_counters(c, s));
   const Counters h = *s.h_cnt;  // copy: later reads overwrite the mirror
@@ -521,7 +567,7 @@ ucc_status ensure_room(ucc_ctx* c, TableSet& s, bool record) {
   if (!room || sparse) {
     unsigned long long cap = s.cur.cap_n;
     if (2 * live > cap || 8 * live > 3 * s.cur.n_slots) cap = std::max<unsigned long long>(5 * live / 2, 1 << 12);
-    UCC_TRY(rebuild(c, s, cap));
+    UCC_TRY(rebuild<KT>(c, s, cap));
     UCC_TRY(read_counters(c, s));
   }
   return UCC_OK;
@@ -531,6 +577,7 @@ ucc_status ensure_room(ucc_ctx* c, TableSet& s, bool record) {
 // when the next factor might not fit or when the Methods-section cut is due;
 // later launches in the chunk then skip, and the host cuts / grows and
 // resumes at the flagged factor.  Chunks shrink when stops come often.
+template <class KT>
 ucc_status run_factors(ucc_ctx* c, TableSet& s, double eps, bool record, int k0, int k1) {
   const unsigned long long n_max = c->opt.n_max > 0 ? (unsigned long long)c->opt.n_max : 0ull;
   UCC_TRY(read_counters(c, s));
@@ -548,8 +595,8 @@ ucc_status run_factors(ucc_ctx* c, TableSet& s, double eps, bool record, int k0,
     const int pw = pick_probe_width(c);
     CUDA_TRY(cudaEventRecord(c->kev[0], c->stream));
     for (int kk = k; kk < end; ++kk) {
-      CUDA_TRY(launch_forward(c->table(s), c->d_factors, kk, eps, (unsigned int)(kk + 1), record ? 1 : 0, c->tape(),
-                              n_max, pw, grid, c->stream));
+      CUDA_TRY(launch_forward(c->template table<KT>(s), c->template dfactors<KT>(), kk, eps, (unsigned int)(kk + 1),
+                              record ? 1 : 0, c->template tape<KT>(), n_max, pw, grid, c->stream));
       c->launches += 2;  // the step and the linking of its appended entries
       c->stats.forward_launches++;
     }
@@ -570,7 +617,7 @@ ucc_status run_factors(ucc_ctx* c, TableSet& s, double eps, bool record, int k0,
       chunk = std::max(2, std::min(64, 2 * (resume - k)));
       if (h.cut_pending) {
         const unsigned long long before = h.n_tail - h.n_dead;
-        UCC_TRY(cut_rebuild(c, s, record, resume - 1));
+        UCC_TRY(cut_rebuild<KT>(c, s, record, resume - 1));
         UCC_TRY(read_counters(c, s));
         const unsigned long long after = s.h_cnt->n_tail - s.h_cnt->n_dead;
         if (after != (unsigned long long)c->opt.n_cut)
@@ -578,7 +625,7 @@ ucc_status run_factors(ucc_ctx* c, TableSet& s, double eps, bool record, int k0,
                                      std::to_string(c->opt.n_cut));
         c->cut_total += (long long)(before - after);
       }
-      UCC_TRY(ensure_room(c, s, record));
+      UCC_TRY(ensure_room<KT>(c, s, record));
       const int minus_one = -1, zero = 0;
       CUDA_TRY(cudaMemcpyAsync(&s.d_cnt->stop_k, &minus_one, sizeof(int), cudaMemcpyHostToDevice, c->stream));
       CUDA_TRY(cudaMemcpyAsync(&s.d_cnt->cut_pending, &zero, sizeof(int), cudaMemcpyHostToDevice, c->stream));
@@ -588,9 +635,9 @@ ucc_status run_factors(ucc_ctx* c, TableSet& s, double eps, bool record, int k0,
       continue;
     }
     chunk = std::min(64, chunk * 2);
-    UCC_TRY(autotune(c, s, end, h.n_tail));
+    UCC_TRY(autotune<KT>(c, s, end, h.n_tail));
     // Compact when a quarter of the stored entries are dropped ones.
-    if (h.n_dead > 4096 && h.n_dead * 4 > h.n_tail) UCC_TRY(rebuild(c, s, s.cur.cap_n));
+    if (h.n_dead > 4096 && h.n_dead * 4 > h.n_tail) UCC_TRY(rebuild<KT>(c, s, s.cur.cap_n));
     k = end;
   }
   return UCC_OK;
@@ -617,16 +664,17 @@ int segment_stride(const ucc_ctx* c) {
   return std::max(1, c->K);
 }
 
+template <class KT>
 ucc_status run_forward(ucc_ctx* c, double eps, bool record) {
   if (!(eps >= 0.0) || std::isinf(eps)) return fail(UCC_EINVAL, "eps must be finite and >= 0");
   TableSet& s = c->ts[c->main];
   c->cut_total = 0;
   c->entropy_on = !record && c->opt.record_entropy != 0;
   c->have_entropy = false;
-  UCC_TRY(reset_table(c, s));
+  UCC_TRY(reset_table<KT>(c, s));
   CUDA_TRY(cudaEventRecord(c->ev[0], c->stream));
   if (!record) {
-    UCC_TRY(run_factors(c, s, eps, false, 0, c->K));
+    UCC_TRY(run_factors<KT>(c, s, eps, false, 0, c->K));
     c->have_entropy = c->entropy_on;
     c->entropy_on = false;
   } else {
@@ -636,9 +684,9 @@ ucc_status run_forward(ucc_ctx* c, double eps, bool record) {
     c->snaps.assign(std::max(0, nseg), Snapshot());
     for (int j = 0; j < nseg; ++j) {
       const int k0 = j * S, k1 = std::min(c->K, k0 + S);
-      if (j > 0) UCC_TRY(take_snapshot(c, s, &c->snaps[j]));
+      if (j > 0) UCC_TRY(take_snapshot<KT>(c, s, &c->snaps[j]));
       UCC_TRY(reset_tape(c, s, k0));
-      UCC_TRY(run_factors(c, s, eps, true, k0, k1));
+      UCC_TRY(run_factors<KT>(c, s, eps, true, k0, k1));
     }
   }
   CUDA_TRY(cudaEventRecord(c->ev[1], c->stream));
@@ -654,6 +702,7 @@ ucc_status run_forward(ucc_ctx* c, double eps, bool record) {
   return UCC_OK;
 }
 
+template <class KT>
 ucc_status run_energy(ucc_ctx* c, double* E, double* norm2) {
   TableSet& s = c->ts[c->main];
   Integrals in;
@@ -668,7 +717,7 @@ ucc_status run_energy(ucc_ctx* c, double* E, double* norm2) {
   UCC_TRY(ensure_partials(c, c->full_grid()));
   CUDA_TRY(cudaMemsetAsync(&s.d_cnt->sig_probes, 0, 2 * sizeof(unsigned long long), c->stream));
   CUDA_TRY(cudaEventRecord(c->ev[2], c->stream));
-  CUDA_TRY(launch_sigma(c->table(s), in, grid, c->stream));
+  CUDA_TRY(launch_sigma(c->template table<KT>(s), in, grid, c->stream));
   c->launches += 2;
   CUDA_TRY(cudaEventRecord(c->ev[3], c->stream));
   UCC_TRY(read_counters(c, s));
@@ -692,6 +741,7 @@ ucc_status run_energy(ucc_ctx* c, double* E, double* norm2) {
 // Reverse steps between reads of the dropped-entry count.
 constexpr int kDeadCheck = 16;
 
+template <class KT>
 ucc_status reverse_segment(ucc_ctx* c, TableSet& s, int k0, int k1) {
   if (k1 <= k0) return UCC_OK;
   std::vector<unsigned long long> off(k1 - k0 + 1);
@@ -727,12 +777,12 @@ ucc_status reverse_segment(ucc_ctx* c, TableSet& s, int k0, int k1) {
       CUDA_TRY(cudaEventElapsedTime(&ms, c->kev[0], c->kev[1]));
       kernel_ms += ms;
       // Live entries now: stored minus those the sweep or the forward dropped.
-      UCC_TRY(rebuild(c, s, s.cur.cap_n, true));
+      UCC_TRY(rebuild<KT>(c, s, s.cur.cap_n, true));
       c->stats.reverse_compactions++;
       UCC_TRY(read_counters(c, s));
       bound = s.h_cnt->n_tail;
       if (bound + rec > s.cur.cap_n || 4ull * (bound + rec) > 3ull * s.cur.n_slots) {
-        UCC_TRY(rebuild(c, s, std::max<unsigned long long>(2 * s.cur.cap_n, 2 * (bound + rec) + 64), true));
+        UCC_TRY(rebuild<KT>(c, s, std::max<unsigned long long>(2 * s.cur.cap_n, 2 * (bound + rec) + 64), true));
         UCC_TRY(read_counters(c, s));
         bound = s.h_cnt->n_tail;
       }
@@ -742,9 +792,11 @@ ucc_status reverse_segment(ucc_ctx* c, TableSet& s, int k0, int k1) {
     }
     if (rec) {
       const int g2 = (int)std::min<unsigned long long>((unsigned long long)grid_full, (rec + 255) / 256);
-      CUDA_TRY(launch_tape_reinsert(c->table(s), c->tape(), k, rec, std::max(g2, 1), c->stream, &c->launches));
+      CUDA_TRY(launch_tape_reinsert(c->template table<KT>(s), c->template tape<KT>(), k, rec, std::max(g2, 1),
+                                    c->stream, &c->launches));
     }
-    CUDA_TRY(launch_reverse(c->table(s), c->d_factors, k, stamp, c->d_grad, pick_probe_width(c), grid, c->stream));
+    CUDA_TRY(launch_reverse(c->template table<KT>(s), c->template dfactors<KT>(), k, stamp, c->d_grad,
+                            pick_probe_width(c), grid, c->stream));
     c->launches++;
     c->stats.reverse_launches++;
     bound += rec;
@@ -759,42 +811,45 @@ ucc_status reverse_segment(ucc_ctx* c, TableSet& s, int k0, int k1) {
   return UCC_OK;
 }
 
+template <class KT>
 ucc_status run_gradient_once(ucc_ctx* c, double eps, double* E, double* grad_out, int on_device);
 
 // dE/dtheta: first on one tape; if the tape would pass its budget, again with
 // segment checkpoints.
+template <class KT>
 ucc_status run_gradient(ucc_ctx* c, double eps, double* E, double* grad_out, int on_device) {
   size_t free_b = 0, total_b = 0;
   CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
-  const unsigned long long held = (unsigned long long)c->tape_cap * sizeof(TapeRec);
+  const unsigned long long held = (unsigned long long)c->tape_cap * c->tape_rec_bytes();
   c->tape_budget = c->opt.tape_budget_mb > 0 ? (unsigned long long)c->opt.tape_budget_mb << 20
                                              : (unsigned long long)(0.6 * (double)(free_b + held));
   c->force_segments = false;
   c->tape_over_budget = false;
-  ucc_status s = run_gradient_once(c, eps, E, grad_out, on_device);
+  ucc_status s = run_gradient_once<KT>(c, eps, E, grad_out, on_device);
   if (s == UCC_ECAPACITY && c->tape_over_budget && c->opt.checkpoint_stride <= 0) {
     release_tape(c);
     c->force_segments = true;
     c->tape_over_budget = false;
     c->tape_budget = 0;
-    s = run_gradient_once(c, eps, E, grad_out, on_device);
+    s = run_gradient_once<KT>(c, eps, E, grad_out, on_device);
   }
   return s;
 }
 
+template <class KT>
 ucc_status run_gradient_once(ucc_ctx* c, double eps, double* E, double* grad_out, int on_device) {
   c->launches = 0;
   c->stats = ucc_stats{};
   c->main = 0;
-  UCC_TRY(run_forward(c, eps, true));
+  UCC_TRY(run_forward<KT>(c, eps, true));
   TableSet& s0 = c->ts[c->main];
   double e = 0.0, n2 = 0.0;
-  UCC_TRY(run_energy(c, &e, &n2));
+  UCC_TRY(run_energy<KT>(c, &e, &n2));
   if (E) *E = e;
   const int grid_full = c->full_grid();
   UCC_TRY(ensure_partials(c, grid_full));
   CUDA_TRY(cudaEventRecord(c->ev[4], c->stream));
-  CUDA_TRY(launch_lambda_init(c->table(s0), grid_full, c->stream));
+  CUDA_TRY(launch_lambda_init(c->template table<KT>(s0), grid_full, c->stream));
   c->launches++;
   const int S = segment_stride(c);
   const int nseg = c->K == 0 ? 0 : (c->K + S - 1) / S;
@@ -807,22 +862,22 @@ ucc_status run_gradient_once(ucc_ctx* c, double eps, double* E, double* grad_out
       TableSet& from = c->ts[c->main];
       TableSet& work = c->ts[1 - c->main];
       if (j == 0) {
-        UCC_TRY(reset_table(c, work));
+        UCC_TRY(reset_table<KT>(c, work));
       } else {
-        UCC_TRY(load_snapshot(c, work, c->snaps[j]));
+        UCC_TRY(load_snapshot<KT>(c, work, c->snaps[j]));
       }
       UCC_TRY(reset_tape(c, work, k0));
-      UCC_TRY(run_factors(c, work, eps, true, k0, k1));
+      UCC_TRY(run_factors<KT>(c, work, eps, true, k0, k1));
       UCC_TRY(read_counters(c, work));
       c->stats.recompute_scanned += (long long)work.h_cnt->scanned;
       c->stats.recompute_rotations += (long long)work.h_cnt->rotations;
       c->stats.recompute_created += (long long)work.h_cnt->created;
       tape_peak = std::max<long long>(tape_peak, (long long)work.h_cnt->tape_n);
-      CUDA_TRY(launch_transfer_lambda(c->table(work), c->table(from), grid_full, c->stream));
+      CUDA_TRY(launch_transfer_lambda(c->template table<KT>(work), c->template table<KT>(from), grid_full, c->stream));
       c->launches++;
       c->main = 1 - c->main;
     }
-    UCC_TRY(reverse_segment(c, c->ts[c->main], k0, k1));
+    UCC_TRY(reverse_segment<KT>(c, c->ts[c->main], k0, k1));
   }
   CUDA_TRY(cudaEventRecord(c->ev[5], c->stream));
   if (grad_out && c->K) {
@@ -845,7 +900,7 @@ ucc_status run_gradient_once(ucc_ctx* c, double eps, double* E, double* grad_out
 ucc_status validate_problem(const ucc_hamiltonian* ham, const ucc_ansatz* an) {
   if (!ham || !an) return fail(UCC_EINVAL, "null hamiltonian or ansatz");
   const int n = ham->n_spatial;
-  if (n < 1 || n > 32) return fail(UCC_EINVAL, "n_spatial must be in [1, 32] (64-bit determinant keys)");
+  if (n < 1 || n > 64) return fail(UCC_EINVAL, "n_spatial must be in [1, 64] (128-bit determinant keys)");
   if (ham->n_alpha < 0 || ham->n_beta < 0 || ham->n_alpha > n || ham->n_beta > n || ham->n_alpha + ham->n_beta < 1)
     return fail(UCC_EINVAL, "electron counts out of range");
   if (!ham->h || !ham->g) return fail(UCC_EINVAL, "null integrals");
@@ -887,9 +942,15 @@ ucc_status validate_problem(const ucc_hamiltonian* ham, const ucc_ansatz* an) {
 ucc_status upload_factors(ucc_ctx* c) {
   for (int k = 0; k < c->K; ++k) {
     const int* r = &c->rows[4 * k];
-    c->factors[k] = make_factor(r[0], r[1], r[2], r[3], c->theta[k]);
+    if (c->wide)
+      c->factors_w[k] = make_factor<Key128>(r[0], r[1], r[2], r[3], c->theta[k]);
+    else
+      c->factors[k] = make_factor<unsigned long long>(r[0], r[1], r[2], r[3], c->theta[k]);
   }
-  if (c->K)
+  if (c->K && c->wide)
+    CUDA_TRY(cudaMemcpyAsync(c->d_factors, c->factors_w.data(), c->K * sizeof(FactorT<Key128>),
+                             cudaMemcpyHostToDevice, c->stream));
+  else if (c->K)
     CUDA_TRY(cudaMemcpyAsync(c->d_factors, c->factors.data(), c->K * sizeof(Factor), cudaMemcpyHostToDevice,
                              c->stream));
   // The host vector must outlive the copy.
@@ -936,15 +997,18 @@ unsigned long long sector_size(const ucc_ctx* c) {
 
 // Entry capacity a job of the persistent batch is given up front: three times
 // its sector (a table holds at most the sector live plus a quarter dropped,
-// and a step may double what it holds), or four times N_MAX when its cut can
+// and a step may double what it holds), or three times N_MAX when its cut can
 // fire.  0 when the job cannot be sized (no cut and a sector too large).
 unsigned long long batch_capacity(const ucc_ctx* c) {
+  if (c->wide) return 0;  // the persistent batched kernels take one-word keys
   const unsigned long long sector = sector_size(c);
   const unsigned long long n_max = c->opt.n_max > 0 ? (unsigned long long)c->opt.n_max : 0ull;
-  unsigned long long cap = (n_max > 0 && sector > n_max) ? 4 * n_max : 3 * sector;
+  unsigned long long cap = (n_max > 0 && sector > n_max) ? 3 * n_max : 3 * sector;
   cap = std::max<unsigned long long>(cap, 4096);
   if (c->opt.max_entries > 0 && cap > 3ull * (unsigned long long)c->opt.max_entries) return 0;
-  if (cap > (1ull << 26)) return 0;  // larger jobs take the one-job path
+  // A job's cuts and compactions run on one block: larger tables take the
+  // one-job path, whose kernels spread a table over the whole GPU.
+  if (cap > (1ull << 22)) return 0;
   return cap;
 }
 
@@ -1000,9 +1064,9 @@ ucc_status batch_persistent(const std::vector<int>& idx, ucc_ctx* const* jobs, d
   auto view_of = [&](int x) {
     ucc_ctx* c = jobs[idx[x]];
     JobView v{};
-    v.t = c->table(c->ts[0]);
-    v.factors = c->d_factors;
-    v.tape = c->tape();
+    v.t = c->template table<unsigned long long>(c->ts[0]);
+    v.factors = c->template dfactors<unsigned long long>();
+    v.tape = c->template tape<unsigned long long>();
     v.in.h = c->d_h;
     v.in.g = c->d_g;
     v.in.n = c->n_spatial;
@@ -1066,7 +1130,7 @@ ucc_status batch_persistent(const std::vector<int>& idx, ucc_ctx* const* jobs, d
       if (ts.cur.cap_n != cap || ts.cur.n_slots != ns) UCC_TRY(ts.cur.allocate(cap, ns));
       if (ts.spare.cap_n != cap || ts.spare.n_slots != ns) UCC_TRY(ts.spare.allocate(cap, ns));
       c->main = 0;
-      UCC_TRY(reset_table(c, ts));
+      UCC_TRY(reset_table<unsigned long long>(c, ts));
       if (record) UCC_TRY(reset_tape(c, ts, 0));
       hs[x] = JobState{};
       hs[x].stop = -1;
@@ -1174,7 +1238,7 @@ ucc_status batch_persistent(const std::vector<int>& idx, ucc_ctx* const* jobs, d
       if (done) break;
       if (!waiting || round > 4096) return fail(UCC_ECUDA, "persistent batch made no progress");
       UCC_TRY(sync_swaps());
-      for (int x = 0; x < n; ++x) hv[x].tape = jobs[idx[x]]->tape();
+      for (int x = 0; x < n; ++x) hv[x].tape = jobs[idx[x]]->template tape<unsigned long long>();
       CUDA_TRY(cudaMemcpyAsync(d_jobs, hv.data(), n * sizeof(JobView), cudaMemcpyHostToDevice, st));
       CUDA_TRY(cudaMemcpyAsync(d_js, hs.data(), n * sizeof(JobState), cudaMemcpyHostToDevice, st));
       UCC_TRY(reset_header(-1));
@@ -1326,17 +1390,29 @@ ucc_status ucc_create(const ucc_hamiltonian* ham, const ucc_ansatz* an, void* cu
   c->rows.assign(an->idx, an->idx + 4 * (size_t)c->K);
   c->theta.assign(c->K, 0.0);
   if (an->theta) std::copy(an->theta, an->theta + c->K, c->theta.begin());
-  c->factors.resize(c->K);
+  c->wide = c->n_so > 64;
+  c->kw = c->wide ? 2 : 1;
+  for (auto& t : c->ts) t.cur.kw = t.spare.kw = c->kw;
+  if (c->wide)
+    c->factors_w.resize(c->K);
+  else
+    c->factors.resize(c->K);
   const size_t n = (size_t)c->n_spatial;
   ucc_status s;
-  if ((s = dalloc(&c->d_factors, std::max(1, c->K))) != UCC_OK) return bail(s);
+  const size_t fbytes = c->wide ? sizeof(FactorT<Key128>) : sizeof(Factor);
+  const size_t cbytes = c->wide ? sizeof(SelectCandT<Key128>) : sizeof(SelectCand);
+  unsigned char* fb = nullptr;
+  unsigned char* cb = nullptr;
+  if ((s = dalloc(&fb, fbytes * (size_t)std::max(1, c->K))) != UCC_OK) return bail(s);
+  c->d_factors = fb;
+  if ((s = dalloc(&cb, cbytes * kSelectCandCap)) != UCC_OK) return bail(s);
+  c->d_cand = cb;
   if ((s = dalloc(&c->d_h, n * n)) != UCC_OK) return bail(s);
   if ((s = dalloc(&c->d_g, n * n * n * n)) != UCC_OK) return bail(s);
   if ((s = dalloc(&c->d_grad, std::max(1, c->K))) != UCC_OK) return bail(s);
   if ((s = c->ts[0].init()) != UCC_OK) return bail(s);
   if ((s = c->ts[1].init()) != UCC_OK) return bail(s);
   if ((s = dalloc(&c->d_sel, 1)) != UCC_OK) return bail(s);
-  if ((s = dalloc(&c->d_cand, kSelectCandCap)) != UCC_OK) return bail(s);
   if ((s = dalloc(&c->t_off, (size_t)c->K + 1)) != UCC_OK) return bail(s);
   if ((s = dalloc(&c->d_pages, kTapeMaxPages)) != UCC_OK) return bail(s);
   if ((s = dalloc(&c->d_entropy, std::max(1, c->K))) != UCC_OK) return bail(s);
@@ -1392,7 +1468,7 @@ ucc_status ucc_apply(ucc_ctx* c, double eps) {
   CUDA_TRY(cudaSetDevice(c->device));
   c->launches = 0;
   c->stats = ucc_stats{};
-  UCC_TRY(run_forward(c, eps, false));
+  UCC_TRY(c->wide ? run_forward<Key128>(c, eps, false) : run_forward<unsigned long long>(c, eps, false));
   c->stats.kernel_launches = c->launches;
   return UCC_OK;
 }
@@ -1402,7 +1478,7 @@ ucc_status ucc_energy(ucc_ctx* c, double* E, double* norm2) {
   if (!c->have_psi) return fail(UCC_ESTATE, "no wavefunction held: call ucc_apply first");
   CUDA_TRY(cudaSetDevice(c->device));
   long long before = c->launches;
-  UCC_TRY(run_energy(c, E, norm2));
+  UCC_TRY(c->wide ? run_energy<Key128>(c, E, norm2) : run_energy<unsigned long long>(c, E, norm2));
   c->stats.kernel_launches = c->launches - before;
   return UCC_OK;
 }
@@ -1410,7 +1486,8 @@ ucc_status ucc_energy(ucc_ctx* c, double* E, double* norm2) {
 ucc_status ucc_gradient(ucc_ctx* c, double eps, double* E, double* grad, int on_device) {
   if (!c) return fail(UCC_EINVAL, "null context");
   CUDA_TRY(cudaSetDevice(c->device));
-  return run_gradient(c, eps, E, grad, on_device);
+  return c->wide ? run_gradient<Key128>(c, eps, E, grad, on_device)
+                 : run_gradient<unsigned long long>(c, eps, E, grad, on_device);
 }
 
 ucc_status ucc_get_wavefunction(ucc_ctx* c, size_t cap, size_t* n, uint64_t* keys, double* amps, double* sigma,
@@ -1433,7 +1510,7 @@ ucc_status ucc_get_wavefunction(ucc_ctx* c, size_t cap, size_t* n, uint64_t* key
   double* ta = nullptr;
   double* tsig = nullptr;
   if (!on_device) {
-    UCC_TRY(dalloc(&tk, live));
+    UCC_TRY(dalloc(&tk, live * c->kw));
     UCC_TRY(dalloc(&ta, live));
     if (sigma) UCC_TRY(dalloc(&tsig, live));
     dk = tk;
@@ -1441,9 +1518,13 @@ ucc_status ucc_get_wavefunction(ucc_ctx* c, size_t cap, size_t* n, uint64_t* key
     ds = tsig;
   }
   CUDA_TRY(cudaMemsetAsync(&tab.d_cnt->new_n, 0, sizeof(unsigned long long), c->stream));
-  CUDA_TRY(launch_export(c->table(tab), live, dk, da, ds, c->full_grid(), c->stream));
+  if (c->wide)
+    CUDA_TRY(launch_export(c->template table<Key128>(tab), live, reinterpret_cast<Key128*>(dk), da, ds,
+                           c->full_grid(), c->stream));
+  else
+    CUDA_TRY(launch_export(c->template table<unsigned long long>(tab), live, dk, da, ds, c->full_grid(), c->stream));
   if (!on_device) {
-    CUDA_TRY(cudaMemcpyAsync(keys, tk, live * sizeof(uint64_t), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaMemcpyAsync(keys, tk, live * c->kw * sizeof(uint64_t), cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(cudaMemcpyAsync(amps, ta, live * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     if (sigma) CUDA_TRY(cudaMemcpyAsync(sigma, tsig, live * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   }
@@ -1490,12 +1571,18 @@ ucc_status ucc_batch_run(int n_jobs, ucc_ctx* const* jobs, double eps, double* E
     ucc_ctx* c = jobs[j];
     if (batch_capacity(c) == 0 || together.size() >= (size_t)kMaxBatchJobs) {
       if (grads && grads[j]) {
-        UCC_TRY(run_gradient(c, eps, &E[j], grads[j], 0));
+        UCC_TRY(c->wide ? run_gradient<Key128>(c, eps, &E[j], grads[j], 0)
+                        : run_gradient<unsigned long long>(c, eps, &E[j], grads[j], 0));
       } else {
         c->launches = 0;
         c->stats = ucc_stats{};
-        UCC_TRY(run_forward(c, eps, false));
-        UCC_TRY(run_energy(c, &E[j], nullptr));
+        if (c->wide) {
+          UCC_TRY(run_forward<Key128>(c, eps, false));
+          UCC_TRY(run_energy<Key128>(c, &E[j], nullptr));
+        } else {
+          UCC_TRY(run_forward<unsigned long long>(c, eps, false));
+          UCC_TRY(run_energy<unsigned long long>(c, &E[j], nullptr));
+        }
       }
     } else {
       together.push_back(j);

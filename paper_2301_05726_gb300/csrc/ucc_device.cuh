@@ -15,13 +15,12 @@ namespace cg = cooperative_groups;
 constexpr int MAX_PROBE = 1 << 14;
 
 // Home slot of a key: Fibonacci hashing (Knuth, TAOCP vol. 3, 6.4) -- the
-// top log2(slots) bits of key * 2^64/phi.  One 64-bit multiply; on the
-// workloads' determinant keys it gives the same linear-probing lengths as a
-// full 64-bit finalizer.
-constexpr unsigned long long kFibonacci = 0x9E3779B97F4A7C15ull;
-
-__device__ __forceinline__ unsigned long long home_slot(const Table& t, unsigned long long key) {
-  return (key * kFibonacci) >> t.slot_shift;
+// top log2(slots) bits of key * 2^64/phi (KeyOps::slot_hash).  One 64-bit
+// multiply per key word; on the workloads' determinant keys it gives the same
+// linear-probing lengths as a full 64-bit finalizer.
+template <class KT>
+__device__ __forceinline__ unsigned long long home_slot(const TableT<KT>& t, KT key) {
+  return KeyOps<KT>::slot_hash(key) >> t.slot_shift;
 }
 
 // Existence filter: a blocked Bloom filter of 32-bit words, 8 filter bits per
@@ -36,32 +35,55 @@ __device__ __forceinline__ unsigned long long home_slot(const Table& t, unsigned
 // probe.  Three bits in one word make collisions far rarer than one bit per
 // key at the same size (the connection probes of the energy pass are mostly
 // of absent keys).
-constexpr unsigned long long kFilterMul = 0xbf58476d1ce4e5b9ull;
-
-__device__ __forceinline__ unsigned int filter_word(const Table& t, unsigned long long h) {
+template <class TT>
+__device__ __forceinline__ unsigned int filter_word(const TT& t, unsigned long long h) {
   return (unsigned int)(h >> 32) >> t.filt_shift;  // the top log2(words) bits of h
 }
-__device__ __forceinline__ unsigned int filter_bits(const Table& t, unsigned long long h) {
+template <class TT>
+__device__ __forceinline__ unsigned int filter_bits(const TT& t, unsigned long long h) {
   // the 32 bits of h just below the word index
   const unsigned int r = __funnelshift_l((unsigned int)h, (unsigned int)(h >> 32), 32 - t.filt_shift);
   return (1u << (r >> 27)) | (1u << ((r >> 22) & 31u)) | (1u << ((r >> 17) & 31u));
 }
 // Whether filter word w holds every bit of the key with filter hash h.
-__device__ __forceinline__ bool filter_hit(const Table& t, unsigned int w, unsigned long long h) {
+template <class TT>
+__device__ __forceinline__ bool filter_hit(const TT& t, unsigned int w, unsigned long long h) {
   const unsigned int m = filter_bits(t, h);
   return (w & m) == m;
 }
 
-__device__ __forceinline__ bool filter_maybe(const Table& t, unsigned long long key) {
+template <class KT>
+__device__ __forceinline__ bool filter_maybe(const TableT<KT>& t, KT key) {
   if (!t.filt) return true;
-  const unsigned long long h = key * kFilterMul;
+  const unsigned long long h = KeyOps<KT>::filt_hash(key);
   return filter_hit(t, t.filt[filter_word(t, h)], h);
 }
 
-__device__ __forceinline__ void filter_add(const Table& t, unsigned long long key) {
+template <class KT>
+__device__ __forceinline__ void filter_add(const TableT<KT>& t, KT key) {
   if (!t.filt) return;
-  const unsigned long long h = key * kFilterMul;
+  const unsigned long long h = KeyOps<KT>::filt_hash(key);
   atomicOr(&t.filt[filter_word(t, h)], filter_bits(t, h));
+}
+
+// 16-byte compare-and-swap on a two-word key (sm_90 and later); returns the
+// previous value.  One-word keys use the 8-byte atomicCAS.
+__device__ __forceinline__ unsigned long long key_cas(unsigned long long* p, unsigned long long cmp,
+                                                      unsigned long long val) {
+  return atomicCAS(p, cmp, val);
+}
+__device__ __forceinline__ Key128 key_cas(Key128* p, Key128 cmp, Key128 val) {
+  Key128 old;
+  asm volatile(
+      "{\n\t.reg .b128 c, v, d;\n\t"
+      "mov.b128 c, {%2, %3};\n\t"
+      "mov.b128 v, {%4, %5};\n\t"
+      "atom.global.cas.b128 d, [%6], c, v;\n\t"
+      "mov.b128 {%0, %1}, d;\n\t}"
+      : "=l"(old.lo), "=l"(old.hi)
+      : "l"(cmp.lo), "l"(cmp.hi), "l"(val.lo), "l"(val.hi), "l"(p)
+      : "memory");
+  return old;
 }
 
 // A dropped entry keeps its key and slot; its amplitude becomes a quiet NaN
@@ -95,7 +117,8 @@ struct Lookup {
   double amp;                // amplitude (ALIVE)
 };
 
-__device__ __forceinline__ void classify(const Table& t, unsigned long long idx, unsigned int stamp, Lookup& r) {
+template <class TT>
+__device__ __forceinline__ void classify(const TT& t, unsigned long long idx, unsigned int stamp, Lookup& r) {
   r.idx = idx;
   double a = t.amps[idx];
   if (!is_dead(a)) {
@@ -106,8 +129,17 @@ __device__ __forceinline__ void classify(const Table& t, unsigned long long idx,
   }
 }
 
+// A lane's key broadcast from lane src.
+__device__ __forceinline__ unsigned long long shfl_key(unsigned long long k, unsigned int src) {
+  return __shfl_sync(0xFFFFFFFFu, k, src);
+}
+__device__ __forceinline__ Key128 shfl_key(Key128 k, unsigned int src) {
+  return {__shfl_sync(0xFFFFFFFFu, k.lo, src), __shfl_sync(0xFFFFFFFFu, k.hi, src)};
+}
+
 // Single-lane linear probe.
-__device__ __forceinline__ Lookup find1(const Table& t, unsigned long long key, unsigned int stamp) {
+template <class KT>
+__device__ __forceinline__ Lookup find1(const TableT<KT>& t, KT key, unsigned int stamp) {
   Lookup r;
   r.state = ABSENT;
   r.idx = 0;
@@ -118,13 +150,13 @@ __device__ __forceinline__ Lookup find1(const Table& t, unsigned long long key, 
     return r;
   }
   for (int step = 0; step < MAX_PROBE; ++step) {
-    Slot s = t.slots[h];
+    const SlotT<KT> s = t.slots[h];
     if (s.key == key) {
       r.slot = h;
       classify(t, s.idx, stamp, r);
       return r;
     }
-    if (s.key == 0ull) {
+    if (KeyOps<KT>::is_zero(s.key)) {
       r.slot = h;
       return r;
     }
@@ -138,8 +170,8 @@ __device__ __forceinline__ Lookup find1(const Table& t, unsigned long long key, 
 // Group-cooperative linear probe: the G lanes of a group read G consecutive
 // slots in one step and vote.  Every lane of the warp must call it (inactive
 // lanes pass active = false); each lane receives the result of its own query.
-template <int G>
-__device__ __forceinline__ Lookup findG(const Table& t, unsigned long long key, bool active, unsigned int stamp) {
+template <int G, class KT>
+__device__ __forceinline__ Lookup findG(const TableT<KT>& t, KT key, bool active, unsigned int stamp) {
   if constexpr (G == 1) {
     Lookup r;
     r.state = ABSENT;
@@ -160,7 +192,7 @@ __device__ __forceinline__ Lookup findG(const Table& t, unsigned long long key, 
     mine.slot = 0;
     for (int q = 0; q < G; ++q) {
       const unsigned int src = gbase + q;
-      unsigned long long qk = __shfl_sync(0xFFFFFFFFu, key, src);
+      const KT qk = shfl_key(key, src);
       bool qa = __shfl_sync(0xFFFFFFFFu, active, src);
       // Group-uniform: every lane of the group sees the same qk / qa.
       unsigned long long res_slot = 0, res_idx = 0;
@@ -175,12 +207,12 @@ __device__ __forceinline__ Lookup findG(const Table& t, unsigned long long key, 
         // All lanes of the warp run this loop in lock step (the trip count is
         // warp-uniform via the ballot below), so full-mask votes are safe.
         unsigned long long my = (h + sub) & t.slot_mask;
-        Slot s;
-        s.key = 1ull;
+        SlotT<KT> s;
+        s.key = KeyOps<KT>::bit(0);
         s.idx = 0;
         if (!decided) s = t.slots[my];
         unsigned int hit = __ballot_sync(0xFFFFFFFFu, !decided && s.key == qk) & gmask;
-        unsigned int emp = __ballot_sync(0xFFFFFFFFu, !decided && s.key == 0ull) & gmask;
+        unsigned int emp = __ballot_sync(0xFFFFFFFFu, !decided && KeyOps<KT>::is_zero(s.key)) & gmask;
         if (!decided) {
           if (hit) {
             int w = __ffs(hit) - 1;
@@ -216,17 +248,18 @@ __device__ __forceinline__ Lookup findG(const Table& t, unsigned long long key, 
 // Claim an empty slot for key, starting at the slot a failed lookup ended on.
 // Only one lane ever inserts a given key during a step, so a lost CAS means
 // another key took the slot and the probe moves on.
-__device__ __forceinline__ unsigned long long claim_slot(const Table& t, unsigned long long key,
-                                                         unsigned long long start, int site = SITE_DUP_CLAIM) {
+template <class KT>
+__device__ __forceinline__ unsigned long long claim_slot(const TableT<KT>& t, KT key, unsigned long long start,
+                                                         int site = SITE_DUP_CLAIM) {
   unsigned long long h = start & t.slot_mask;
   for (int step = 0; step < MAX_PROBE; ++step) {
-    unsigned long long prev = atomicCAS(&t.slots[h].key, 0ull, key);
-    if (prev == 0ull) {
+    const KT prev = key_cas(&t.slots[h].key, KeyOps<KT>::zero(), key);
+    if (KeyOps<KT>::is_zero(prev)) {
       filter_add(t, key);
       return h;
     }
     if (prev == key) {
-      raise_consistency(t.cnt, site, key);
+      raise_consistency(t.cnt, site, KeyOps<KT>::lo(key));
       return h;
     }
     h = (h + 1) & t.slot_mask;
@@ -246,7 +279,8 @@ __device__ __forceinline__ unsigned long long aggregated_add(unsigned long long*
 }
 
 // Append (key, amp) as a new entry and point a slot at it.
-__device__ __forceinline__ bool insert_new(const Table& t, unsigned long long key, double amp, unsigned int born,
+template <class KT>
+__device__ __forceinline__ bool insert_new(const TableT<KT>& t, KT key, double amp, unsigned int born,
                                            unsigned long long start_slot, bool with_born, bool with_lam,
                                            int site = SITE_DUP_CLAIM) {
   unsigned long long s = claim_slot(t, key, start_slot, site);
@@ -304,7 +338,8 @@ __device__ __forceinline__ bool last_block_arrive(Counters* c) {
   return last;
 }
 
-__device__ __forceinline__ TapeRec& tape_at(const Tape& tp, unsigned long long x) {
+template <class KT>
+__device__ __forceinline__ TapeRecT<KT>& tape_at(const TapeT<KT>& tp, unsigned long long x) {
   return tp.pages[x >> kTapePageBits][x & (kTapePageRecs - 1ull)];
 }
 

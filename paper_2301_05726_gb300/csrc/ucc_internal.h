@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "ucc_keys.cuh"
+
 namespace ucc {
 
 // One factor U_k of Eq. 3 as the kernels need it.  tau_k = a+_a a+_b a_j a_i.
@@ -17,18 +19,24 @@ namespace ucc {
 //                   pconst);
 //   c, s : cos(theta_k), sin(theta_k) from the host's libm;
 //   ic   : 1/cos(theta_k), used by the reverse sweep to undo a lone member.
-struct Factor {
-  unsigned long long occ, vir, pmask;
+template <class KT>
+struct FactorT {
+  KT occ, vir, pmask;
   double c, s, ic;
   int pconst, is_double;
 };
+using Factor = FactorT<unsigned long long>;
 static_assert(sizeof(Factor) == 56, "Factor layout");
 
 // Open-addressing hash slot: key 0 = empty (no valid determinant has zero
 // electrons); idx = position of the entry in the compacted arrays.
-struct __align__(16) Slot {
-  unsigned long long key, idx;
+template <class KT>
+struct __align__(16) SlotT {
+  KT key;
+  unsigned long long idx;
 };
+using Slot = SlotT<unsigned long long>;
+static_assert(sizeof(Slot) == 16 && sizeof(SlotT<Key128>) == 32, "slot layout");
 
 // Device-resident counters of one run, zeroed at reset.
 struct Counters {
@@ -74,13 +82,14 @@ enum DeviceError : int {
 };
 
 // Everything a kernel needs to address the wavefunction table.
-struct Table {
-  unsigned long long* keys;  // [cap_n] determinant keys
+template <class KT>
+struct TableT {
+  KT* keys;                  // [cap_n] determinant keys
   double* amps;              // [cap_n] amplitudes; a dropped entry holds a tagged NaN
   unsigned int* born;        // [cap_n] factor that created the entry (gradient runs)
   double* lam;               // [cap_n] adjoint vector (gradient runs)
   double* sigma;             // [cap_n] P_S H psi (energy runs)
-  Slot* slots;               // [slot_mask + 1], a power of two
+  SlotT<KT>* slots;          // [slot_mask + 1], a power of two
   unsigned long long slot_mask;
   int slot_shift;            // 64 - log2(slot_mask + 1): home slot = (key * phi64) >> slot_shift
   int filt_shift;            // 32 - log2(filter words)
@@ -90,15 +99,18 @@ struct Table {
   double* partials;          // [grid] per-block partial sums
   double* entropy;           // [K] Eq. 6 after each factor (nullptr: not recorded)
 };
+using Table = TableT<unsigned long long>;
 
 // Kill-tape record: a stored entry that fell below eps or was cut, with its
 // value just before the drop and the factor that created it.
-struct TapeRec {
-  unsigned long long key;
+template <class KT>
+struct TapeRecT {
+  KT key;
   double val;
   unsigned int born;
   unsigned int pad;
 };
+using TapeRec = TapeRecT<unsigned long long>;
 
 // The tape is paged so it can grow to tens of GB without copying: record x
 // lives in pages[x >> kTapePageBits][x & (kTapePageRecs - 1)].
@@ -106,11 +118,13 @@ constexpr int kTapePageBits = 20;
 constexpr unsigned long long kTapePageRecs = 1ull << kTapePageBits;  // 1M records, 24 MB
 constexpr int kTapeMaxPages = 65536;                                 // up to 1.6 TB
 
-struct Tape {
-  TapeRec* const* pages;     // [kTapeMaxPages] device array of page pointers
-  unsigned long long* off;   // [K + 1] tape_n at the start of factor k
-  unsigned long long cap;    // records in the allocated pages
+template <class KT>
+struct TapeT {
+  TapeRecT<KT>* const* pages;  // [kTapeMaxPages] device array of page pointers
+  unsigned long long* off;     // [K + 1] tape_n at the start of factor k
+  unsigned long long cap;      // records in the allocated pages
 };
+using Tape = TapeT<unsigned long long>;
 
 // Spatial integrals for the energy kernel.
 struct Integrals {
@@ -123,7 +137,8 @@ struct Integrals {
 // Radix-selection state of the N_MAX / N_CUT truncation.
 struct SelectState {
   unsigned long long prefix, target;          // |c| bits of the threshold, rank left inside it
-  unsigned long long key_prefix, key_target;  // key tie-break among |c| == threshold
+  unsigned long long key_prefix, key_target;  // key tie-break among |c| == threshold (low word)
+  unsigned long long key_prefix_hi;           // its high word (two-word keys)
   unsigned long long count_eq, cut_total;
   unsigned long long n_cand;                  // entries gathered into the candidate buffer
   int need_keys, pad;
@@ -131,9 +146,12 @@ struct SelectState {
 };
 
 // A candidate of the selection's last passes: |c| as its IEEE bit pattern and the key.
-struct SelectCand {
-  unsigned long long mag, key;
+template <class KT>
+struct SelectCandT {
+  unsigned long long mag;
+  KT key;
 };
+using SelectCand = SelectCandT<unsigned long long>;
 constexpr unsigned long long kSelectCandCap = 1ull << 16;  // candidates the buffer holds
 
 // A second set of table arrays of a job (same sizes as its current ones): the
@@ -199,35 +217,51 @@ constexpr unsigned long long kMaxEntries = 1ull << 31;
 constexpr unsigned int BORN_INITIAL = 0xFFFFFFFFu;  // the reference determinant
 
 // --- launch wrappers (each returns the launch's cudaError_t) ---------------
-cudaError_t launch_reset(const Table& t, unsigned long long hf, cudaStream_t st);
-cudaError_t launch_forward(const Table& t, const Factor* factors, int k, double eps, unsigned int stamp,
-                           int record, const Tape& tape, unsigned long long n_max, int probe_width, int grid,
+// The single-problem path is built for one-word keys (KT = unsigned long
+// long, up to 64 spin-orbitals) and two-word keys (KT = Key128, up to 128).
+template <class KT>
+cudaError_t launch_reset(const TableT<KT>& t, KT hf, cudaStream_t st);
+template <class KT>
+cudaError_t launch_forward(const TableT<KT>& t, const FactorT<KT>* factors, int k, double eps, unsigned int stamp,
+                           int record, const TapeT<KT>& tape, unsigned long long n_max, int probe_width, int grid,
                            cudaStream_t st);
 // The N_CUT-th entry by (|c| descending, key ascending) into sel: prefix (its |c| bits), need_keys and
 // key_prefix (the largest kept key among entries with that |c|).
-cudaError_t launch_select_threshold(const Table& t, SelectState* sel, SelectCand* cand, unsigned long long n_cut,
-                                    int grid, cudaStream_t st, long long* launches);
+template <class KT>
+cudaError_t launch_select_threshold(const TableT<KT>& t, SelectState* sel, SelectCandT<KT>* cand,
+                                    unsigned long long n_cut, int grid, cudaStream_t st, long long* launches);
 // Copy the entries the threshold keeps into `to` (live entries only, unordered, counted in new_n) and
 // record the ones it drops on the tape as factor k's (record) or account their entropy.
-cudaError_t launch_cut_compact(const Table& from, const Table& to, const SelectState* sel, int record,
-                               const Tape& tape, int k, int grid, cudaStream_t st);
-cudaError_t launch_compact(const Table& from, const Table& to, int with_born, int grid, cudaStream_t st);
-cudaError_t launch_rehash(const Table& t, int grid, cudaStream_t st);
-cudaError_t launch_finish_rebuild(const Table& t, cudaStream_t st);
-cudaError_t launch_export(const Table& t, unsigned long long cap, unsigned long long* keys, double* amps,
-                          double* sigma, int grid, cudaStream_t st);
-cudaError_t launch_sigma(const Table& t, const Integrals& in, int grid, cudaStream_t st);
-cudaError_t launch_lambda_init(const Table& t, int grid, cudaStream_t st);
-cudaError_t launch_tape_reinsert(const Table& t, const Tape& tape, int k, unsigned long long records, int grid,
-                                 cudaStream_t st, long long* launches);
-cudaError_t launch_reverse(const Table& t, const Factor* factors, int k, unsigned int stamp, double* grad,
+template <class KT>
+cudaError_t launch_cut_compact(const TableT<KT>& from, const TableT<KT>& to, const SelectState* sel, int record,
+                               const TapeT<KT>& tape, int k, int grid, cudaStream_t st);
+template <class KT>
+cudaError_t launch_compact(const TableT<KT>& from, const TableT<KT>& to, int with_born, int grid, cudaStream_t st);
+template <class KT>
+cudaError_t launch_rehash(const TableT<KT>& t, int grid, cudaStream_t st);
+template <class KT>
+cudaError_t launch_finish_rebuild(const TableT<KT>& t, cudaStream_t st);
+template <class KT>
+cudaError_t launch_export(const TableT<KT>& t, unsigned long long cap, KT* keys, double* amps, double* sigma,
+                          int grid, cudaStream_t st);
+template <class KT>
+cudaError_t launch_sigma(const TableT<KT>& t, const Integrals& in, int grid, cudaStream_t st);
+template <class KT>
+cudaError_t launch_lambda_init(const TableT<KT>& t, int grid, cudaStream_t st);
+template <class KT>
+cudaError_t launch_tape_reinsert(const TableT<KT>& t, const TapeT<KT>& tape, int k, unsigned long long records,
+                                 int grid, cudaStream_t st, long long* launches);
+template <class KT>
+cudaError_t launch_reverse(const TableT<KT>& t, const FactorT<KT>* factors, int k, unsigned int stamp, double* grad,
                            int probe_width, int grid, cudaStream_t st);
-cudaError_t launch_restore(const Table& t, const unsigned long long* keys, const double* amps, unsigned long long n,
-                           int grid, cudaStream_t st);
-cudaError_t launch_transfer_lambda(const Table& dst, const Table& src, int grid, cudaStream_t st);
-cudaError_t launch_probe_bench(const Table& t, const Factor& f, int probe_width, unsigned long long* sink, int grid,
-                               cudaStream_t st);
-int sigma_smem_bytes(int n_so);
+template <class KT>
+cudaError_t launch_restore(const TableT<KT>& t, const KT* keys, const double* amps, unsigned long long n, int grid,
+                           cudaStream_t st);
+template <class KT>
+cudaError_t launch_transfer_lambda(const TableT<KT>& dst, const TableT<KT>& src, int grid, cudaStream_t st);
+template <class KT>
+cudaError_t launch_probe_bench(const TableT<KT>& t, const FactorT<KT>& f, int probe_width, unsigned long long* sink,
+                               int grid, cudaStream_t st);
 // Batched (many-job) energy: the layout of every job's stored entries, then
 // sigma and the energy sums of every job in one launch.
 cudaError_t launch_batch_layout(const JobView* jobs, JobState* js, int n_jobs, BatchHeader* bh, cudaStream_t st);

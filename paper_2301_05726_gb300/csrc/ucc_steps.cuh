@@ -55,11 +55,12 @@ __device__ __forceinline__ double entropy_term(double c) {
   return p > 0.0 ? -p * log(p) : 0.0;
 }
 
-__device__ __forceinline__ void record_kill(const Table& t, const Tape& tape, unsigned long long key, double val,
+template <class KT>
+__device__ __forceinline__ void record_kill(const TableT<KT>& t, const TapeT<KT>& tape, KT key, double val,
                                             unsigned int born) {
   unsigned long long ti = aggregated_add(&t.cnt->tape_n);
   if (ti < tape.cap) {
-    TapeRec& rec = tape_at(tape, ti);
+    TapeRecT<KT>& rec = tape_at(tape, ti);
     rec.key = key;
     rec.val = val;
     rec.born = born;
@@ -81,8 +82,9 @@ __device__ __forceinline__ void record_kill(const Table& t, const Tape& tape, un
 // looks a created key up (its only partner is the creating entry), so the
 // slot is claimed after the step (link_appended) and the claim's round trip
 // stays off the step's critical path.
-__device__ __forceinline__ void append_unlinked(const Table& t, unsigned long long key, double amp,
-                                                unsigned int born, bool with_born) {
+template <class KT>
+__device__ __forceinline__ void append_unlinked(const TableT<KT>& t, KT key, double amp, unsigned int born,
+                                                bool with_born) {
   const unsigned long long idx = aggregated_add(&t.cnt->n_tail);
   if (idx >= t.cap_n) {
     raise_error(t.cnt, ERR_CAPACITY);
@@ -95,11 +97,12 @@ __device__ __forceinline__ void append_unlinked(const Table& t, unsigned long lo
 
 // Give appended entry idx its hash slot unless its key already has one (a
 // revived key, whose slot the step repointed).
-__device__ __forceinline__ void link_appended(const Table& t, unsigned long long key, unsigned long long idx) {
+template <class KT>
+__device__ __forceinline__ void link_appended(const TableT<KT>& t, KT key, unsigned long long idx) {
   unsigned long long h = home_slot(t, key);
   for (int step = 0; step < MAX_PROBE; ++step) {
-    const unsigned long long prev = atomicCAS(&t.slots[h].key, 0ull, key);
-    if (prev == 0ull) {
+    const KT prev = key_cas(&t.slots[h].key, KeyOps<KT>::zero(), key);
+    if (KeyOps<KT>::is_zero(prev)) {
       t.slots[h].idx = idx;
       filter_add(t, key);
       return;
@@ -112,19 +115,19 @@ __device__ __forceinline__ void link_appended(const Table& t, unsigned long long
 
 // DEFER: created entries are appended unlinked (link_appended runs after the
 // step); otherwise they are hashed at once.
-template <bool RECORD, bool DEFER = false>
-__device__ __forceinline__ void forward_resolve(const Table& t, const Factor& f, int k, double eps, unsigned int stamp,
-                                                const Tape& tape, unsigned long long i, unsigned long long X,
+template <bool RECORD, bool DEFER = false, class KT>
+__device__ __forceinline__ void forward_resolve(const TableT<KT>& t, const FactorT<KT>& f, int k, double eps,
+                                                unsigned int stamp, const TapeT<KT>& tape, unsigned long long i, KT X,
                                                 double cX, bool ex, const Lookup& r, StepCounts& sc) {
-  const unsigned long long Y = X ^ (f.occ | f.vir);
+  const KT Y = X ^ (f.occ | f.vir);
   const bool partner_live = (r.state == ALIVE);
   if (!ex && (partner_live || r.state == DEAD_NOW)) return;  // E's thread owns the pair
   if (ex && r.state == DEAD_NOW) {
     raise_consistency(t.cnt, SITE_PAIR_OWNER);
     return;
   }
-  const unsigned long long E = ex ? X : Y;
-  const int parity = (__popcll(E & f.pmask) + f.pconst) & 1;
+  const KT E = ex ? X : Y;
+  const int parity = (KeyOps<KT>::popc(E & f.pmask) + f.pconst) & 1;
   const double ss = neg_if(f.s, parity);  // s * sin(theta), exact
   const double cE = ex ? cX : 0.0;
   const double cD = ex ? (partner_live ? r.amp : 0.0) : cX;
@@ -203,25 +206,26 @@ __device__ __forceinline__ void forward_resolve(const Table& t, const Factor& f,
 // Scan half of a factor step: whether stored entry i (in_range false past the
 // end of the table) is a live member of one of the factor's linked pairs.  X
 // is its key, cX its amplitude, ex whether it is the excited member E.
-__device__ __forceinline__ bool linked_entry(const Table& t, const Factor& f, unsigned long long i, bool in_range,
-                                             unsigned long long& X, double& cX, bool& ex) {
-  X = 0ull;
+template <class KT>
+__device__ __forceinline__ bool linked_entry(const TableT<KT>& t, const FactorT<KT>& f, unsigned long long i,
+                                             bool in_range, KT& X, double& cX, bool& ex) {
+  X = KeyOps<KT>::zero();
   cX = 0.0;
   ex = false;
   if (!in_range) return false;
   X = t.keys[i];
-  const unsigned long long tX = X & (f.occ | f.vir);  // occ and vir are disjoint
+  const KT tX = X & (f.occ | f.vir);  // occ and vir are disjoint
   ex = tX == f.occ;
   if (!(ex || tX == f.vir)) return false;
   cX = t.amps[i];
   return !is_dead(cX);
 }
 
-template <int G, bool RECORD>
-__device__ __forceinline__ void forward_entry(const Table& t, const Factor& f, int k, double eps, unsigned int stamp,
-                                              const Tape& tape, unsigned long long i, bool in_range,
-                                              StepCounts& sc) {
-  unsigned long long X;
+template <int G, bool RECORD, class KT>
+__device__ __forceinline__ void forward_entry(const TableT<KT>& t, const FactorT<KT>& f, int k, double eps,
+                                              unsigned int stamp, const TapeT<KT>& tape, unsigned long long i,
+                                              bool in_range, StepCounts& sc) {
+  KT X;
   double cX;
   bool ex;
   const bool act = linked_entry(t, f, i, in_range, X, cX, ex);
@@ -238,15 +242,16 @@ __device__ __forceinline__ void forward_entry(const Table& t, const Factor& f, i
 // warp calls this.
 // The reverse step for one linked entry i (key X, live amplitude cX, ex = X
 // is the excited member) whose partner lookup is r.
-__device__ __forceinline__ void reverse_resolve(const Table& t, const Factor& f, int k, unsigned int stamp,
-                                                unsigned long long i, unsigned long long X, double cX, double muX,
-                                                bool ex, const Lookup& r, double& acc, unsigned int& pairs,
+template <class KT>
+__device__ __forceinline__ void reverse_resolve(const TableT<KT>& t, const FactorT<KT>& f, int k, unsigned int stamp,
+                                                unsigned long long i, KT X, double cX, double muX, bool ex,
+                                                const Lookup& r, double& acc, unsigned int& pairs,
                                                 unsigned int& kills) {
-  const unsigned long long Y = X ^ (f.occ | f.vir);
+  const KT Y = X ^ (f.occ | f.vir);
   const bool partner_live = (r.state == ALIVE);
   if (!ex && (partner_live || r.state == DEAD_NOW)) return;  // E's thread owns the pair
-  const unsigned long long E = ex ? X : Y;
-  const int parity = (__popcll(E & f.pmask) + f.pconst) & 1;
+  const KT E = ex ? X : Y;
+  const int parity = (KeyOps<KT>::popc(E & f.pmask) + f.pconst) & 1;
   const double ss = neg_if(f.s, parity);
   ++pairs;
   if (partner_live) {
@@ -289,11 +294,11 @@ __device__ __forceinline__ void reverse_resolve(const Table& t, const Factor& f,
   }
 }
 
-template <int G>
-__device__ __forceinline__ void reverse_entry(const Table& t, const Factor& f, int k, unsigned int stamp,
+template <int G, class KT>
+__device__ __forceinline__ void reverse_entry(const TableT<KT>& t, const FactorT<KT>& f, int k, unsigned int stamp,
                                               unsigned long long i, bool in_range, double& acc, unsigned int& pairs,
                                               unsigned int& kills) {
-  unsigned long long X;
+  KT X;
   double cX;
   bool ex;
   const bool act = linked_entry(t, f, i, in_range, X, cX, ex);
@@ -329,29 +334,30 @@ constexpr int kQueue = 64;
 constexpr unsigned int kExBit = 1u << 31;
 static_assert(kMaxEntries <= (1ull << 31), "queue indices are 31-bit");
 
-template <bool AUX>
+template <class KT, bool AUX>
 struct LinkQueueT {
   unsigned int i[kQueue];  // entry index, kExBit set for the excited member
-  unsigned long long X[kQueue];
+  KT X[kQueue];
   double c[kQueue];
   double m[AUX ? kQueue : 1];
 };
 
-template <bool AUX>
+template <class KT, bool AUX>
 struct __align__(16) ScanStageT {
-  unsigned long long X[kRound];
+  KT X[kRound];
   double c[kRound];
   double m[AUX ? kRound : 2];
 };
 
 // Per-warp shared memory of for_each_linked.
-template <bool AUX>
+template <class KT, bool AUX>
 struct LinkScratchT {
-  ScanStageT<AUX> stage[2];
-  LinkQueueT<AUX> linked;  // linked entries, before the filter test
-  LinkQueueT<AUX> probe;   // linked entries whose partner may be stored
+  ScanStageT<KT, AUX> stage[2];
+  LinkQueueT<KT, AUX> linked;  // linked entries, before the filter test
+  LinkQueueT<KT, AUX> probe;   // linked entries whose partner may be stored
 };
-using LinkScratch = LinkScratchT<false>;
+template <class KT>
+using LinkScratch = LinkScratchT<KT, false>;
 
 // Threads per block of the kernels built on for_each_linked: with four warps
 // per block, the eight blocks an SM holds at 64 registers per thread also fit
@@ -367,16 +373,18 @@ __device__ __forceinline__ void cp_async_wait_all_but_last() { asm volatile("cp.
 
 // The staged scan copies 16-byte pieces starting at even entries, so keys and
 // amps (and lam) must start on a 16-byte boundary (device allocations do).
-inline bool scan_aligned(const Table& t) {
+template <class KT>
+inline bool scan_aligned(const TableT<KT>& t) {
   return ((reinterpret_cast<uintptr_t>(t.keys) | reinterpret_cast<uintptr_t>(t.amps) |
            reinterpret_cast<uintptr_t>(t.lam)) & 15u) == 0u;
 }
 
 // Copy entries [base, min(base + kRound, n)) of keys and amps (and aux) into a
-// stage: 16-byte pieces of two entries; the piece holding entry n - 1 alone
-// copies 8 bytes (the rest zero-filled) and pieces past n are not issued.
-template <bool AUX>
-__device__ __forceinline__ void stage_round(const Table& t, const double* aux, ScanStageT<AUX>& st,
+// stage: 16-byte pieces of two entries (of one entry for two-word keys); the
+// piece holding entry n - 1 alone copies 8 bytes (the rest zero-filled) and
+// pieces past n are not issued.
+template <class KT, bool AUX>
+__device__ __forceinline__ void stage_round(const TableT<KT>& t, const double* aux, ScanStageT<KT, AUX>& st,
                                             unsigned long long base, unsigned long long n, unsigned int lane) {
 #pragma unroll
   for (int h = 0; h < kRound / 64; ++h) {
@@ -384,9 +392,17 @@ __device__ __forceinline__ void stage_round(const Table& t, const double* aux, S
     const unsigned long long g = base + (unsigned long long)e;
     if (g < n) {
       const int bytes = g + 1ull < n ? 16 : 8;
-      cp_async16(&st.X[e], t.keys + g, bytes);
+      if (sizeof(KT) == 8) cp_async16(&st.X[e], t.keys + g, bytes);
       cp_async16(&st.c[e], t.amps + g, bytes);
       if (AUX) cp_async16(&st.m[e], aux + g, bytes);
+    }
+  }
+  if (sizeof(KT) == 16) {
+#pragma unroll
+    for (int h = 0; h < kRound / 32; ++h) {
+      const int e = (int)(lane + 32u * h);
+      const unsigned long long g = base + (unsigned long long)e;
+      if (g < n) cp_async16(&st.X[e], t.keys + g, 16);
     }
   }
 }
@@ -402,9 +418,9 @@ __device__ __forceinline__ Lookup absent_lookup() {
 }
 
 // Append (i, X, c, ex, m) of the active lanes (ballot mk) to queue q at qn.
-template <bool AUX>
-__device__ __forceinline__ void enqueue(LinkQueueT<AUX>& q, int qn, unsigned int mk, unsigned int below_me, bool act,
-                                        unsigned long long i, unsigned long long X, double c, bool ex, double m) {
+template <class KT, bool AUX>
+__device__ __forceinline__ void enqueue(LinkQueueT<KT, AUX>& q, int qn, unsigned int mk, unsigned int below_me,
+                                        bool act, unsigned long long i, KT X, double c, bool ex, double m) {
   if (act) {
     const int p = qn + __popc(mk & below_me);
     q.i[p] = (unsigned int)i | (ex ? kExBit : 0u);
@@ -416,12 +432,12 @@ __device__ __forceinline__ void enqueue(LinkQueueT<AUX>& q, int qn, unsigned int
 
 // Pop the last 32 entries of a queue holding qn >= 32 into the lanes and call
 // f(i, X, c, ex, m, true).
-template <bool AUX, class F>
-__device__ __forceinline__ void drain32(LinkQueueT<AUX>& q, int& qn, unsigned int lane, F& f) {
+template <class KT, bool AUX, class F>
+__device__ __forceinline__ void drain32(LinkQueueT<KT, AUX>& q, int& qn, unsigned int lane, F& f) {
   __syncwarp();
   const int p = qn - 32 + (int)lane;
   const unsigned int qi = q.i[p];
-  const unsigned long long qX = q.X[p];
+  const KT qX = q.X[p];
   const double qc = q.c[p];
   const double qm = AUX ? q.m[p] : 0.0;
   __syncwarp();
@@ -430,12 +446,12 @@ __device__ __forceinline__ void drain32(LinkQueueT<AUX>& q, int& qn, unsigned in
 }
 
 // The qn < 32 entries left in a queue (lanes past qn inactive); empties it.
-template <bool AUX, class F>
-__device__ __forceinline__ void drain_rest(LinkQueueT<AUX>& q, int& qn, unsigned int lane, F& f) {
+template <class KT, bool AUX, class F>
+__device__ __forceinline__ void drain_rest(LinkQueueT<KT, AUX>& q, int& qn, unsigned int lane, F& f) {
   __syncwarp();
   const bool a = (int)lane < qn;
   unsigned int qi = 0u;
-  unsigned long long qX = 0ull;
+  KT qX = KeyOps<KT>::zero();
   double qc = 0.0, qm = 0.0;
   if (a) {
     qi = q.i[lane];
@@ -455,56 +471,56 @@ __device__ __forceinline__ void drain_rest(LinkQueueT<AUX>& q, int& qn, unsigned
 // pre(i, active) for lone entries (loaded together with the filter word, so a
 // lone entry waits for a single round trip) and 0 for probed ones.  Every lane
 // of the warp calls this; lone and probe are called by all lanes together.
-template <bool AUX, class Pre, class Lone, class Probe>
-__device__ __forceinline__ void for_each_linked(const Table& t, const Factor& f, unsigned long long n,
-                                                LinkScratchT<AUX>& w, const double* aux, Pre pre, Lone lone,
+template <bool AUX, class KT, class Pre, class Lone, class Probe>
+__device__ __forceinline__ void for_each_linked(const TableT<KT>& t, const FactorT<KT>& f, unsigned long long n,
+                                                LinkScratchT<KT, AUX>& w, const double* aux, Pre pre, Lone lone,
                                                 Probe probe) {
   const unsigned int lane = threadIdx.x & 31u;
   const unsigned int below_me = (1u << lane) - 1u;
   const unsigned long long warp = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const unsigned long long nwarps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
   const unsigned long long step = nwarps * (unsigned long long)kRound;
-  const unsigned long long m = f.occ | f.vir;
+  const KT m = f.occ | f.vir;
   int nl = 0, np = 0;  // warp-uniform lengths of the linked and probe queues
   // Up to 32 linked entries: the partner's filter bit sends each lane to lone
   // at once or onto the probe queue.
-  auto split = [&](unsigned long long i, unsigned long long X, double c, bool ex, double mu, bool act) {
+  auto split = [&](unsigned long long i, KT X, double c, bool ex, double mu, bool act) {
     if (!AUX) mu = pre(i, act);
     bool maybe = act;
     if (act && t.filt) {
-      const unsigned long long h = (X ^ m) * kFilterMul;
+      const unsigned long long h = KeyOps<KT>::filt_hash(X ^ m);
       maybe = filter_hit(t, t.filt[filter_word(t, h)], h);
     }
     const bool pr = act && maybe;
     const unsigned int mp = __ballot_sync(0xFFFFFFFFu, pr);
-    enqueue<AUX>(w.probe, np, mp, below_me, pr, i, X, c, ex, mu);
+    enqueue<KT, AUX>(w.probe, np, mp, below_me, pr, i, X, c, ex, mu);
     np += __popc(mp);
     lone(i, X, c, ex, mu, act && !maybe);
-    if (np >= 32) drain32<AUX>(w.probe, np, lane, probe);
+    if (np >= 32) drain32<KT, AUX>(w.probe, np, lane, probe);
   };
   unsigned long long base = warp * (unsigned long long)kRound;
-  if (base < n) stage_round<AUX>(t, aux, w.stage[0], base, n, lane);
+  if (base < n) stage_round<KT, AUX>(t, aux, w.stage[0], base, n, lane);
   cp_async_commit();
   for (int r = 0; base < n; base += step, ++r) {
     // Next round's copy into the other buffer (its last reader was round r - 1).
-    if (base + step < n) stage_round<AUX>(t, aux, w.stage[(r + 1) & 1], base + step, n, lane);
+    if (base + step < n) stage_round<KT, AUX>(t, aux, w.stage[(r + 1) & 1], base + step, n, lane);
     cp_async_commit();
     cp_async_wait_all_but_last();  // this round's copy has landed (this lane's pieces)
     __syncwarp();                  // ... and every other lane's
-    const ScanStageT<AUX>& st = w.stage[r & 1];
+    const ScanStageT<KT, AUX>& st = w.stage[r & 1];
     // Not unrolled: the body inlines the resolve paths (instruction cache).
 #pragma unroll 1
     for (int u = 0; u < kScanTiles; ++u) {
       const int e = 32 * u + (int)lane;
       const unsigned long long i = base + (unsigned long long)e;
       bool act = false, ex = false;
-      unsigned long long X = 0ull;
+      KT X = KeyOps<KT>::zero();
       double cX = 0.0, mu = 0.0;
       if (i < n) {
         X = st.X[e];
         // occ and vir are disjoint: E holds exactly occ of the factor's
         // orbitals, D exactly vir
-        const unsigned long long tX = X & m;
+        const KT tX = X & m;
         ex = tX == f.occ;
         if (ex || tX == f.vir) {
           cX = st.c[e];
@@ -513,22 +529,16 @@ __device__ __forceinline__ void for_each_linked(const Table& t, const Factor& f,
         }
       }
       const unsigned int ml = __ballot_sync(0xFFFFFFFFu, act);
-      enqueue<AUX>(w.linked, nl, ml, below_me, act, i, X, cX, ex, mu);
+      enqueue<KT, AUX>(w.linked, nl, ml, below_me, act, i, X, cX, ex, mu);
       nl += __popc(ml);
-      if (nl >= 32) drain32<AUX>(w.linked, nl, lane, split);
+      if (nl >= 32) drain32<KT, AUX>(w.linked, nl, lane, split);
     }
     __syncwarp();  // every lane is done with this buffer before it is refilled
   }
   asm volatile("cp.async.wait_all;\n" ::: "memory");  // nothing left in flight
-  if (nl > 0) drain_rest<AUX>(w.linked, nl, lane, split);
-  if (np > 0) drain_rest<AUX>(w.probe, np, lane, probe);
+  if (nl > 0) drain_rest<KT, AUX>(w.linked, nl, lane, split);
+  if (np > 0) drain_rest<KT, AUX>(w.probe, np, lane, probe);
 }
-
-constexpr int kMaxSpin = 32;                          // spin-orbitals of one spin
-constexpr int kMaxPairs = kMaxSpin * (kMaxSpin - 1) / 2;  // same-spin empty pairs
-
-
-__device__ __forceinline__ unsigned long long below(int p) { return (1ull << p) - 1ull; }
 
 // (ab|cd) in chemist notation over spatial orbitals.
 __device__ __forceinline__ double chem(const Integrals& in, int a, int b, int c, int d) {
@@ -550,28 +560,30 @@ __device__ __forceinline__ double h_so(const Integrals& in, int p, int q) {
 }
 
 // Sign of a+_r a+_s a_q a_p |I> (p, q occupied; r, s empty; all distinct).
-__device__ __forceinline__ int double_parity(unsigned long long I, int p, int q, int r, int s) {
-  const unsigned long long msk = below(p) ^ below(q) ^ below(r) ^ below(s);
-  return (__popcll(I & msk) + (p < q) + (p < s) + (q < s) + (p < r) + (q < r) + (s < r)) & 1;
+template <class KT>
+__device__ __forceinline__ int double_parity(KT I, int p, int q, int r, int s) {
+  using K = KeyOps<KT>;
+  const KT msk = K::below(p) ^ K::below(q) ^ K::below(r) ^ K::below(s);
+  return (K::popc(I & msk) + (p < q) + (p < s) + (q < s) + (p < r) + (q < r) + (s < r)) & 1;
 }
 
 // Sign of a+_r a_p |I>.
-__device__ __forceinline__ int single_parity(unsigned long long I, int p, int r) {
-  return (__popcll(I & (below(p) ^ below(r))) + (p < r)) & 1;
+template <class KT>
+__device__ __forceinline__ int single_parity(KT I, int p, int r) {
+  using K = KeyOps<KT>;
+  return (K::popc(I & (K::below(p) ^ K::below(r))) + (p < r)) & 1;
 }
-
-
 
 // Connections a lane tests per round of the energy pass (filter words in flight).
 constexpr int kV = 2;
 
 // Slot probe for a key the filter did not exclude: whether it is stored and
 // live, with its amplitude and entry index.
-__device__ __forceinline__ bool probe_live_at(const Table& t, unsigned long long key, double* amp,
-                                              unsigned long long* idx) {
+template <class KT>
+__device__ __forceinline__ bool probe_live_at(const TableT<KT>& t, KT key, double* amp, unsigned long long* idx) {
   unsigned long long h = home_slot(t, key);
   for (int step = 0; step < MAX_PROBE; ++step) {
-    const Slot s = t.slots[h];
+    const SlotT<KT> s = t.slots[h];
     if (s.key == key) {
       const double a = t.amps[s.idx];
       if (is_dead(a)) return false;
@@ -579,46 +591,45 @@ __device__ __forceinline__ bool probe_live_at(const Table& t, unsigned long long
       *idx = s.idx;
       return true;
     }
-    if (s.key == 0ull) return false;
+    if (KeyOps<KT>::is_zero(s.key)) return false;
     h = (h + 1) & t.slot_mask;
   }
   raise_error(t.cnt, ERR_PROBE_BOUND);
   return false;
 }
 
-// Spin-orbital p has spin p & 1: alpha on even bits, beta on odd bits.
-constexpr unsigned long long kAlphaBits = 0x5555555555555555ull;
-constexpr unsigned long long kBetaBits = 0xAAAAAAAAAAAAAAAAull;
-
-// Per-warp lists of one determinant I for the lower-triangle sigma.
+// Per-warp lists of one determinant I for the lower-triangle sigma; NS =
+// spin-orbitals of one spin a key holds.  Spin-orbital p has spin p & 1.
+template <class KT>
 struct LowerLists {
-  unsigned char occ[2][kMaxSpin];
-  unsigned char emp[2][kMaxSpin];
+  static constexpr int NS = KeyOps<KT>::kBits / 2;
+  static constexpr int kPairs = NS * (NS - 1) / 2;
+  unsigned char occ[2][NS];
+  unsigned char emp[2][NS];
   int n_occ[2], n_emp[2];
-  unsigned short pairs[2][kMaxPairs];       // same-spin empty pairs (r | s << 8), r < s, ordered by s
-  unsigned short opp[kMaxSpin * kMaxSpin];  // (r alpha | s beta << 8), ordered by max(r, s)
-  unsigned long long hitJ[32 * (kV + 1)];   // connections whose filter word holds all their bits
-  unsigned int hitCode[32 * (kV + 1)];      // and their excitation (connection_code)
-  unsigned long long mulBit[64];            // kFilterMul * 2^x: filter-hash term of spin-orbital x
+  unsigned short pairs[2][kPairs];      // same-spin empty pairs (r | s << 8), r < s, ordered by s
+  unsigned short opp[NS * NS];          // (r alpha | s beta << 8), ordered by max(r, s)
+  KT hitJ[32 * (kV + 1)];               // connections whose filter word holds all their bits
+  unsigned int hitCode[32 * (kV + 1)];  // and their excitation (connection_code)
+  unsigned long long mulBit[2 * NS];    // filter-hash term of spin-orbital x
 };
 
-// An excitation of I packed in 26 bits: kind (0 single p -> r, 1 double
-// p, q -> r, s) and the four spin-orbital indices.
+// An excitation of I packed in 30 bits: kind (0 single p -> r, 1 double
+// p, q -> r, s) and the four spin-orbital indices, 7 bits each.
 __device__ __forceinline__ unsigned int connection_code(int kind, int p, int q, int r, int s) {
-  return (unsigned int)kind | ((unsigned int)p << 2) | ((unsigned int)q << 8) | ((unsigned int)r << 14) |
-         ((unsigned int)s << 20);
+  return (unsigned int)kind | ((unsigned int)p << 2) | ((unsigned int)q << 9) | ((unsigned int)r << 16) |
+         ((unsigned int)s << 23);
 }
 
 // The connections J < I of the lower-triangle energy pass, with the warp in
 // lock step (count is warp-uniform): the lanes test kV filter words each and
 // queue the connections whose word holds all their bits (hash_of(u) gives
-// J's filter hash J * kFilterMul, key_of(u) J itself, code_of(u) its
-// excitation); whenever 32 or more are queued after a round, resolve_hits
-// takes them 32 at a time, so the slot probes of rare hits run on full warps
-// instead of stalling the loop once per hit.  The queue holds fewer than 32
-// between rounds.
-template <class HashOf, class KeyOf, class CodeOf, class Resolve>
-__device__ __forceinline__ void probe_lower(const Table& t, LowerLists& L, int& qn, int count, int lane,
+// J's filter hash, key_of(u) J itself, code_of(u) its excitation); whenever
+// 32 or more are queued after a round, resolve_hits takes them 32 at a time,
+// so the slot probes of rare hits run on full warps instead of stalling the
+// loop once per hit.  The queue holds fewer than 32 between rounds.
+template <class KT, class HashOf, class KeyOf, class CodeOf, class Resolve>
+__device__ __forceinline__ void probe_lower(const TableT<KT>& t, LowerLists<KT>& L, int& qn, int count, int lane,
                                             HashOf hash_of, KeyOf key_of, CodeOf code_of, Resolve resolve_hits,
                                             unsigned long long& probes) {
   const unsigned int below_me = (1u << lane) - 1u;
@@ -661,27 +672,30 @@ __device__ __forceinline__ void probe_lower(const Table& t, LowerLists& L, int& 
 // highest changed spin-orbital is a hole, max(P) > max(Q), so every list
 // below is cut to a prefix by counting the empty orbitals under max(P): no
 // connection J > I is generated.  Every lane of the warp calls this.
-__device__ __forceinline__ double sigma_lower(const Table& t, const Integrals& in, LowerLists& L,
-                                              unsigned long long I, double cI, int lane, double& diag,
-                                              unsigned long long& probes, unsigned long long& hits) {
-  const unsigned long long all = in.n_so >= 64 ? ~0ull : ((1ull << in.n_so) - 1ull);
-  const unsigned long long emask = ~I & all;
+template <class KT>
+__device__ __forceinline__ double sigma_lower(const TableT<KT>& t, const Integrals& in, LowerLists<KT>& L, KT I,
+                                              double cI, int lane, double& diag, unsigned long long& probes,
+                                              unsigned long long& hits) {
+  using K = KeyOps<KT>;
+  const KT alpha = K::alpha(), beta = ~K::alpha();
+  const KT all = K::below(in.n_so);
+  const KT emask = ~I & all;
   // empty spin-orbitals of spin sp below orbital m
-  auto empty_below = [&](int sp, int m) { return __popcll(emask & (sp ? kBetaBits : kAlphaBits) & below(m)); };
+  auto empty_below = [&](int sp, int m) { return K::popc(emask & (sp ? beta : alpha) & K::below(m)); };
   // Occupied and empty lists by spin, ascending: lanes over the orbitals, each
   // placed at the count of same-kind, same-spin orbitals below it.
   for (int p = lane; p < in.n_so; p += 32) {
     const int sp = p & 1;
-    const unsigned long long spin = sp ? kBetaBits : kAlphaBits;
-    if ((I >> p) & 1ull)
-      L.occ[sp][__popcll(I & spin & below(p))] = (unsigned char)p;
+    const KT spin = sp ? beta : alpha;
+    if (K::test(I, p))
+      L.occ[sp][K::popc(I & spin & K::below(p))] = (unsigned char)p;
     else
-      L.emp[sp][__popcll(emask & spin & below(p))] = (unsigned char)p;
+      L.emp[sp][K::popc(emask & spin & K::below(p))] = (unsigned char)p;
   }
   if (lane < 2) {
-    const unsigned long long spin = lane ? kBetaBits : kAlphaBits;
-    L.n_occ[lane] = __popcll(I & all & spin);
-    L.n_emp[lane] = __popcll(emask & spin);
+    const KT spin = lane ? beta : alpha;
+    L.n_occ[lane] = K::popc(I & all & spin);
+    L.n_emp[lane] = K::popc(emask & spin);
   }
   __syncwarp();
   for (int sp = 0; sp < 2; ++sp) {
@@ -697,13 +711,13 @@ __device__ __forceinline__ double sigma_lower(const Table& t, const Integrals& i
     }
   }
   // Filter-hash terms: J = (I with the holes cleared) + 2^r + 2^s exactly (the
-  // particles are empty in I), so J * kFilterMul = base + mulBit[r] + mulBit[s]
+  // particles are empty in I), so hash(J) = base + mulBit[r] + mulBit[s]
   // modulo 2^64, with one base per hole set.
-  for (int x = lane; x < 64; x += 32) L.mulBit[x] = kFilterMul << x;
+  for (int x = lane; x < 2 * LowerLists<KT>::NS; x += 32) L.mulBit[x] = K::filt_bit(x);
   // Opposite-spin empty pairs grouped by their larger orbital o: the pairs
   // with max < o number (alpha empties below o) * (beta empties below o).
   for (int o = lane; o < in.n_so; o += 32) {
-    if (!((emask >> o) & 1ull)) continue;
+    if (!K::test(emask, o)) continue;
     const int ra = empty_below(0, o), sb = empty_below(1, o);
     const int st = ra * sb;
     if ((o & 1) == 0) {
@@ -732,7 +746,7 @@ __device__ __forceinline__ double sigma_lower(const Table& t, const Integrals& i
   int qn = 0;  // warp-uniform length of the hit queue
   // <J|H|I> for the queued excitation code of J = tau I.
   auto elem = [&](unsigned int code) {
-    const int p = (code >> 2) & 63, q = (code >> 8) & 63, r = (code >> 14) & 63, s = (code >> 20) & 63;
+    const int p = (code >> 2) & 127, q = (code >> 9) & 127, r = (code >> 16) & 127, s = (code >> 23) & 127;
     if ((code & 3u) == 0u) {
       double v = h_so(in, r, p);
       for (int sk = 0; sk < 2; ++sk)
@@ -751,7 +765,7 @@ __device__ __forceinline__ double sigma_lower(const Table& t, const Integrals& i
     __syncwarp();
     const bool a = lane < take;
     const int pidx = qn - take + lane;
-    const unsigned long long J = a ? L.hitJ[pidx] : 0ull;
+    const KT J = a ? L.hitJ[pidx] : K::zero();
     const unsigned int code = a ? L.hitCode[pidx] : 0u;
     __syncwarp();
     qn -= take;
@@ -768,10 +782,10 @@ __device__ __forceinline__ double sigma_lower(const Table& t, const Integrals& i
   for (int sp = 0; sp < 2; ++sp)
     for (int x = 0; x < L.n_occ[sp]; ++x) {
       const int p = L.occ[sp][x];
-      const unsigned long long base = (I ^ (1ull << p)) * kFilterMul;
+      const unsigned long long base = K::filt_hash(I ^ K::bit(p));
       probe_lower(
           t, L, qn, empty_below(sp, p), lane, [&](int u) { return base + L.mulBit[L.emp[sp][u]]; },
-          [&](int u) { return I ^ ((1ull << p) | (1ull << L.emp[sp][u])); },
+          [&](int u) { return I ^ (K::bit(p) | K::bit(L.emp[sp][u])); },
           [&](int u) { return connection_code(0, p, 0, L.emp[sp][u], 0); }, resolve_hits, probes);
     }
   // Doubles, same spin: holes p < q, particles r < s < q.
@@ -780,8 +794,8 @@ __device__ __forceinline__ double sigma_lower(const Table& t, const Integrals& i
     for (int x = 0; x < no; ++x)
       for (int y = x + 1; y < no; ++y) {
         const int p = L.occ[sp][x], q = L.occ[sp][y];
-        const unsigned long long hole = (1ull << p) | (1ull << q);
-        const unsigned long long base = (I ^ hole) * kFilterMul;
+        const KT hole = K::bit(p) | K::bit(q);
+        const unsigned long long base = K::filt_hash(I ^ hole);
         const int y0 = empty_below(sp, q);
         probe_lower(
             t, L, qn, y0 * (y0 - 1) / 2, lane,
@@ -791,7 +805,7 @@ __device__ __forceinline__ double sigma_lower(const Table& t, const Integrals& i
             },
             [&](int u) {
               const unsigned short pr = L.pairs[sp][u];
-              return I ^ (hole | (1ull << (pr & 0xFF)) | (1ull << (pr >> 8)));
+              return I ^ (hole | K::bit(pr & 0xFF) | K::bit(pr >> 8));
             },
             [&](int u) {
               const unsigned short pr = L.pairs[sp][u];
@@ -806,8 +820,8 @@ __device__ __forceinline__ double sigma_lower(const Table& t, const Integrals& i
     for (int y = 0; y < L.n_occ[1]; ++y) {
       const int p = L.occ[0][x], q = L.occ[1][y];
       const int m = p > q ? p : q;
-      const unsigned long long hole = (1ull << p) | (1ull << q);
-      const unsigned long long base = (I ^ hole) * kFilterMul;
+      const KT hole = K::bit(p) | K::bit(q);
+      const unsigned long long base = K::filt_hash(I ^ hole);
       probe_lower(
           t, L, qn, empty_below(0, m) * empty_below(1, m), lane,
           [&](int u) {
@@ -816,7 +830,7 @@ __device__ __forceinline__ double sigma_lower(const Table& t, const Integrals& i
           },
           [&](int u) {
             const unsigned short pr = L.opp[u];
-            return I ^ (hole | (1ull << (pr & 0xFF)) | (1ull << (pr >> 8)));
+            return I ^ (hole | K::bit(pr & 0xFF) | K::bit(pr >> 8));
           },
           [&](int u) {
             const unsigned short pr = L.opp[u];

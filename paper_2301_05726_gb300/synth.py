@@ -10,7 +10,8 @@ over spin-orbitals, and one angle theta per factor of Eq. 3.
 Conventions shared by every consumer of these inputs:
 
 * spin-orbital index p = 2*spatial + spin (spin 0 = alpha, 1 = beta), so the
-  Jordan-Wigner qubit of spin-orbital p is bit p of a 64-bit determinant key;
+  Jordan-Wigner qubit of spin-orbital p is bit p of the determinant key (one
+  64-bit word up to 64 spin-orbitals, two words up to 128);
 * the reference determinant occupies spatial orbitals 0..n_alpha-1 (alpha) and
   0..n_beta-1 (beta);
 * an excitation row (i, j, a, b) stands for tau = a+_a a+_b a_j a_i (a single
@@ -169,8 +170,8 @@ def make_problem(seed: int, n_spatial: int, n_alpha: int, n_beta: int, sigma_the
     (singles, then doubles), then order and truncate the factor list."""
     if not (0 < n_alpha <= n_spatial and 0 < n_beta <= n_spatial):
         raise ValueError("electron counts out of range")
-    if 2 * n_spatial > 64:
-        raise ValueError("at most 64 spin-orbitals (64-bit determinant keys)")
+    if 2 * n_spatial > 128:
+        raise ValueError("at most 128 spin-orbitals (two-word determinant keys)")
     rng = np.random.default_rng(seed)
     h, g = make_integrals(rng, n_spatial)
     s, d = enumerate_excitations(n_spatial, n_alpha, n_beta)

@@ -77,7 +77,8 @@ def test_validation_rejects_too_many_orbitals(lib):
     from paper_2301_05726_gb300._lib import UCC_EINVAL
     prob = synth.config_problem(1)
     import dataclasses
-    big = dataclasses.replace(prob, n_spatial=33, h=np.zeros((33, 33)), g=np.zeros((33,) * 4))
+    # up to 64 spatial orbitals (two-word keys); 65 is refused before any device call
+    big = dataclasses.replace(prob, n_spatial=65, h=np.zeros((65, 65)), g=np.zeros((65,) * 4))
     st, _, msg = _create(lib, big)
     assert st == UCC_EINVAL and "n_spatial" in msg
 
