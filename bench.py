@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--n1-fd-components", type=int, default=2)
     ap.add_argument("--n1-batch", type=int, default=2, help="theta vectors in the 40-spin-orbital batched leg")
     ap.add_argument("--no-batch", action="store_true", help="skip the 256-job batched leg")
+    ap.add_argument("--no-wide", action="store_true", help="skip the 72-spin-orbital leg")
     return ap.parse_args()
 
 
@@ -430,6 +431,28 @@ def batch_leg(args):
 BATCH_N_MAX, BATCH_N_CUT = 8000, 5000
 
 
+def wide_leg(args):
+    """A 72-spin-orbital problem shaped like the paper's CH2O/cc-pVDZ frozen-core case (36 spatial orbitals,
+    12 electrons, the 5,000 largest doubles and all singles, the production cut N_MAX = 8,000 / N_CUT =
+    5,000, eps = 1e-8): two-word determinant keys.  One full evaluation (apply, energy, adjoint)."""
+    import torch
+    from paper_2301_05726_gb300 import synth
+    from paper_2301_05726_gb300.api import UCCContext
+    p = synth.make_problem(7200, 36, 6, 6, 0.02, eps=1e-8, m_doubles=5000, name="72so_12e_md5000_cut8000")
+    p.n_max, p.n_cut = BATCH_N_MAX, BATCH_N_CUT
+    ctx = UCCContext(p)
+    ctx.gradient()  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    E, _ = ctx.gradient()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    st = ctx.stats()
+    ctx.close()
+    return {"workload": p.name, "n_so": p.n_so, "n_elec": p.n_elec, "n_factors": p.n_exc, "key_words": 2,
+            "eval_s": dt, "det_rotations_per_s": st["rotations"] / dt, "n_det": st["n_det"], "cut": st["cut"]}
+
+
 def run_ours(args, prob):
     import numpy as np
     import torch
@@ -520,6 +543,9 @@ def run_ours(args, prob):
     batched = None
     if rank == 0 and not args.no_batch:
         batched = batch_leg(args)
+    wide = None
+    if rank == 0 and not args.no_wide:
+        wide = wide_leg(args)
 
     if rank != 0:
         if world > 1:
@@ -558,6 +584,7 @@ def run_ours(args, prob):
         "vs_plain": plain,
         "n1_40so": n1,
         "batched": batched,
+        "wide_72so": wide,
         "e2e": {"value": rot_all / (e2e_ms / 1e3), "unit": UNIT, "steps": len(e2e_times),
                 "h2d_bytes_per_step": FACTOR_BYTES * prob.n_exc, "d2h_bytes_per_step": 8 * prob.n_exc + 8},
         "gpu_launches": int(tot["kernel_launches"]),
