@@ -27,6 +27,12 @@ template <class KT>
 __host__ __device__ constexpr int sigma_warps() {
   return sizeof(KT) == 8 ? 8 : 2;
 }
+// Blocks per SM that the lists allow (47 KB a block for one-word keys, 39 KB
+// for two-word ones, of 228 KB); the register budget is held to match.
+template <class KT>
+__host__ __device__ constexpr int sigma_min_blocks() {
+  return sizeof(KT) == 8 ? 4 : 5;
+}
 // sigma[0, n_tail) = 0 before the lower-triangle pass accumulates into it.
 template <class KT>
 __global__ void __launch_bounds__(256) k_sigma_zero(TableT<KT> t) {
@@ -37,7 +43,7 @@ __global__ void __launch_bounds__(256) k_sigma_zero(TableT<KT> t) {
 }
 
 template <class KT>
-__global__ void __launch_bounds__(sigma_warps<KT>() * 32) k_sigma(TableT<KT> t, Integrals in) {
+__global__ void __launch_bounds__(sigma_warps<KT>() * 32, sigma_min_blocks<KT>()) k_sigma(TableT<KT> t, Integrals in) {
   constexpr int kWarps = sigma_warps<KT>();
   __shared__ LowerLists<KT> lists[kWarps];
   const int w = threadIdx.x >> 5;

@@ -240,40 +240,6 @@ __global__ void __launch_bounds__(kFinishThreads) k_select_finish(TableT<KT> t, 
   }
 }
 
-// Exclusive prefix over the block of two per-thread counts (each < 2^16),
-// packed as a + (b << 16), with one atomicAdd per count on the global
-// counters ca and cb: returns this thread's first position for each.
-__device__ __forceinline__ void block_reserve2(unsigned int a, unsigned int b, unsigned long long* ca,
-                                               unsigned long long* cb, unsigned long long& pa,
-                                               unsigned long long& pb) {
-  __shared__ unsigned int s_w[kThreads / 32];
-  __shared__ unsigned long long s_base[2];
-  const unsigned int lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
-  const unsigned int v = a | (b << 16);
-  unsigned int incl = v;
-  for (int o = 1; o < 32; o <<= 1) {
-    const unsigned int y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-    if ((int)lane >= o) incl += y;
-  }
-  if (lane == 31) s_w[w] = incl;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned int run = 0;
-    for (int x = 0; x < kThreads / 32; ++x) {
-      const unsigned int t = s_w[x];
-      s_w[x] = run;
-      run += t;
-    }
-    s_base[0] = (run & 0xFFFFu) ? atomicAdd(ca, (unsigned long long)(run & 0xFFFFu)) : 0ull;
-    s_base[1] = (run >> 16) ? atomicAdd(cb, (unsigned long long)(run >> 16)) : 0ull;
-  }
-  __syncthreads();
-  const unsigned int excl = s_w[w] + incl - v;
-  pa = s_base[0] + (excl & 0xFFFFu);
-  pb = s_base[1] + (excl >> 16);
-  __syncthreads();  // s_w and s_base are reused by the next call
-}
-
 // The cut fused with the compaction that follows it.  Each block takes tiles
 // of 4 x kThreads entries; a live entry above the threshold (|c| > T, or
 // |c| == T and key <= key threshold when ties are broken) goes to the spare
@@ -313,37 +279,74 @@ __global__ void __launch_bounds__(kThreads) k_cut_compact(TableT<KT> from, Table
       nk += keep;
       nd += !keep;
     }
-    unsigned long long pk, pd;
-    block_reserve2(nk, RECORD ? nd : 0u, &from.cnt->new_n, &from.cnt->tape_n, pk, pd);
+    // Places: per tile one reservation per counter for the block; inside it
+    // the warps in order, and inside a warp tile u after tile u - 1 with the
+    // lanes in order, so a warp's kept entries (and tape records) of one tile
+    // land next to each other (coalesced stores).
+    unsigned int mk[kPer], md[kPer], wk = 0, wd = 0;
 #pragma unroll
     for (int u = 0; u < kPer; ++u) {
-      if (state[u] == 0) continue;
+      mk[u] = __ballot_sync(0xFFFFFFFFu, state[u] == 1);
+      md[u] = __ballot_sync(0xFFFFFFFFu, state[u] == 2);
+      wk += __popc(mk[u]);
+      wd += __popc(md[u]);
+    }
+    (void)nk;
+    (void)nd;
+    __shared__ unsigned int s_wk[kThreads / 32], s_wd[kThreads / 32];
+    __shared__ unsigned long long s_bk, s_bd;
+    const unsigned int lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
+    const unsigned int below_me = (1u << lane) - 1u;
+    if (lane == 0) {
+      s_wk[w] = wk;
+      s_wd[w] = wd;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned int rk = 0, rd = 0;
+      for (int x = 0; x < kThreads / 32; ++x) {
+        const unsigned int a = s_wk[x], b = s_wd[x];
+        s_wk[x] = rk;
+        s_wd[x] = rd;
+        rk += a;
+        rd += b;
+      }
+      s_bk = rk ? atomicAdd(&from.cnt->new_n, (unsigned long long)rk) : 0ull;
+      s_bd = (RECORD && rd) ? atomicAdd(&from.cnt->tape_n, (unsigned long long)rd) : 0ull;
+    }
+    __syncthreads();
+    unsigned long long pk = s_bk + s_wk[w], pd = s_bd + s_wd[w];
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
       const unsigned long long i = base + (unsigned long long)u * kThreads + threadIdx.x;
       if (state[u] == 1) {
-        if (pk < to.cap_n) {
-          to.keys[pk] = key[u];
-          to.amps[pk] = a[u];
-          if (to.born) to.born[pk] = from.born[i];
+        const unsigned long long at = pk + __popc(mk[u] & below_me);
+        if (at < to.cap_n) {
+          to.keys[at] = key[u];
+          to.amps[at] = a[u];
+          if (to.born) to.born[at] = from.born[i];
         } else {
           raise_error(from.cnt, ERR_CAPACITY);
         }
-        ++pk;
-      } else {
+      } else if (state[u] == 2) {
         ++dropped;
         if (from.entropy) dS -= entropy_term(a[u]);
         if (RECORD) {
-          if (pd < tape.cap) {
-            TapeRecT<KT>& rec = tape_at(tape, pd);
+          const unsigned long long at = pd + __popc(md[u] & below_me);
+          if (at < tape.cap) {
+            TapeRecT<KT>& rec = tape_at(tape, at);
             rec.key = key[u];
             rec.val = a[u];
             rec.born = from.born[i];
           } else {
             raise_error(from.cnt, ERR_TAPE_FULL);
           }
-          ++pd;
         }
       }
+      pk += __popc(mk[u]);
+      pd += __popc(md[u]);
     }
+    __syncthreads();  // s_wk, s_wd, s_bk, s_bd are reused by the next tile
   }
   __shared__ unsigned long long s_d;
   if (threadIdx.x == 0) s_d = 0;

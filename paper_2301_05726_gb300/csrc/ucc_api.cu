@@ -116,14 +116,26 @@ struct TableSet {
   Arrays cur, spare;
   Counters* d_cnt = nullptr;
   Counters* h_cnt = nullptr;
+  // The spare's slot array and filter are cleared on a side stream right
+  // after it is swapped out, overlapping the factor steps that follow; the
+  // next rebuild waits for `clean` instead of clearing on the main stream.
+  cudaEvent_t clean = nullptr;
+  bool clean_pending = false;
   void release() {
     cur.release();
     spare.release();
     dfree(d_cnt);
     if (h_cnt) cudaFreeHost(h_cnt);
     h_cnt = nullptr;
+    if (clean) cudaEventDestroy(clean);
+    clean = nullptr;
+    clean_pending = false;
   }
   ucc_status init() {
+    if (cudaEventCreateWithFlags(&clean, cudaEventDisableTiming) != cudaSuccess) {
+      clean = nullptr;
+      return fail(UCC_ECUDA, "event creation failed");
+    }
     UCC_TRY(dalloc(&d_cnt, 1));
     if (cudaMallocHost((void**)&h_cnt, sizeof(Counters)) != cudaSuccess) {
       h_cnt = nullptr;
@@ -153,6 +165,7 @@ struct ucc_ctx {
   int device = 0;
   int num_sms = 1;
   cudaStream_t stream = nullptr;
+  cudaStream_t side = nullptr;   // clears spare hash arrays off the critical path
   int n_spatial = 0, n_alpha = 0, n_beta = 0, n_so = 0;
   double e_nuc = 0.0;
   int K = 0;
@@ -304,8 +317,17 @@ ucc_status prepare_spare(ucc_ctx* c, TableSet& s, unsigned long long new_cap, Ta
     return fail(UCC_ECAPACITY, "the wavefunction needs more than 2^31 stored entries (" + std::to_string(new_cap) +
                                    ")");
   unsigned long long ns = slots_for(new_cap);
+  bool cleared = false;
+  if (s.clean_pending) {
+    // the side stream's clearing of these arrays must finish first (also when
+    // they are released below: their memory may be handed out again)
+    CUDA_TRY(cudaStreamWaitEvent(c->stream, s.clean, 0));
+    s.clean_pending = false;
+    cleared = true;
+  }
   if (s.spare.cap_n != new_cap || s.spare.n_slots != ns) {
     s.spare.release();
+    cleared = false;
     ucc_status st = s.spare.allocate(new_cap, ns);
     if (st != UCC_OK) {
       s.spare.release();
@@ -325,9 +347,32 @@ ucc_status prepare_spare(ucc_ctx* c, TableSet& s, unsigned long long new_cap, Ta
   to.filt_shift = 32 - (__builtin_ctzll(ns) - 2);
   to.cap_n = new_cap;
   CUDA_TRY(cudaMemsetAsync(&s.d_cnt->new_n, 0, sizeof(unsigned long long), c->stream));
-  CUDA_TRY(cudaMemsetAsync(to.slots, 0, ns * sizeof(SlotT<KT>), c->stream));
-  CUDA_TRY(cudaMemsetAsync(to.filt, 0, ns / 4 * sizeof(unsigned int), c->stream));
+  if (!cleared) {
+    CUDA_TRY(cudaMemsetAsync(to.slots, 0, ns * sizeof(SlotT<KT>), c->stream));
+    CUDA_TRY(cudaMemsetAsync(to.filt, 0, ns / 4 * sizeof(unsigned int), c->stream));
+  }
   *out = to;
+  return UCC_OK;
+}
+
+// After a swap: clear the arrays just swapped out (the new spare) on the side
+// stream once the main stream has finished with them.
+ucc_status clear_spare_async(ucc_ctx* c, TableSet& s) {
+  if (!c->side || s.spare.cap_n == 0) return UCC_OK;
+  CUDA_TRY(cudaEventRecord(s.clean, c->stream));
+  CUDA_TRY(cudaStreamWaitEvent(c->side, s.clean, 0));
+  CUDA_TRY(cudaMemsetAsync(s.spare.slots, 0, s.spare.n_slots * s.spare.kw * sizeof(Slot), c->side));
+  CUDA_TRY(cudaMemsetAsync(s.spare.filt, 0, s.spare.n_slots / 4 * sizeof(unsigned int), c->side));
+  CUDA_TRY(cudaEventRecord(s.clean, c->side));
+  s.clean_pending = true;
+  return UCC_OK;
+}
+
+// Wait (on the main stream) for a pending side-stream clearing of the spare.
+ucc_status settle_spare(ucc_ctx* c, TableSet& s) {
+  if (!s.clean_pending) return UCC_OK;
+  CUDA_TRY(cudaStreamWaitEvent(c->stream, s.clean, 0));
+  s.clean_pending = false;
   return UCC_OK;
 }
 
@@ -340,7 +385,10 @@ ucc_status finish_rebuild(ucc_ctx* c, TableSet& s, const TableT<KT>& to) {
   c->launches += 2;
   std::swap(s.cur, s.spare);
   // After growth the old, smaller arrays are not reused: free them now.
-  if (s.spare.cap_n != s.cur.cap_n) s.spare.release();
+  if (s.spare.cap_n != s.cur.cap_n)
+    s.spare.release();
+  else
+    UCC_TRY(clear_spare_async(c, s));
   c->stats.rebuilds++;
   return UCC_OK;
 }
@@ -962,6 +1010,11 @@ void destroy(ucc_ctx* c) {
   if (!c) return;
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->side) {
+    cudaStreamSynchronize(c->side);
+    cudaStreamDestroy(c->side);
+    c->side = nullptr;
+  }
   c->ts[0].release();
   c->ts[1].release();
   for (auto& sn : c->snaps) sn.release();
@@ -1127,6 +1180,7 @@ ucc_status batch_persistent(const std::vector<int>& idx, ucc_ctx* const* jobs, d
       const unsigned long long cap = batch_capacity(c);
       const unsigned long long ns = slots_for(cap);
       TableSet& ts = c->ts[0];
+      UCC_TRY(settle_spare(c, ts));  // the kernels use the spare arrays directly
       if (ts.cur.cap_n != cap || ts.cur.n_slots != ns) UCC_TRY(ts.cur.allocate(cap, ns));
       if (ts.spare.cap_n != cap || ts.spare.n_slots != ns) UCC_TRY(ts.spare.allocate(cap, ns));
       c->main = 0;
@@ -1381,6 +1435,10 @@ ucc_status ucc_create(const ucc_hamiltonian* ham, const ucc_ansatz* an, void* cu
   if (cudaGetDeviceProperties(&prop, c->device) != cudaSuccess) return bail(fail(UCC_ECUDA, "device query failed"));
   c->num_sms = prop.multiProcessorCount;
   c->stream = (cudaStream_t)cuda_stream;
+  if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess) {
+    c->side = nullptr;
+    return bail(fail(UCC_ECUDA, "stream creation failed"));
+  }
   c->n_spatial = ham->n_spatial;
   c->n_alpha = ham->n_alpha;
   c->n_beta = ham->n_beta;
