@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--n1-batch", type=int, default=2, help="theta vectors in the 40-spin-orbital batched leg")
     ap.add_argument("--no-batch", action="store_true", help="skip the 256-job batched leg")
     ap.add_argument("--no-wide", action="store_true", help="skip the 72-spin-orbital leg")
+    ap.add_argument("--no-ncut", action="store_true", help="skip the fixed-parameter cut sweep")
     return ap.parse_args()
 
 
@@ -421,9 +422,17 @@ def batch_leg(args):
         c.gradient(eps=1e-8)
     torch.cuda.synchronize()
     t_s = time.perf_counter() - t0
+    rot_s = sum(c.stats()["rotations"] for c in sc)
     for c in sc:
         c.close()
-    out["sample_vs_one_by_one"] = {"jobs": sample, "batched_s": t_b, "one_by_one_s": t_s, "speedup": t_s / t_b}
+    # The sample batched alone is latency-bound (its longest job sets the time); the throughput
+    # comparison sets the whole batch against the one-job path's rate on the sample, both per
+    # evaluation and per det-rotation (the sample's jobs are smaller or larger than the average).
+    out["sample_vs_one_by_one"] = {
+        "jobs": sample, "batched_s": t_b, "one_by_one_s": t_s, "speedup": t_s / t_b,
+        "one_by_one_evals_per_s": len(sample) / t_s, "one_by_one_det_rotations_per_s": rot_s / t_s,
+        "throughput_speedup_evals": out["evals_per_s"] / (len(sample) / t_s),
+        "throughput_speedup_det_rotations": out["det_rotations_per_s"] / (rot_s / t_s)}
     return out
 
 
@@ -451,6 +460,38 @@ def wide_leg(args):
     ctx.close()
     return {"workload": p.name, "n_so": p.n_so, "n_elec": p.n_elec, "n_factors": p.n_exc, "key_words": 2,
             "eval_s": dt, "det_rotations_per_s": st["rotations"] / dt, "n_det": st["n_det"], "cut": st["cut"]}
+
+
+NCUT_SWEEP = (1000, 2000, 3000, 4000, 5000, 20000, 100000, 500000)
+
+
+def ncut_leg(args):
+    """Energy of fixed parameters as the cut grows (Results, discussion of Fig. 3c): a 64-spin-orbital,
+    10-electron problem shaped like the paper's NH3/cc-pCVDZ study (the 5,000 largest doubles and all
+    singles), evaluated at N_CUT = 1,000-5,000 with N_MAX = 8,000 (the optimisation-time settings), then
+    with the wavefunction allowed to grow (N_MAX = 1.6 N_CUT).  One context; apply and energy per cut."""
+    import torch
+    from paper_2301_05726_gb300 import synth
+    from paper_2301_05726_gb300.api import UCCContext
+    p = synth.fig3_problem()
+    ctx = UCCContext(p)
+    ctx.apply()  # warm-up at the problem's own cut
+    ctx.energy()
+    rows = []
+    for n_cut in NCUT_SWEEP:
+        n_max = 8000 if n_cut <= 5000 else 8 * n_cut // 5
+        ctx.set_options(n_max=n_max, n_cut=n_cut)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.apply()
+        E, n2 = ctx.energy()
+        dt = time.perf_counter() - t0
+        st = ctx.stats()
+        rows.append({"n_max": n_max, "n_cut": n_cut, "E": E, "norm2": n2, "n_det": st["n_det"], "cut": st["cut"],
+                     "s": dt})
+    ctx.close()
+    return {"workload": p.name, "n_so": p.n_so, "n_elec": p.n_elec, "n_factors": p.n_exc, "eps": p.eps,
+            "sweep": rows}
 
 
 def run_ours(args, prob):
@@ -546,6 +587,9 @@ def run_ours(args, prob):
     wide = None
     if rank == 0 and not args.no_wide:
         wide = wide_leg(args)
+    ncut = None
+    if rank == 0 and not args.no_ncut:
+        ncut = ncut_leg(args)
 
     if rank != 0:
         if world > 1:
@@ -585,6 +629,7 @@ def run_ours(args, prob):
         "n1_40so": n1,
         "batched": batched,
         "wide_72so": wide,
+        "ncut_sweep_64so": ncut,
         "e2e": {"value": rot_all / (e2e_ms / 1e3), "unit": UNIT, "steps": len(e2e_times),
                 "h2d_bytes_per_step": FACTOR_BYTES * prob.n_exc, "d2h_bytes_per_step": 8 * prob.n_exc + 8},
         "gpu_launches": int(tot["kernel_launches"]),

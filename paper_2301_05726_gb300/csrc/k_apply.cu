@@ -52,9 +52,12 @@ __global__ void __launch_bounds__(kStepThreads, 8) k_forward(TableT<KT> t, const
   __shared__ LinkScratch<KT> s_w[kStepThreads / 32];
   if (threadIdx.x == 0) s_skip = *((volatile int*)&t.cnt->stop_k) >= 0;
   __syncthreads();
-  const bool skip = s_skip != 0;
+  // An earlier factor of this chunk stopped it: every block of the launch
+  // reads the same flag (only this launch's last block could change it, after
+  // every other block has read it), so the whole launch leaves at once.
+  if (s_skip != 0) return;
   StepCounts sc;
-  if (!skip) {
+  {
     const FactorT<KT> f = factors[k];
     const unsigned long long n = min(*((volatile unsigned long long*)&t.cnt->n_scan), t.cap_n);
     for_each_linked<false>(
@@ -73,7 +76,7 @@ __global__ void __launch_bounds__(kStepThreads, 8) k_forward(TableT<KT> t, const
     if (threadIdx.x == 0) t.partials[blockIdx.x] = b;
   }
   const bool last = last_block_arrive(t.cnt);
-  if (last && t.entropy && !skip) {
+  if (last && t.entropy) {
     // Fixed-order sum of the block changes, added once to the running total.
     double s = 0.0;
     for (unsigned int x = threadIdx.x; x < gridDim.x; x += blockDim.x) s += ld_cg(&t.partials[x]);
@@ -86,7 +89,7 @@ __global__ void __launch_bounds__(kStepThreads, 8) k_forward(TableT<KT> t, const
   if (last && threadIdx.x == 0) {
     Counters* c = t.cnt;
     c->done = 0u;
-    if (!skip) {
+    {
       const unsigned long long nt = ld_cg(&c->n_tail);
       c->link_from = ld_cg(&c->n_scan);  // this step's appended entries, linked next
       c->link_to = nt;

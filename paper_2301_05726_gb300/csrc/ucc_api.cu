@@ -632,8 +632,22 @@ ucc_status run_factors(ucc_ctx* c, TableSet& s, double eps, bool record, int k0,
   unsigned long long n_known = s.h_cnt->n_tail;
   int chunk = 64;
   int k = k0;
+  // Growth per factor of the live entries and of the table's tail, from the
+  // last chunk: a chunk is sized to end just past the factor expected to
+  // stop it (a cut or a table that needs room), so few launches after a stop
+  // are skipped and few chunks end early.
+  double g_live = 0.0, g_tail = 0.0;
+  auto predicted_chunk = [&](const Counters& h, unsigned long long cap, unsigned long long slots) {
+    double f = 64.0;
+    const double live = (double)(h.n_tail - h.n_dead);
+    if (n_max > 0 && g_live > 0.0) f = std::min(f, ((double)n_max - live) / g_live);
+    const double nt_lim = std::min((double)cap / 2.0, 3.0 * (double)slots / 8.0);
+    if (g_tail > 0.0) f = std::min(f, (nt_lim - (double)h.n_tail) / g_tail);
+    return (int)std::max(2.0, std::min(64.0, std::floor(f) + 2.0));
+  };
   while (k < k1) {
     const int end = std::min(k1, k + chunk);
+    const unsigned long long live0 = s.h_cnt->n_tail - s.h_cnt->n_dead, tail0 = s.h_cnt->n_tail;
     // Grid sized from the last known count (grid-stride loops stay correct if
     // the table grew since).
     const unsigned long long est = std::min<unsigned long long>(n_known * 4, s.cur.cap_n);
@@ -658,11 +672,16 @@ ucc_status run_factors(ucc_ctx* c, TableSet& s, double eps, bool record, int k0,
     const Counters h = *s.h_cnt;  // copy: later reads overwrite the mirror
     n_known = h.n_tail;
     c->stats.peak_entries = std::max<long long>(c->stats.peak_entries, (long long)h.n_tail);
+    {
+      const int applied = h.stop_k >= 0 ? h.stop_k - k : end - k;
+      if (applied > 0) {
+        g_live = ((double)(h.n_tail - h.n_dead) - (double)live0) / applied;
+        g_tail = ((double)h.n_tail - (double)tail0) / applied;
+      }
+    }
     if (h.stop_k >= 0) {
       const int resume = h.stop_k;
       if (resume <= k || resume > end) return fail(UCC_ECUDA, "invalid resume factor");
-      // Stops every few factors: launch fewer factors per round trip.
-      chunk = std::max(2, std::min(64, 2 * (resume - k)));
       if (h.cut_pending) {
         const unsigned long long before = h.n_tail - h.n_dead;
         UCC_TRY(cut_rebuild<KT>(c, s, record, resume - 1));
@@ -679,13 +698,17 @@ ucc_status run_factors(ucc_ctx* c, TableSet& s, double eps, bool record, int k0,
       CUDA_TRY(cudaMemcpyAsync(&s.d_cnt->cut_pending, &zero, sizeof(int), cudaMemcpyHostToDevice, c->stream));
       UCC_TRY(read_counters(c, s));
       n_known = s.h_cnt->n_tail;
+      chunk = predicted_chunk(*s.h_cnt, s.cur.cap_n, s.cur.n_slots);
       k = resume;
       continue;
     }
-    chunk = std::min(64, chunk * 2);
     UCC_TRY(autotune<KT>(c, s, end, h.n_tail));
     // Compact when a quarter of the stored entries are dropped ones.
-    if (h.n_dead > 4096 && h.n_dead * 4 > h.n_tail) UCC_TRY(rebuild<KT>(c, s, s.cur.cap_n));
+    if (h.n_dead > 4096 && h.n_dead * 4 > h.n_tail) {
+      UCC_TRY(rebuild<KT>(c, s, s.cur.cap_n));
+      UCC_TRY(read_counters(c, s));
+    }
+    chunk = predicted_chunk(*s.h_cnt, s.cur.cap_n, s.cur.n_slots);
     k = end;
   }
   return UCC_OK;

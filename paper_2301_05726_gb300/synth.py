@@ -231,3 +231,14 @@ def batch_job_problem(j: int, sigma_theta: float = 0.02, eps: float = 1e-8) -> P
 def hilbert_size(n_spatial: int, n_alpha: int, n_beta: int) -> int:
     """Number of determinants with fixed alpha and beta electron counts."""
     return math.comb(n_spatial, n_alpha) * math.comb(n_spatial, n_beta)
+
+
+def fig3_problem(m_doubles: int = 5000) -> Problem:
+    """The shape of the paper's NH3/cc-pCVDZ study of the cut (Results,
+    discussion of Fig. 3): 32 spatial orbitals (64 spin-orbitals, the highest
+    virtual removed), 10 electrons, the m_doubles largest doubles plus all
+    singles, and the optimisation-time cut N_MAX = 8,000 / N_CUT = 5,000.
+    Synthetic integrals and angles; no eps (the cut alone bounds the map)."""
+    p = make_problem(3200, 32, 5, 5, 0.02, eps=0.0, m_doubles=m_doubles, name=f"64so_10e_md{m_doubles}_cut8000")
+    p.n_max, p.n_cut = 8000, 5000
+    return p

@@ -432,3 +432,34 @@ def test_truncation_with_many_exact_ties(torch_cuda):
     assert_same_state(gk, ga, ok, oa)
     st = ctx.stats()
     assert st["cut"] == oc["cut"] and st["rotations"] == oc["rotations"]
+
+
+def test_reevaluate_fixed_theta_at_larger_cuts(torch_cuda):
+    # Results, discussion of Fig. 3c: with the parameters held fixed, the
+    # energy is computed again while the wavefunction may grow past the N_CUT
+    # used in the optimisation.  One context, its cut changed between
+    # evaluations: every evaluation matches the oracle at that cut (state
+    # bit-identical, E within 1e-10), and returning to the first cut gives
+    # the first state bit for bit (nothing of the larger runs is kept; the
+    # energy's summation order follows the table's layout, which the larger
+    # runs resized, so E agrees to rounding).
+    prob = synth.fig3_problem().prefix(400)
+    o = oracle_for(prob)
+    ctx = ctx_for(prob)
+    energies, states = [], []
+    for n_cut in (300, 600, 1200, 2400, 300):
+        n_max = 8 * n_cut // 5
+        ctx.set_options(n_max=n_max, n_cut=n_cut)
+        ctx.apply()
+        E, n2 = ctx.energy()
+        ok, oa, oc = o.apply(n_max=n_max, n_cut=n_cut)
+        gk, ga = ctx.wavefunction()
+        assert np.array_equal(gk, ok) and not np.any(ga != oa), n_cut
+        assert ctx.stats()["cut"] == oc["cut"] > 0
+        E_o, n2_o = o.energy(ok, oa)
+        assert abs(E - E_o) <= E_TOL and abs(n2 - n2_o) <= 1e-12
+        energies.append(E)
+        states.append((gk, ga))
+    assert np.array_equal(states[-1][0], states[0][0]) and np.array_equal(states[-1][1], states[0][1])
+    assert abs(energies[-1] - energies[0]) <= 1e-12
+    assert len(set(energies[:4])) == 4
