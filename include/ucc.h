@@ -110,7 +110,19 @@ typedef struct {
   int32_t batch_tiles;       /* ucc_batch_run: 32-entry tiles a warp takes per
                                 visit of a job (1, 2, 4 or 8); 0 = autotuned.
                                 Read from the first job. */
-  int32_t pad_;
+  int32_t energy_route;      /* ucc_energy / ucc_gradient: 0 = by buckets of
+                                shared cores when their records fit device
+                                memory, else per connection; 1 = per
+                                connection (every single and double excitation
+                                of each stored determinant looked up in the
+                                hash); 2 = by buckets (UCC_ENOMEM if the
+                                record buffer cannot be allocated) */
+  int32_t energy_test_partitions;     /* test only: core partitions of the
+                                         bucketed energy (a power of two;
+                                         0 = sized by the library) */
+  int32_t energy_test_buffer_records; /* test only: cap on the records one
+                                         round of the bucketed energy holds
+                                         (0 = sized by the library) */
 } ucc_options;
 
 /* Counters of the last apply / gradient call. */
@@ -128,8 +140,10 @@ typedef struct {
   int64_t tape_entries;     /* adjoint kill-tape records (gradient only) */
   int64_t kernel_launches;  /* kernels this library launched in the last call */
   int64_t scanned;          /* determinant keys read by the forward factor steps */
-  int64_t sigma_probes;     /* hash lookups of the last energy evaluation */
-  int64_t sigma_hits;       /* of which found a live determinant */
+  int64_t sigma_probes;     /* last energy evaluation: hash lookups (per
+                               connection) or core records (by buckets) */
+  int64_t sigma_hits;       /* connected pairs of stored determinants found,
+                               each pair counted once */
   int64_t reverse_pairs;    /* linked pairs handled by the reverse sweep */
   int64_t recompute_scanned;   /* gradient: keys read while recomputing segments */
   int64_t recompute_rotations; /* gradient: pairs rotated while recomputing segments */
@@ -149,6 +163,8 @@ typedef struct {
   double cut_ms;            /* device time of the Methods-section cuts (selection,
                                compaction, rehash) of the last forward pass */
   double rebuild_ms;        /* device time of the other compactions and growths */
+  int64_t energy_route;     /* route of the last energy evaluation: 1 per
+                               connection, 2 by buckets of shared cores */
 } ucc_stats;
 
 /* Create a context: validate and upload the problem (h, g, the factor table

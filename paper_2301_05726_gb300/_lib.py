@@ -37,7 +37,8 @@ class Options(ctypes.Structure):
                 ("probe_width", ctypes.c_int32), ("checkpoint_stride", ctypes.c_int32),
                 ("tape_budget_mb", ctypes.c_int32), ("record_entropy", ctypes.c_int32),
                 ("batch_wait_ms", ctypes.c_int32), ("batch_test_skip_block", ctypes.c_int32),
-                ("batch_tiles", ctypes.c_int32), ("pad_", ctypes.c_int32)]
+                ("batch_tiles", ctypes.c_int32), ("energy_route", ctypes.c_int32),
+                ("energy_test_partitions", ctypes.c_int32), ("energy_test_buffer_records", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -48,7 +49,7 @@ class Stats(ctypes.Structure):
         "reverse_launches", "probe_width", "reverse_scanned", "reverse_compactions")] + \
         [(n, ctypes.c_double) for n in ("apply_ms", "energy_ms", "reverse_ms", "forward_kernel_ms",
                                         "reverse_kernel_ms")] + [("batch_tiles", ctypes.c_int64)] + \
-        [(n, ctypes.c_double) for n in ("cut_ms", "rebuild_ms")]
+        [(n, ctypes.c_double) for n in ("cut_ms", "rebuild_ms")] + [("energy_route", ctypes.c_int64)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}

@@ -18,7 +18,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libucc.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["ucc_api.cu", "k_apply.cu", "k_energy.cu", "k_adjoint.cu", "k_select.cu", "k_batch.cu", "k_persist.cu",
+SOURCES = ["ucc_api.cu", "k_apply.cu", "k_energy.cu", "k_sigma_bucket.cu", "k_adjoint.cu", "k_select.cu", "k_batch.cu", "k_persist.cu",
            "ucc_static.cu"]
 HEADERS = ["ucc_internal.h", "ucc_device.cuh", "ucc_steps.cuh"]
 

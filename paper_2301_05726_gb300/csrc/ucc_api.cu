@@ -183,6 +183,14 @@ struct ucc_ctx {
   double* d_grad = nullptr;
   double* d_partials = nullptr;
   int partial_cap = 0;
+  // Bucketed energy: per-partition counts, fill counters and offsets, and the
+  // record buffer (kept between evaluations).
+  unsigned int* d_sb_cnt = nullptr;
+  unsigned int* d_sb_fill = nullptr;
+  unsigned long long* d_sb_off = nullptr;
+  unsigned long long sb_parts = 0;
+  unsigned char* d_sb_rec = nullptr;
+  size_t sb_rec_cap = 0;  // bytes
   SelectState* d_sel = nullptr;
   void* d_cand = nullptr;  // SelectCandT<KT>[kSelectCandCap]: candidates of the cut's last selection passes
   double* d_entropy = nullptr;  // [K] Eq. 6 after each factor of the last apply
@@ -773,6 +781,118 @@ ucc_status run_forward(ucc_ctx* c, double eps, bool record) {
   return UCC_OK;
 }
 
+// Record buffer of the bucketed energy: at most this much device memory, and
+// at most this share of what is free.
+constexpr size_t kSbBudgetBytes = size_t(8) << 30;
+constexpr double kSbBudgetShare = 0.4;
+
+// sigma, E and <psi|psi> by buckets of shared cores (records of partitions in
+// rounds that fit the record buffer).  *done = false, with nothing launched,
+// when the buffers cannot be had and the route allows the per-connection pass.
+template <class KT>
+ucc_status energy_by_buckets(ucc_ctx* c, TableSet& s, const Integrals& in, bool* done, unsigned long long* records) {
+  *done = false;
+  const bool must = c->opt.energy_route == 2;
+  const Counters h = *s.h_cnt;
+  const unsigned long long n = h.n_tail, live = h.n_tail - h.n_dead;
+  const unsigned long long ne = (unsigned long long)(c->n_alpha + c->n_beta);
+  const unsigned long long est = live * (ne + ne * (ne - 1) / 2);
+  if (est == 0) {
+    if (must) return fail(UCC_ESTATE, "no stored determinant to bucket");
+    return UCC_OK;
+  }
+  int log2p = 0;
+  if (c->opt.energy_test_partitions > 0)
+    while ((1 << log2p) < c->opt.energy_test_partitions) ++log2p;
+  else
+    while (log2p < 24 && (est >> log2p) > (unsigned long long)sb_partition_target()) ++log2p;
+  const unsigned long long P = 1ull << log2p;
+  auto unavailable = [&](const char* what) -> ucc_status {
+    if (must) return fail(UCC_ENOMEM, std::string("bucketed energy: ") + what);
+    cudaGetLastError();  // clear a failed allocation
+    return UCC_OK;
+  };
+  if (c->sb_parts < P) {
+    dfree(c->d_sb_cnt);
+    dfree(c->d_sb_fill);
+    dfree(c->d_sb_off);
+    c->sb_parts = 0;
+    if (dalloc(&c->d_sb_cnt, P) != UCC_OK || dalloc(&c->d_sb_fill, P) != UCC_OK ||
+        dalloc(&c->d_sb_off, P + 1) != UCC_OK) {
+      dfree(c->d_sb_cnt);
+      dfree(c->d_sb_fill);
+      dfree(c->d_sb_off);
+      return unavailable("partition arrays");
+    }
+    c->sb_parts = P;
+  }
+  const size_t rec_bytes = sb_record_bytes(c->wide ? 2 : 1);
+  size_t free_b = 0, total_b = 0;
+  CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+  const size_t want = std::min<size_t>(kSbBudgetBytes, (size_t)est * rec_bytes);
+  if (c->sb_rec_cap < want && c->sb_rec_cap < (size_t)(kSbBudgetShare * (double)(free_b + c->sb_rec_cap))) {
+    dfree(c->d_sb_rec);
+    c->sb_rec_cap = 0;
+    size_t bytes = std::min(want, (size_t)(kSbBudgetShare * (double)free_b));
+    bytes -= bytes % 32;
+    if (bytes < 32 * rec_bytes || dalloc(&c->d_sb_rec, bytes) != UCC_OK) return unavailable("record buffer");
+    c->sb_rec_cap = bytes;
+  }
+  unsigned long long cap_recs = c->sb_rec_cap / rec_bytes;
+  if (c->opt.energy_test_buffer_records > 0)
+    cap_recs = std::min<unsigned long long>(cap_recs, (unsigned long long)c->opt.energy_test_buffer_records);
+  const int grid = (int)std::max<unsigned long long>(
+      1ull, std::min<unsigned long long>((unsigned long long)c->full_grid(8), (n + 255) / 256));
+  const int pair_grid = std::max(1, c->num_sms * std::max(1, sb_blocks_per_sm(c->wide ? 2 : 1)));
+  const TableT<KT> t = c->template table<KT>(s);
+  SigRecT<KT>* rec = reinterpret_cast<SigRecT<KT>*>(c->d_sb_rec);
+  CUDA_TRY(cudaMemsetAsync(c->d_sb_cnt, 0, P * sizeof(unsigned int), c->stream));
+  CUDA_TRY(cudaMemsetAsync(t.sigma, 0, n * sizeof(double), c->stream));
+  CUDA_TRY(launch_sb_count(t, c->d_sb_cnt, log2p, grid, c->stream));
+  CUDA_TRY(launch_sb_scan(c->d_sb_cnt, c->d_sb_off, P, c->stream));
+  c->launches += 2;
+  auto off_at = [&](unsigned long long p, unsigned long long* v) -> ucc_status {
+    CUDA_TRY(cudaMemcpyAsync(v, c->d_sb_off + p, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return UCC_OK;
+  };
+  unsigned long long total = 0;
+  UCC_TRY(off_at(P, &total));
+  *records = total;
+  // Rounds: partition ranges whose records fit the buffer, halved until they do.
+  std::vector<std::pair<unsigned long long, unsigned long long>> todo;
+  {
+    const unsigned long long rounds = std::max<unsigned long long>(1ull, (total + cap_recs - 1) / cap_recs);
+    unsigned long long width = P;
+    while (width > 1 && P / width < rounds) width >>= 1;
+    for (unsigned long long p = P; p > 0; p -= width) todo.push_back({p - width, p});
+  }
+  while (!todo.empty()) {
+    const auto [p0, p1] = todo.back();
+    todo.pop_back();
+    unsigned long long a = 0, b = 0;
+    UCC_TRY(off_at(p0, &a));
+    UCC_TRY(off_at(p1, &b));
+    if (b - a > cap_recs) {
+      if (p1 - p0 == 1) return fail(UCC_ECAPACITY, "one core partition outgrew the record buffer");
+      const unsigned long long mid = p0 + (p1 - p0) / 2;
+      todo.push_back({mid, p1});
+      todo.push_back({p0, mid});
+      continue;
+    }
+    if (b == a) continue;
+    CUDA_TRY(cudaMemsetAsync(c->d_sb_fill + p0, 0, (p1 - p0) * sizeof(unsigned int), c->stream));
+    CUDA_TRY(launch_sb_scatter(t, c->d_sb_off, c->d_sb_fill, rec, log2p, p0, p1, a, grid, c->stream));
+    CUDA_TRY(launch_sb_pairs(t, in, rec, c->d_sb_off, log2p, p0, p1, a,
+                             (int)std::min<unsigned long long>((unsigned long long)pair_grid, p1 - p0), c->stream));
+    c->launches += 2;
+  }
+  CUDA_TRY(launch_sb_finish(t, in, grid, c->stream));
+  c->launches++;
+  *done = true;
+  return UCC_OK;
+}
+
 template <class KT>
 ucc_status run_energy(ucc_ctx* c, double* E, double* norm2) {
   TableSet& s = c->ts[c->main];
@@ -788,15 +908,23 @@ ucc_status run_energy(ucc_ctx* c, double* E, double* norm2) {
   UCC_TRY(ensure_partials(c, c->full_grid()));
   CUDA_TRY(cudaMemsetAsync(&s.d_cnt->sig_probes, 0, 2 * sizeof(unsigned long long), c->stream));
   CUDA_TRY(cudaEventRecord(c->ev[2], c->stream));
-  CUDA_TRY(launch_sigma(c->template table<KT>(s), in, grid, c->stream));
-  c->launches += 2;
+  bool bucketed = false;
+  unsigned long long records = 0;
+  if (c->opt.energy_route != 1) UCC_TRY(energy_by_buckets<KT>(c, s, in, &bucketed, &records));
+  if (!bucketed) {
+    CUDA_TRY(launch_sigma(c->template table<KT>(s), in, grid, c->stream));
+    c->launches += 2;
+  }
   CUDA_TRY(cudaEventRecord(c->ev[3], c->stream));
   UCC_TRY(read_counters(c, s));
   float ms = 0.f;
   CUDA_TRY(cudaEventElapsedTime(&ms, c->ev[2], c->ev[3]));
   c->stats.energy_ms = ms;
-  c->stats.sigma_probes = (long long)s.h_cnt->sig_probes;
-  c->stats.sigma_hits = (long long)s.h_cnt->sig_hits;
+  c->stats.energy_route = bucketed ? 2 : 1;
+  // probes: hash lookups (per connection) or core records (by buckets); hits:
+  // connected stored pairs, each counted once
+  c->stats.sigma_probes = bucketed ? (long long)records : (long long)s.h_cnt->sig_probes;
+  c->stats.sigma_hits = bucketed ? (long long)(s.h_cnt->sig_hits / 2) : (long long)s.h_cnt->sig_hits;
   const double n2 = s.h_cnt->norm2;
   if (norm2) *norm2 = n2;
   if (E) *E = s.h_cnt->e_num / n2 + c->e_nuc;
@@ -1046,6 +1174,10 @@ void destroy(ucc_ctx* c) {
   dfree(c->d_g);
   dfree(c->d_grad);
   dfree(c->d_partials);
+  dfree(c->d_sb_cnt);
+  dfree(c->d_sb_fill);
+  dfree(c->d_sb_off);
+  dfree(c->d_sb_rec);
   dfree(c->d_sel);
   dfree(c->d_cand);
   release_tape(c);
@@ -1540,6 +1672,11 @@ ucc_status ucc_set_options(ucc_ctx* c, const ucc_options* opt) {
   if (o.batch_wait_ms < 0 || o.batch_test_skip_block < 0) return fail(UCC_EINVAL, "negative option");
   if (o.batch_tiles != 0 && o.batch_tiles != 1 && o.batch_tiles != 2 && o.batch_tiles != 4 && o.batch_tiles != 8)
     return fail(UCC_EINVAL, "batch_tiles must be 0, 1, 2, 4 or 8");
+  if (o.energy_route < 0 || o.energy_route > 2) return fail(UCC_EINVAL, "energy_route must be 0, 1 or 2");
+  if (o.energy_test_partitions < 0 || (o.energy_test_partitions & (o.energy_test_partitions - 1)) != 0 ||
+      o.energy_test_partitions > (1 << 24))
+    return fail(UCC_EINVAL, "energy_test_partitions must be 0 or a power of two up to 2^24");
+  if (o.energy_test_buffer_records < 0) return fail(UCC_EINVAL, "negative option");
   c->opt = o;
   return UCC_OK;
 }

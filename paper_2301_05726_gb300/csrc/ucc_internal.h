@@ -134,6 +134,18 @@ struct Integrals {
   int n_so;
 };
 
+// One record of the bucketed energy: a core K (a stored determinant with one
+// or two electrons removed), the determinant's amplitude and entry index, and
+// the removed spin-orbitals p | q << 8 (q = 0xFF for one).
+template <class KT>
+struct __align__(sizeof(KT) == 16 ? 16 : 8) SigRecT {
+  KT K;
+  double c;
+  unsigned int i;
+  unsigned short pq;
+  unsigned short pad;
+};
+
 // Radix-selection state of the N_MAX / N_CUT truncation.
 struct SelectState {
   unsigned long long prefix, target;          // |c| bits of the threshold, rank left inside it
@@ -248,6 +260,25 @@ template <class KT>
 cudaError_t launch_sigma(const TableT<KT>& t, const Integrals& in, int grid, cudaStream_t st);
 template <class KT>
 cudaError_t launch_lambda_init(const TableT<KT>& t, int grid, cudaStream_t st);
+// Bucketed energy: records per core partition, their prefix sum, the records
+// of partitions [p0, p1) (fill: per-partition counters, zeroed per round),
+// the pair sums into sigma, and the diagonal with E and <psi|psi>.
+template <class KT>
+cudaError_t launch_sb_count(const TableT<KT>& t, unsigned int* cnt, int log2p, int grid, cudaStream_t st);
+cudaError_t launch_sb_scan(const unsigned int* cnt, unsigned long long* off, unsigned long long n, cudaStream_t st);
+template <class KT>
+cudaError_t launch_sb_scatter(const TableT<KT>& t, const unsigned long long* off, unsigned int* fill,
+                              SigRecT<KT>* rec, int log2p, unsigned long long p0, unsigned long long p1,
+                              unsigned long long base, int grid, cudaStream_t st);
+template <class KT>
+cudaError_t launch_sb_pairs(const TableT<KT>& t, const Integrals& in, const SigRecT<KT>* rec,
+                            const unsigned long long* off, int log2p, unsigned long long p0, unsigned long long p1,
+                            unsigned long long base, int grid, cudaStream_t st);
+template <class KT>
+cudaError_t launch_sb_finish(const TableT<KT>& t, const Integrals& in, int grid, cudaStream_t st);
+size_t sb_record_bytes(int key_words);
+int sb_blocks_per_sm(int key_words);
+int sb_partition_target();  // mean records per partition the host aims for
 template <class KT>
 cudaError_t launch_tape_reinsert(const TableT<KT>& t, const TapeT<KT>& tape, int k, unsigned long long records,
                                  int grid, cudaStream_t st, long long* launches);
