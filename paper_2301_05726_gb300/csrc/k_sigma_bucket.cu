@@ -30,7 +30,7 @@ namespace {
 constexpr unsigned int kSingle = 0xFFu;
 // Records per partition held in shared memory, and the counting-sort bins.
 constexpr int kSbCap = 3072;
-constexpr int kSbBins = 2048;
+constexpr int kSbBins = 2048;  // a multiple of kSbThreads
 constexpr int kSbBinBits = 11;
 constexpr int kSbThreads = 512;
 
@@ -107,6 +107,23 @@ __global__ void __launch_bounds__(1024) k_sb_scan(const unsigned int* __restrict
   if (threadIdx.x == blockDim.x - 1) off[n] = s_part[threadIdx.x];
 }
 
+// A record as one 256-bit store (a whole 32-byte sector: no partial-sector
+// write for the memory to merge).
+__device__ __forceinline__ void store_words(void* at, unsigned long long a, unsigned long long b, unsigned long long c,
+                                            unsigned long long d) {
+  asm volatile("st.global.v4.b64 [%0], {%1, %2, %3, %4};" ::"l"(at), "l"(a), "l"(b), "l"(c), "l"(d) : "memory");
+}
+__device__ __forceinline__ void store_record(SigRecT<unsigned long long>* at, unsigned long long K, double c,
+                                             unsigned int i, unsigned int pq) {
+  store_words(at, K, (unsigned long long)__double_as_longlong(c), (unsigned long long)i | ((unsigned long long)pq << 32),
+              0ull);
+}
+__device__ __forceinline__ void store_record(SigRecT<Key128>* at, Key128 K, double c, unsigned int i,
+                                             unsigned int pq) {
+  store_words(at, K.lo, K.hi, (unsigned long long)__double_as_longlong(c),
+              (unsigned long long)i | ((unsigned long long)pq << 32));
+}
+
 // The records of partitions [p0, p1), at rec[off[p] - base + fill[p]++].
 template <class KT>
 __global__ void __launch_bounds__(256) k_sb_scatter(TableT<KT> t, const unsigned long long* __restrict__ off,
@@ -126,14 +143,7 @@ __global__ void __launch_bounds__(256) k_sb_scatter(TableT<KT> t, const unsigned
         raise_error(t.cnt, ERR_CAPACITY);
         return;
       }
-      const unsigned long long at = off[p] - base + f;
-      SigRecT<KT> r;
-      r.K = core;
-      r.c = c;
-      r.i = (unsigned int)i;
-      r.pq = (unsigned short)removed;
-      r.pad = 0;
-      rec[at] = r;
+      store_record(rec + (off[p] - base + f), core, c, (unsigned int)i, removed);
     });
   }
 }
@@ -186,15 +196,56 @@ __device__ unsigned long long pairs_in_global(const TableT<KT>& t, const Integra
 
 template <class KT>
 constexpr size_t sb_smem_bytes() {
-  return (size_t)kSbCap * (sizeof(KT) + sizeof(double) + sizeof(unsigned int) + 2 * sizeof(unsigned short) +
-                           sizeof(unsigned short)) +
-         (size_t)(2 * kSbBins + 1) * sizeof(unsigned int);
+  return (size_t)kSbCap * (sizeof(KT) + sizeof(double) + sizeof(unsigned int) + sizeof(unsigned short)) +
+         (size_t)(3 * kSbBins + 2) * sizeof(unsigned int);
 }
 
-// One block per partition of [p0, p1) (grid-stride): the partition's records
-// into shared memory, a counting sort by core-hash bin, then every record sums
-// <I|H|J> c_J over the records of its core (found within its bin) and adds the
-// sum to sigma_I.
+// Exclusive scans over the bins of a (n_b records) and b (n_b (n_b - 1)
+// ordered pairs) into sa and sb (kSbBins + 1 entries each, the totals last);
+// every thread of the block calls this.
+__device__ __forceinline__ void scan_bins(const unsigned int* cnt, unsigned int* sa, unsigned int* sb,
+                                          unsigned int* s_a, unsigned int* s_b) {
+  constexpr int kPer = kSbBins / kSbThreads;
+  const unsigned int tid = threadIdx.x;
+  unsigned int ta = 0u, tb = 0u;
+#pragma unroll
+  for (int u = 0; u < kPer; ++u) {
+    const unsigned int n = cnt[tid * kPer + u];
+    ta += n;
+    tb += n * (n ? n - 1u : 0u);
+  }
+  s_a[tid] = ta;
+  s_b[tid] = tb;
+  __syncthreads();
+  for (int d = 1; d < kSbThreads; d <<= 1) {
+    const unsigned int xa = tid >= (unsigned int)d ? s_a[tid - d] : 0u;
+    const unsigned int xb = tid >= (unsigned int)d ? s_b[tid - d] : 0u;
+    __syncthreads();
+    s_a[tid] += xa;
+    s_b[tid] += xb;
+    __syncthreads();
+  }
+  unsigned int ra = tid ? s_a[tid - 1] : 0u, rb = tid ? s_b[tid - 1] : 0u;
+#pragma unroll
+  for (int u = 0; u < kPer; ++u) {
+    const unsigned int n = cnt[tid * kPer + u];
+    sa[tid * kPer + u] = ra;
+    sb[tid * kPer + u] = rb;
+    ra += n;
+    rb += n * (n ? n - 1u : 0u);
+  }
+  if (tid == kSbThreads - 1) {
+    sa[kSbBins] = ra;
+    sb[kSbBins] = rb;
+  }
+}
+
+// One block per partition of [p0, p1) (grid-stride).  The partition's records
+// are counted by core-hash bin (a core's records share a bin), placed into
+// shared memory in bin order, and then the ordered pairs (x, w), x != w, of
+// every bin are split evenly over the threads: each walks its contiguous share
+// of pair indices, evaluates <I_x|H|J_w> c_w where the cores agree, and adds
+// the sum of a record to sigma when its walk leaves that record.
 template <class KT>
 __global__ void __launch_bounds__(kSbThreads) k_sb_pairs(TableT<KT> t, Integrals in, const SigRecT<KT>* __restrict__ rec,
                                                          const unsigned long long* __restrict__ off, int log2p,
@@ -205,11 +256,10 @@ __global__ void __launch_bounds__(kSbThreads) k_sb_pairs(TableT<KT> t, Integrals
   double* sc = reinterpret_cast<double*>(sK + kSbCap);
   unsigned int* si = reinterpret_cast<unsigned int*>(sc + kSbCap);
   unsigned short* sp = reinterpret_cast<unsigned short*>(si + kSbCap);
-  unsigned short* sb = sp + kSbCap;
-  unsigned short* perm = sb + kSbCap;
-  unsigned int* cursor = reinterpret_cast<unsigned int*>(perm + kSbCap);
-  unsigned int* start = cursor + kSbBins;  // kSbBins + 1 entries
-  __shared__ unsigned int s_sum[kSbThreads];
+  unsigned int* cnt = reinterpret_cast<unsigned int*>(sp + kSbCap);  // counts, then placement cursors
+  unsigned int* start = cnt + kSbBins;                                // kSbBins + 1: records before each bin
+  unsigned int* pst = start + kSbBins + 1;                            // kSbBins + 1: ordered pairs before each bin
+  __shared__ unsigned int s_a[kSbThreads], s_b[kSbThreads];
   const unsigned int tid = threadIdx.x;
   unsigned long long pairs = 0;
   for (unsigned long long p = p0 + blockIdx.x; p < p1; p += gridDim.x) {
@@ -220,61 +270,73 @@ __global__ void __launch_bounds__(kSbThreads) k_sb_pairs(TableT<KT> t, Integrals
       continue;
     }
     const int mi = (int)m;
-    for (int b = (int)tid; b < kSbBins; b += kSbThreads) cursor[b] = 0u;
+    for (int b = (int)tid; b < kSbBins; b += kSbThreads) cnt[b] = 0u;
+    __syncthreads();
+    for (int x = (int)tid; x < mi; x += kSbThreads) atomicAdd(&cnt[bin_of(core_hash(rec[lo + x].K), log2p)], 1u);
+    __syncthreads();
+    scan_bins(cnt, start, pst, s_a, s_b);
+    __syncthreads();
+    for (int b = (int)tid; b < kSbBins; b += kSbThreads) cnt[b] = start[b];
     __syncthreads();
     for (int x = (int)tid; x < mi; x += kSbThreads) {
       const SigRecT<KT> r = rec[lo + (unsigned long long)x];
-      sK[x] = r.K;
-      sc[x] = r.c;
-      si[x] = r.i;
-      sp[x] = r.pq;
-      const int b = bin_of(core_hash(r.K), log2p);
-      sb[x] = (unsigned short)b;
-      atomicAdd(&cursor[b], 1u);
+      const unsigned int at = atomicAdd(&cnt[bin_of(core_hash(r.K), log2p)], 1u);
+      sK[at] = r.K;
+      sc[at] = r.c;
+      si[at] = r.i;
+      sp[at] = r.pq;
     }
     __syncthreads();
-    // Exclusive scan of the bin counts: four bins per thread, then the
-    // thread sums (Hillis-Steele).
-    constexpr int kPer = kSbBins / kSbThreads;
-    unsigned int v[kPer], tot = 0u;
-#pragma unroll
-    for (int u = 0; u < kPer; ++u) {
-      v[u] = cursor[tid * kPer + u];
-      tot += v[u];
-    }
-    s_sum[tid] = tot;
-    __syncthreads();
-    for (int d = 1; d < kSbThreads; d <<= 1) {
-      const unsigned int a = tid >= (unsigned int)d ? s_sum[tid - d] : 0u;
-      __syncthreads();
-      s_sum[tid] += a;
-      __syncthreads();
-    }
-    unsigned int run = tid ? s_sum[tid - 1] : 0u;
-#pragma unroll
-    for (int u = 0; u < kPer; ++u) {
-      start[tid * kPer + u] = run;
-      cursor[tid * kPer + u] = run;
-      run += v[u];
-    }
-    if (tid == 0) start[kSbBins] = (unsigned int)mi;
-    __syncthreads();
-    for (int x = (int)tid; x < mi; x += kSbThreads) perm[atomicAdd(&cursor[sb[x]], 1u)] = (unsigned short)x;
-    __syncthreads();
-    // Sorted positions: the lanes of a warp mostly share a bin and a core.
-    for (int y = (int)tid; y < mi; y += kSbThreads) {
-      const int x = perm[y];
-      const KT K = sK[x];
-      const unsigned int rx = sp[x];
-      const int b = sb[x];
+    const unsigned int T = pst[kSbBins];
+    const unsigned int per = (T + kSbThreads - 1u) / kSbThreads;
+    unsigned int j = tid * per;
+    const unsigned int j_end = min(T, j + per);
+    if (j < j_end) {
+      // the bin holding pair index j: the last b with pst[b] <= j
+      int lo_b = 0, hi_b = kSbBins;
+      while (hi_b - lo_b > 1) {
+        const int mid = (lo_b + hi_b) >> 1;
+        if (pst[mid] <= j)
+          lo_b = mid;
+        else
+          hi_b = mid;
+      }
+      int b = lo_b;
+      unsigned int mb = start[b + 1] - start[b];
+      unsigned int loc = j - pst[b];
+      unsigned int u = loc / (mb - 1u), v = loc % (mb - 1u);
+      v += (v >= u) ? 1u : 0u;
+      unsigned int x = start[b] + u;
+      KT K = sK[x];
+      unsigned int rx = sp[x];
       double acc = 0.0;
-      for (int z = (int)start[b]; z < (int)start[b + 1]; ++z) {
-        const int w = perm[z];
-        if (w == x || !(sK[w] == K)) continue;
-        double h;
-        if (pair_element(in, K, rx, sp[w], &h)) {
-          acc += h * sc[w];
-          ++pairs;
+      for (; j < j_end; ++j) {
+        const unsigned int w = start[b] + v;
+        if (sK[w] == K) {
+          double h;
+          if (pair_element(in, K, rx, sp[w], &h)) {
+            acc += h * sc[w];
+            ++pairs;
+          }
+        }
+        // next pair: (u, v + 1) skipping v == u; then the next record; then
+        // the next bin holding a pair
+        if (++v == u) ++v;
+        if (v >= mb) {
+          if (acc != 0.0) atomicAdd(&t.sigma[si[x]], acc);
+          acc = 0.0;
+          if (++u >= mb) {
+            if (j + 1u >= j_end) break;
+            do {
+              ++b;
+            } while (pst[b + 1] == pst[b]);
+            mb = start[b + 1] - start[b];
+            u = 0u;
+          }
+          v = (u == 0u) ? 1u : 0u;
+          x = start[b] + u;
+          K = sK[x];
+          rx = sp[x];
         }
       }
       if (acc != 0.0) atomicAdd(&t.sigma[si[x]], acc);
@@ -353,18 +415,25 @@ cudaError_t launch_sb_scatter(const TableT<KT>& t, const unsigned long long* off
   return cudaGetLastError();
 }
 
+// The pairs kernel's dynamic shared memory is above the default 48 KB limit:
+// raised once per key width, before any launch or occupancy query.
+template <class KT>
+cudaError_t sb_allow_smem() {
+  static bool done = false;
+  if (done) return cudaSuccess;
+  const cudaError_t e =
+      cudaFuncSetAttribute(k_sb_pairs<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb_smem_bytes<KT>());
+  if (e == cudaSuccess) done = true;
+  return e;
+}
+
 template <class KT>
 cudaError_t launch_sb_pairs(const TableT<KT>& t, const Integrals& in, const SigRecT<KT>* rec,
                             const unsigned long long* off, int log2p, unsigned long long p0, unsigned long long p1,
                             unsigned long long base, int grid, cudaStream_t st) {
-  constexpr size_t smem = sb_smem_bytes<KT>();
-  static bool attr = false;
-  if (!attr) {
-    const cudaError_t e = cudaFuncSetAttribute(k_sb_pairs<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
-  k_sb_pairs<KT><<<grid, kSbThreads, smem, st>>>(t, in, rec, off, log2p, p0, p1, base);
+  const cudaError_t e = sb_allow_smem<KT>();
+  if (e != cudaSuccess) return e;
+  k_sb_pairs<KT><<<grid, kSbThreads, sb_smem_bytes<KT>(), st>>>(t, in, rec, off, log2p, p0, p1, base);
   return cudaGetLastError();
 }
 
@@ -376,11 +445,17 @@ cudaError_t launch_sb_finish(const TableT<KT>& t, const Integrals& in, int grid,
 
 int sb_blocks_per_sm(int key_words) {
   int nb = 0;
-  const cudaError_t e =
-      key_words == 2
-          ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sb_pairs<Key128>, kSbThreads, sb_smem_bytes<Key128>())
-          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sb_pairs<unsigned long long>, kSbThreads,
-                                                          sb_smem_bytes<unsigned long long>());
+  cudaError_t e;
+  if (key_words == 2) {
+    e = sb_allow_smem<Key128>();
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sb_pairs<Key128>, kSbThreads, sb_smem_bytes<Key128>());
+  } else {
+    e = sb_allow_smem<unsigned long long>();
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sb_pairs<unsigned long long>, kSbThreads,
+                                                        sb_smem_bytes<unsigned long long>());
+  }
   return e == cudaSuccess ? nb : 0;
 }
 

@@ -783,7 +783,7 @@ ucc_status run_forward(ucc_ctx* c, double eps, bool record) {
 
 // Record buffer of the bucketed energy: at most this much device memory, and
 // at most this share of what is free.
-constexpr size_t kSbBudgetBytes = size_t(8) << 30;
+constexpr size_t kSbBudgetBytes = size_t(32) << 30;
 constexpr double kSbBudgetShare = 0.4;
 
 // sigma, E and <psi|psi> by buckets of shared cores (records of partitions in

@@ -136,15 +136,18 @@ struct Integrals {
 
 // One record of the bucketed energy: a core K (a stored determinant with one
 // or two electrons removed), the determinant's amplitude and entry index, and
-// the removed spin-orbitals p | q << 8 (q = 0xFF for one).
+// the removed spin-orbitals p | q << 8 (q = 0xFF for one).  32 bytes for
+// either key width, 32-byte aligned: a record is one DRAM sector, written by
+// one 256-bit store.
 template <class KT>
-struct __align__(sizeof(KT) == 16 ? 16 : 8) SigRecT {
+struct __align__(32) SigRecT {
   KT K;
   double c;
   unsigned int i;
   unsigned short pq;
   unsigned short pad;
 };
+static_assert(sizeof(SigRecT<unsigned long long>) == 32, "record is one sector");
 
 // Radix-selection state of the N_MAX / N_CUT truncation.
 struct SelectState {
