@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the 256-job batched leg")
     ap.add_argument("--no-wide", action="store_true", help="skip the 72-spin-orbital leg")
     ap.add_argument("--no-ncut", action="store_true", help="skip the fixed-parameter cut sweep")
+    ap.add_argument("--n-max", type=int, default=None,
+                    help="exploration: the workload's N_MAX (with --n-cut; default: the workload's own cut)")
+    ap.add_argument("--n-cut", type=int, default=None)
     return ap.parse_args()
 
 
@@ -651,6 +654,9 @@ def run_ours(args, prob):
 def main():
     args = parse()
     prob = workload(args.workload)
+    if args.n_max is not None:
+        prob.n_max = args.n_max
+        prob.n_cut = args.n_cut if args.n_cut is not None else args.n_max * 5 // 8
     if args.impl == "reference":
         run_reference(args, prob)
     else:

@@ -258,9 +258,9 @@ ucc_status ucc_batch_run(int n_jobs, ucc_ctx* const* jobs, double eps, double* E
  * one file-scope device array that every device loading the library holds
  * until the process exits.  The first call on a device, with that device
  * current, looks up the array's device address (cudaGetSymbolAddress) and
- * keeps it for the life of the library; make that first call before any
- * stream capture.  Resetting the device (cudaDeviceReset) after that call is
- * not supported: the module reloads and the kept address goes stale.  Every call reuses the array
+ * keeps it for the life of the library.  Resetting the device
+ * (cudaDeviceReset) after that call is not supported: the module reloads and
+ * the kept address goes stale.  Every call reuses the array
  * and clears it first, so calls whose work overlaps on the GPU race: do not
  * run two at once on one device.  n_det above UCC_STATIC_MAX_DETS, or 0,
  * returns UCC_EINVAL; malformed keys or amplitudes return UCC_EINVAL. */
