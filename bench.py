@@ -250,17 +250,18 @@ def flush_l2(buf):
     buf.add_(1.0)
 
 
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per algorithmic byte of a kernel, from one
-# ncu capture of a few launches of that kernel alone on a full-size table; a launch's traffic is taken as
-# this ratio times its algorithmic bytes.  Empty (traffic reported as null) until the current build of
-# the kernel has been captured.
-TRAFFIC_PER_ALGORITHMIC_BYTE = {}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per entry a launch scans, from one ncu capture
+# of three launches of that kernel alone on a 1,000-factor prefix of the 64-so workload (about 8.6e6
+# entries per launch, far larger than L2; the summary under profiles/ gives the command); a full-size
+# launch's traffic is taken as this figure times the entries it scans.  A kernel is left out (traffic
+# reported as null) once its code has changed since its capture.
+TRAFFIC_PER_SCANNED_ENTRY = {}
 
 
-def _roofline(kernel, bytes_, ms, launches, hbm, peak_kind):
+def _roofline(kernel, bytes_, ms, launches, hbm, peak_kind, scanned=0):
     ach = bytes_ / (ms / 1e3) / 1e9 if ms > 0 else 0.0
-    ratio = TRAFFIC_PER_ALGORITHMIC_BYTE.get(kernel)
-    traffic = ratio * bytes_ / max(1, launches) if ratio else None
+    per = TRAFFIC_PER_SCANNED_ENTRY.get(kernel)
+    traffic = per * scanned / max(1, launches) if per and scanned else None
     return {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": traffic,
             "kernel": kernel, "peak_kind": peak_kind, "launches": launches,
             "avg_launch_ms": ms / max(1, launches), "algorithmic_bytes": bytes_, "total_ms": ms}
@@ -274,7 +275,10 @@ def byte_models(tot):
     member model: a rotation whose partner is absent (created, or computed below eps and never stored)
     touches only its own member (16 B forward: amplitude read and write; 32 B reverse: amplitude and
     adjoint read and written); a stored pair is charged as in the pair model.  Both charge 8 B per key
-    scanned and 32 B per created entry (key and amplitude written, slot claimed)."""
+    scanned and 32 B per created entry (key and amplitude written, slot claimed).  The energy: by
+    buckets (route 2) a 32 B record written and read per core (sigma_probes counts the records) and 40 B
+    per determinant (key and amplitude read by the record passes, sigma written and read back); per
+    connection (route 1) 24 B per determinant and 16 B per connected stored pair."""
     scanned = tot["scanned"] + tot["recompute_scanned"]
     rot = tot["rotations"] + tot["recompute_rotations"]
     cre = tot["created"] + tot["recompute_created"]
@@ -282,11 +286,14 @@ def byte_models(tot):
     both = rot - lone
     rev_lone = min(tot["reverse_pairs"], tot["dropped_new"])
     rev_both = tot["reverse_pairs"] - rev_lone
-    sig = 24.0 * tot["n_det"] + 16.0 * tot["sigma_hits"]
+    if tot.get("energy_route_last") == 2:
+        sig = 64.0 * tot["sigma_probes"] + 40.0 * tot["n_det"]
+    else:
+        sig = 24.0 * tot["n_det"] + 16.0 * tot["sigma_hits"]
     return {
-        "pair": {"k_forward": 8.0 * scanned + 48.0 * rot + 32.0 * cre, "k_sigma": sig,
+        "pair": {"k_forward": 8.0 * scanned + 48.0 * rot + 32.0 * cre, "energy": sig,
                  "k_reverse": 8.0 * tot["scanned"] + 80.0 * tot["reverse_pairs"]},
-        "member": {"k_forward": 8.0 * scanned + 16.0 * lone + 48.0 * both + 32.0 * cre, "k_sigma": sig,
+        "member": {"k_forward": 8.0 * scanned + 16.0 * lone + 48.0 * both + 32.0 * cre, "energy": sig,
                    "k_reverse": 8.0 * tot["scanned"] + 32.0 * rev_lone + 80.0 * rev_both},
     }
 
@@ -549,8 +556,10 @@ def run_ours(args, prob):
         ev1.record(stream)
         ev1.synchronize()
         times.append(ev0.elapsed_time(ev1))
-        for k, v in ctx.stats().items():
+        st = ctx.stats()
+        for k, v in st.items():
             tot[k] = tot.get(k, 0) + v
+        tot["energy_route_last"] = st["energy_route"]
     torch.cuda.synchronize()
     clocks = sampler.stop()
     ms = sum(times) / len(times)
@@ -600,10 +609,10 @@ def run_ours(args, prob):
         return
     hbm, peak_kind = peaks()
     models = byte_models(tot)
-    kernel_ms = {"k_forward": (tot["forward_kernel_ms"], tot["forward_launches"]),
-                 "k_sigma": (tot["energy_ms"], n_steps),
-                 "k_reverse": (tot["reverse_kernel_ms"], tot["reverse_launches"])}
-    kernels = {m: {k: _roofline(k, models[m][k], t, n, hbm, peak_kind) for k, (t, n) in kernel_ms.items()}
+    kernel_ms = {"k_forward": (tot["forward_kernel_ms"], tot["forward_launches"], tot["scanned"]),
+                 "energy": (tot["energy_ms"], n_steps, 0),
+                 "k_reverse": (tot["reverse_kernel_ms"], tot["reverse_launches"], tot["reverse_scanned"])}
+    kernels = {m: {k: _roofline(k, models[m][k], t, n, hbm, peak_kind, sc) for k, (t, n, sc) in kernel_ms.items()}
                for m in models}
     dom = max(kernels["member"].values(), key=lambda r: r["total_ms"])
     roof = {k: dom[k] for k in ("bound", "achieved", "peak", "unit", "frac", "traffic", "kernel", "peak_kind",

@@ -143,8 +143,9 @@ __global__ void __launch_bounds__(kThreads) k_link_tail(TableT<KT> t) {
 template <class KT, int G>
 __global__ void __launch_bounds__(kStepThreads, 8) k_reverse(TableT<KT> t, const FactorT<KT>* __restrict__ factors,
                                                              int k, unsigned int stamp, double* grad) {
-  // The adjoint of a linked entry is loaded with its partner's filter word
-  // (staging it with every scanned entry costs more than it saves).
+  // The adjoint of a linked entry is prefetched into L2 when the entry is
+  // queued and loaded with its partner's filter word (staging it with every
+  // scanned entry costs more than it saves).
   __shared__ LinkScratch<KT> s_w[kStepThreads / 32];
   const FactorT<KT> f = factors[k];
   const unsigned long long n = min(*((volatile unsigned long long*)&t.cnt->n_tail), t.cap_n);
@@ -159,7 +160,9 @@ __global__ void __launch_bounds__(kStepThreads, 8) k_reverse(TableT<KT> t, const
         const double mu = act ? t.lam[i] : 0.0;
         Lookup r = findG<G>(t, X ^ (f.occ | f.vir), act, stamp);
         if (act) reverse_resolve(t, f, k, stamp, i, X, cX, mu, ex, r, acc, pairs, kills);
-      });
+      },
+      // the adjoint of a queued entry moves towards L2 while the scan goes on
+      [&](unsigned long long i) { prefetch_l2(&t.lam[i]); });
   {
     // Entries this step removed (born at factor k) count as dropped, so the
     // host can compact the table when they pile up.

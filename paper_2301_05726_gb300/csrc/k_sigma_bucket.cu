@@ -200,43 +200,65 @@ constexpr size_t sb_smem_bytes() {
          (size_t)(3 * kSbBins + 2) * sizeof(unsigned int);
 }
 
-// Exclusive scans over the bins of a (n_b records) and b (n_b (n_b - 1)
-// ordered pairs) into sa and sb (kSbBins + 1 entries each, the totals last);
-// every thread of the block calls this.
-__device__ __forceinline__ void scan_bins(const unsigned int* cnt, unsigned int* sa, unsigned int* sb,
-                                          unsigned int* s_a, unsigned int* s_b) {
+// Exclusive scans over the bins of n_b records (into sa) and of n_b (n_b - 1)
+// ordered pairs (into sb), kSbBins + 1 entries each with the totals last; cnt
+// is overwritten with sa (the placement cursors).  Warp-shuffle scans, two
+// block barriers.  Every thread of the block calls this.
+__device__ __forceinline__ void scan_bins(unsigned int* cnt, unsigned int* sa, unsigned int* sb, unsigned int* s_wa,
+                                          unsigned int* s_wb) {
   constexpr int kPer = kSbBins / kSbThreads;
-  const unsigned int tid = threadIdx.x;
-  unsigned int ta = 0u, tb = 0u;
+  constexpr int kWarps = kSbThreads / 32;
+  const unsigned int tid = threadIdx.x, lane = tid & 31u, wid = tid >> 5;
+  unsigned int n[kPer], ta = 0u, tb = 0u;
 #pragma unroll
   for (int u = 0; u < kPer; ++u) {
-    const unsigned int n = cnt[tid * kPer + u];
-    ta += n;
-    tb += n * (n ? n - 1u : 0u);
+    n[u] = cnt[tid * kPer + u];
+    ta += n[u];
+    tb += n[u] * (n[u] ? n[u] - 1u : 0u);
   }
-  s_a[tid] = ta;
-  s_b[tid] = tb;
+  unsigned int ia = ta, ib = tb;  // inclusive within the warp
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const unsigned int ya = __shfl_up_sync(0xFFFFFFFFu, ia, d), yb = __shfl_up_sync(0xFFFFFFFFu, ib, d);
+    if (lane >= (unsigned int)d) {
+      ia += ya;
+      ib += yb;
+    }
+  }
+  if (lane == 31u) {
+    s_wa[wid] = ia;
+    s_wb[wid] = ib;
+  }
   __syncthreads();
-  for (int d = 1; d < kSbThreads; d <<= 1) {
-    const unsigned int xa = tid >= (unsigned int)d ? s_a[tid - d] : 0u;
-    const unsigned int xb = tid >= (unsigned int)d ? s_b[tid - d] : 0u;
-    __syncthreads();
-    s_a[tid] += xa;
-    s_b[tid] += xb;
-    __syncthreads();
+  if (wid == 0) {
+    unsigned int va = lane < (unsigned int)kWarps ? s_wa[lane] : 0u, vb = lane < (unsigned int)kWarps ? s_wb[lane] : 0u;
+    unsigned int xa = va, xb = vb;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const unsigned int ya = __shfl_up_sync(0xFFFFFFFFu, xa, d), yb = __shfl_up_sync(0xFFFFFFFFu, xb, d);
+      if (lane >= (unsigned int)d) {
+        xa += ya;
+        xb += yb;
+      }
+    }
+    if (lane < (unsigned int)kWarps) {
+      s_wa[lane] = xa - va;  // exclusive prefix of the warp totals
+      s_wb[lane] = xb - vb;
+    }
+    if (lane == (unsigned int)kWarps - 1u) {
+      sa[kSbBins] = xa;
+      sb[kSbBins] = xb;
+    }
   }
-  unsigned int ra = tid ? s_a[tid - 1] : 0u, rb = tid ? s_b[tid - 1] : 0u;
+  __syncthreads();
+  unsigned int ra = s_wa[wid] + ia - ta, rb = s_wb[wid] + ib - tb;
 #pragma unroll
   for (int u = 0; u < kPer; ++u) {
-    const unsigned int n = cnt[tid * kPer + u];
     sa[tid * kPer + u] = ra;
     sb[tid * kPer + u] = rb;
-    ra += n;
-    rb += n * (n ? n - 1u : 0u);
-  }
-  if (tid == kSbThreads - 1) {
-    sa[kSbBins] = ra;
-    sb[kSbBins] = rb;
+    cnt[tid * kPer + u] = ra;
+    ra += n[u];
+    rb += n[u] * (n[u] ? n[u] - 1u : 0u);
   }
 }
 
@@ -259,7 +281,7 @@ __global__ void __launch_bounds__(kSbThreads) k_sb_pairs(TableT<KT> t, Integrals
   unsigned int* cnt = reinterpret_cast<unsigned int*>(sp + kSbCap);  // counts, then placement cursors
   unsigned int* start = cnt + kSbBins;                                // kSbBins + 1: records before each bin
   unsigned int* pst = start + kSbBins + 1;                            // kSbBins + 1: ordered pairs before each bin
-  __shared__ unsigned int s_a[kSbThreads], s_b[kSbThreads];
+  __shared__ unsigned int s_a[kSbThreads / 32], s_b[kSbThreads / 32];
   const unsigned int tid = threadIdx.x;
   unsigned long long pairs = 0;
   for (unsigned long long p = p0 + blockIdx.x; p < p1; p += gridDim.x) {
@@ -275,8 +297,6 @@ __global__ void __launch_bounds__(kSbThreads) k_sb_pairs(TableT<KT> t, Integrals
     for (int x = (int)tid; x < mi; x += kSbThreads) atomicAdd(&cnt[bin_of(core_hash(rec[lo + x].K), log2p)], 1u);
     __syncthreads();
     scan_bins(cnt, start, pst, s_a, s_b);
-    __syncthreads();
-    for (int b = (int)tid; b < kSbBins; b += kSbThreads) cnt[b] = start[b];
     __syncthreads();
     for (int x = (int)tid; x < mi; x += kSbThreads) {
       const SigRecT<KT> r = rec[lo + (unsigned long long)x];

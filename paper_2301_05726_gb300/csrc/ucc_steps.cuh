@@ -471,10 +471,12 @@ __device__ __forceinline__ void drain_rest(LinkQueueT<KT, AUX>& q, int& qn, unsi
 // pre(i, active) for lone entries (loaded together with the filter word, so a
 // lone entry waits for a single round trip) and 0 for probed ones.  Every lane
 // of the warp calls this; lone and probe are called by all lanes together.
-template <bool AUX, class KT, class Pre, class Lone, class Probe>
+// hint(i) is called for each live linked entry i when it is queued (a
+// prefetch of what its resolution will load).
+template <bool AUX, class KT, class Pre, class Lone, class Probe, class Hint>
 __device__ __forceinline__ void for_each_linked(const TableT<KT>& t, const FactorT<KT>& f, unsigned long long n,
                                                 LinkScratchT<KT, AUX>& w, const double* aux, Pre pre, Lone lone,
-                                                Probe probe) {
+                                                Probe probe, Hint hint) {
   const unsigned int lane = threadIdx.x & 31u;
   const unsigned int below_me = (1u << lane) - 1u;
   const unsigned long long warp = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -529,6 +531,7 @@ __device__ __forceinline__ void for_each_linked(const TableT<KT>& t, const Facto
         }
       }
       const unsigned int ml = __ballot_sync(0xFFFFFFFFu, act);
+      if (act) hint(i);
       enqueue<KT, AUX>(w.linked, nl, ml, below_me, act, i, X, cX, ex, mu);
       nl += __popc(ml);
       if (nl >= 32) drain32<KT, AUX>(w.linked, nl, lane, split);
@@ -538,6 +541,18 @@ __device__ __forceinline__ void for_each_linked(const TableT<KT>& t, const Facto
   asm volatile("cp.async.wait_all;\n" ::: "memory");  // nothing left in flight
   if (nl > 0) drain_rest<KT, AUX>(w.linked, nl, lane, split);
   if (np > 0) drain_rest<KT, AUX>(w.probe, np, lane, probe);
+}
+
+template <bool AUX, class KT, class Pre, class Lone, class Probe>
+__device__ __forceinline__ void for_each_linked(const TableT<KT>& t, const FactorT<KT>& f, unsigned long long n,
+                                                LinkScratchT<KT, AUX>& w, const double* aux, Pre pre, Lone lone,
+                                                Probe probe) {
+  for_each_linked<AUX>(t, f, n, w, aux, pre, lone, probe, [](unsigned long long) {});
+}
+
+// Bring the line holding p into L2 (no register result, no wait).
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
 // (ab|cd) in chemist notation over spatial orbitals.

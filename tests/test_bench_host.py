@@ -44,11 +44,12 @@ def test_oracle_sample_reuses_a_fixed_prefix(monkeypatch):
     assert seen == [54] and nf == 54 and rate == 10 * 54 / 0.5 and evals == 2.0
 
 
-def test_traffic_is_scaled_from_algorithmic_bytes(monkeypatch):
-    monkeypatch.setattr(bench, "TRAFFIC_PER_ALGORITHMIC_BYTE", {"k_reverse": 1.5})
-    r = bench._roofline("k_reverse", 4e9, 10.0, 4, 6000.0, "measured")
-    assert r["traffic"] == 1.5 * 1e9
-    assert bench._roofline("k_sigma", 1e9, 10.0, 1, 6000.0, "measured")["traffic"] is None
+def test_traffic_is_scaled_by_the_entries_scanned(monkeypatch):
+    monkeypatch.setattr(bench, "TRAFFIC_PER_SCANNED_ENTRY", {"k_reverse": 47.0})
+    r = bench._roofline("k_reverse", 4e9, 10.0, 4, 6000.0, "measured", scanned=4e7)
+    assert r["traffic"] == 47.0 * 1e7
+    assert bench._roofline("energy", 1e9, 10.0, 1, 6000.0, "measured")["traffic"] is None
+    assert bench._roofline("k_reverse", 4e9, 10.0, 4, 6000.0, "measured")["traffic"] is None
 
 
 def test_member_model_charges_lone_rotations_one_member():
@@ -60,7 +61,9 @@ def test_member_model_charges_lone_rotations_one_member():
     assert m["member"]["k_forward"] == 8 * 1000 + 16 * 90 + 48 * 10 + 32 * 10
     assert m["pair"]["k_reverse"] == 8 * 1000 + 80 * 100
     assert m["member"]["k_reverse"] == 8 * 1000 + 32 * 80 + 80 * 20
-    assert m["member"]["k_sigma"] == m["pair"]["k_sigma"] == 24 * 50 + 16 * 7
+    assert m["member"]["energy"] == m["pair"]["energy"] == 24 * 50 + 16 * 7
+    tot.update(energy_route_last=2, sigma_probes=900)
+    assert bench.byte_models(tot)["member"]["energy"] == 64 * 900 + 40 * 50
 
 
 def test_host_info_names_the_cpu():
