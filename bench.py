@@ -255,7 +255,7 @@ def flush_l2(buf):
 # entries per launch, far larger than L2; the summary under profiles/ gives the command); a full-size
 # launch's traffic is taken as this figure times the entries it scans.  A kernel is left out (traffic
 # reported as null) once its code has changed since its capture.
-TRAFFIC_PER_SCANNED_ENTRY = {}
+TRAFFIC_PER_SCANNED_ENTRY = {"k_reverse": 47.3}
 
 
 def _roofline(kernel, bytes_, ms, launches, hbm, peak_kind, scanned=0):
