@@ -214,9 +214,10 @@ __global__ void __launch_bounds__(kThreads) k_rehash(TableT<KT> t) {
 }
 
 template <class KT>
-__global__ void k_finish_rebuild(TableT<KT> t) {
+__global__ void k_finish_rebuild(TableT<KT> t, unsigned long long expect) {
   Counters* c = t.cnt;
   const unsigned long long n = min(*((volatile unsigned long long*)&c->new_n), t.cap_n);
+  if (expect != ~0ull && n != expect) raise_consistency(c, SITE_CUT_COUNT, n);
   c->n_tail = n;
   c->n_scan = n;
   c->n_dead = 0;
@@ -316,8 +317,8 @@ cudaError_t launch_rehash(const TableT<KT>& t, int grid, cudaStream_t st) {
 }
 
 template <class KT>
-cudaError_t launch_finish_rebuild(const TableT<KT>& t, cudaStream_t st) {
-  k_finish_rebuild<KT><<<1, 1, 0, st>>>(t);
+cudaError_t launch_finish_rebuild(const TableT<KT>& t, unsigned long long expect, cudaStream_t st) {
+  k_finish_rebuild<KT><<<1, 1, 0, st>>>(t, expect);
   return cudaGetLastError();
 }
 
@@ -334,7 +335,7 @@ cudaError_t launch_export(const TableT<KT>& t, unsigned long long cap, KT* keys,
                                           const TapeT<KT>&, unsigned long long, int, int, cudaStream_t);           \
   template cudaError_t launch_compact<KT>(const TableT<KT>&, const TableT<KT>&, int, int, cudaStream_t);           \
   template cudaError_t launch_rehash<KT>(const TableT<KT>&, int, cudaStream_t);                                    \
-  template cudaError_t launch_finish_rebuild<KT>(const TableT<KT>&, cudaStream_t);                                 \
+  template cudaError_t launch_finish_rebuild<KT>(const TableT<KT>&, unsigned long long, cudaStream_t);                                 \
   template cudaError_t launch_export<KT>(const TableT<KT>&, unsigned long long, KT*, double*, double*, int,        \
                                          cudaStream_t);
 UCC_APPLY_INSTANTIATE(unsigned long long)

@@ -212,7 +212,12 @@ struct ucc_ctx {
   bool have_sigma = false;
   cudaEvent_t ev[6] = {};
   cudaEvent_t kev[2] = {};  // around each chunk of factor launches
-  cudaEvent_t rev_[2] = {};  // around each cut / rebuild
+  // Event pairs around cuts and rebuilds, read without waiting for them: the
+  // elapsed times are added to their totals when a pass ends (or the pool
+  // is full), so timing a cut costs the host no round trip.
+  std::vector<cudaEvent_t> tev;  // two per pair
+  std::vector<double*> tev_acc;  // the total each recorded pair adds to
+  size_t tev_used = 0;           // pairs recorded since the last flush
   ucc_stats stats{};
   int probe_width = 1;
   long long launches = 0;
@@ -386,10 +391,10 @@ ucc_status settle_spare(ucc_ctx* c, TableSet& s) {
 
 // Hash the compacted spare arrays `to` and make them the current ones.
 template <class KT>
-ucc_status finish_rebuild(ucc_ctx* c, TableSet& s, const TableT<KT>& to) {
+ucc_status finish_rebuild(ucc_ctx* c, TableSet& s, const TableT<KT>& to, unsigned long long expect = ~0ull) {
   const int grid = c->full_grid();
   CUDA_TRY(launch_rehash(to, grid, c->stream));
-  CUDA_TRY(launch_finish_rebuild(to, c->stream));
+  CUDA_TRY(launch_finish_rebuild(to, expect, c->stream));
   c->launches += 2;
   std::swap(s.cur, s.spare);
   // After growth the old, smaller arrays are not reused: free them now.
@@ -405,24 +410,56 @@ ucc_status finish_rebuild(ucc_ctx* c, TableSet& s, const TableT<KT>& to) {
 // rebuild the hash.  Counters are updated on the device.
 // Device time between the two events, added to *acc after the stream reaches
 // the second one.
-ucc_status add_elapsed(ucc_ctx* c, double* acc) {
-  float ms = 0.f;
-  CUDA_TRY(cudaEventSynchronize(c->rev_[1]));
-  CUDA_TRY(cudaEventElapsedTime(&ms, c->rev_[0], c->rev_[1]));
-  *acc += ms;
+constexpr size_t kTimingPairs = 256;
+
+// Stats are about to be reset: pairs a failed call left pending are dropped.
+void drop_timings(ucc_ctx* c) {
+  c->tev_used = 0;
+  c->tev_acc.clear();
+}
+
+// Add the elapsed times of the recorded pairs to their totals (waits for the
+// last one, which the stream reaches after all the others).
+ucc_status flush_timings(ucc_ctx* c) {
+  if (c->tev_used == 0) return UCC_OK;
+  CUDA_TRY(cudaEventSynchronize(c->tev[2 * c->tev_used - 1]));
+  for (size_t x = 0; x < c->tev_used; ++x) {
+    float ms = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&ms, c->tev[2 * x], c->tev[2 * x + 1]));
+    *c->tev_acc[x] += ms;
+  }
+  c->tev_used = 0;
+  c->tev_acc.clear();
+  return UCC_OK;
+}
+
+ucc_status timed_begin(ucc_ctx* c) {
+  if (c->tev_used == kTimingPairs) UCC_TRY(flush_timings(c));
+  while (c->tev.size() < 2 * (c->tev_used + 1)) {
+    cudaEvent_t e = nullptr;
+    CUDA_TRY(cudaEventCreate(&e));
+    c->tev.push_back(e);
+  }
+  CUDA_TRY(cudaEventRecord(c->tev[2 * c->tev_used], c->stream));
+  return UCC_OK;
+}
+
+ucc_status timed_end(ucc_ctx* c, double* acc) {
+  CUDA_TRY(cudaEventRecord(c->tev[2 * c->tev_used + 1], c->stream));
+  c->tev_acc.push_back(acc);
+  ++c->tev_used;
   return UCC_OK;
 }
 
 template <class KT>
 ucc_status rebuild(ucc_ctx* c, TableSet& s, unsigned long long new_cap, bool with_lam = false) {
   TableT<KT> to;
-  CUDA_TRY(cudaEventRecord(c->rev_[0], c->stream));
+  UCC_TRY(timed_begin(c));
   UCC_TRY(prepare_spare(c, s, new_cap, &to));
   CUDA_TRY(launch_compact(c->template table<KT>(s), to, with_lam ? 2 : 1, c->full_grid(), c->stream));
   c->launches++;
   UCC_TRY(finish_rebuild(c, s, to));
-  CUDA_TRY(cudaEventRecord(c->rev_[1], c->stream));
-  return add_elapsed(c, &c->stats.rebuild_ms);
+  return timed_end(c, &c->stats.rebuild_ms);
 }
 
 // The Methods-section cut after factor k: select the N_CUT-th entry, then one
@@ -432,7 +469,7 @@ ucc_status rebuild(ucc_ctx* c, TableSet& s, unsigned long long new_cap, bool wit
 template <class KT>
 ucc_status cut_rebuild(ucc_ctx* c, TableSet& s, bool record, int k) {
   const int grid = c->full_grid();
-  CUDA_TRY(cudaEventRecord(c->rev_[0], c->stream));
+  UCC_TRY(timed_begin(c));
   CUDA_TRY(launch_select_threshold(c->template table<KT>(s), c->d_sel, c->template dcand<KT>(),
                                    (unsigned long long)c->opt.n_cut, grid, c->stream, &c->launches));
   TableT<KT> to;
@@ -440,9 +477,9 @@ ucc_status cut_rebuild(ucc_ctx* c, TableSet& s, bool record, int k) {
   CUDA_TRY(launch_cut_compact(c->template table<KT>(s), to, c->d_sel, record ? 1 : 0, c->template tape<KT>(), k,
                               grid, c->stream));
   c->launches++;
-  UCC_TRY(finish_rebuild(c, s, to));
-  CUDA_TRY(cudaEventRecord(c->rev_[1], c->stream));
-  return add_elapsed(c, &c->stats.cut_ms);
+  // the kept count must be N_CUT (checked on the device: no round trip here)
+  UCC_TRY(finish_rebuild(c, s, to, (unsigned long long)c->opt.n_cut));
+  return timed_end(c, &c->stats.cut_ms);
 }
 
 // Grow the paged tape to hold `need` records (pages are added, never moved).
@@ -610,23 +647,32 @@ ucc_status autotune(ucc_ctx* c, TableSet& s, int k, unsigned long long n) {
 // Make room for the next factor: it may append one entry per stored entry
 // (and, in gradient runs, drop as many onto the tape).  Compacts when a
 // quarter of the stored entries are dropped ones.
+// Room for the next factor of table s, whose counters the host knows (*h,
+// updated here): grow or compact when the next factor might not fit or a
+// quarter of the stored entries are dropped; more kill tape when recording.
 template <class KT>
-ucc_status ensure_room(ucc_ctx* c, TableSet& s, bool record) {
-  UCC_TRY(read_counters(c, s));
-  const Counters h = *s.h_cnt;  // copy: later reads overwrite the mirror
-  const unsigned long long live = h.n_tail - h.n_dead;
+ucc_status ensure_room_known(ucc_ctx* c, TableSet& s, bool record, Counters* h) {
+  const unsigned long long live = h->n_tail - h->n_dead;
   if (c->opt.max_entries > 0 && live > (unsigned long long)c->opt.max_entries)
     return fail(UCC_ECAPACITY, "wavefunction exceeds max_entries (" + std::to_string(live) + " live)");
-  const bool room = 2 * h.n_tail <= s.cur.cap_n && 8 * h.n_tail <= 3 * s.cur.n_slots;
-  const bool sparse = h.n_dead > 4096 && h.n_dead * 4 > h.n_tail;
-  if (record) UCC_TRY(ensure_tape(c, h.tape_n + 2 * live + (1 << 12)));
+  const bool room = 2 * h->n_tail <= s.cur.cap_n && 8 * h->n_tail <= 3 * s.cur.n_slots;
+  const bool sparse = h->n_dead > 4096 && h->n_dead * 4 > h->n_tail;
+  if (record) UCC_TRY(ensure_tape(c, h->tape_n + 2 * live + (1 << 12)));
   if (!room || sparse) {
     unsigned long long cap = s.cur.cap_n;
     if (2 * live > cap || 8 * live > 3 * s.cur.n_slots) cap = std::max<unsigned long long>(5 * live / 2, 1 << 12);
     UCC_TRY(rebuild<KT>(c, s, cap));
-    UCC_TRY(read_counters(c, s));
+    h->n_tail = live;  // a compaction keeps exactly the live entries
+    h->n_dead = 0;
   }
   return UCC_OK;
+}
+
+template <class KT>
+ucc_status ensure_room(ucc_ctx* c, TableSet& s, bool record) {
+  UCC_TRY(read_counters(c, s));
+  Counters h = *s.h_cnt;  // copy: later reads overwrite the mirror
+  return ensure_room_known<KT>(c, s, record, &h);
 }
 
 // Factors [k0, k1) on table s.  The last block of each factor flags a stop
@@ -690,23 +736,27 @@ ucc_status run_factors(ucc_ctx* c, TableSet& s, double eps, bool record, int k0,
     if (h.stop_k >= 0) {
       const int resume = h.stop_k;
       if (resume <= k || resume > end) return fail(UCC_ECUDA, "invalid resume factor");
+      // The host follows the table's counters through the cut and any growth
+      // without reading them back: the cut keeps exactly N_CUT entries with
+      // none dropped (the device checks the count) and records the other live
+      // ones on the tape.
+      Counters known = h;
       if (h.cut_pending) {
-        const unsigned long long before = h.n_tail - h.n_dead;
+        const unsigned long long before = h.n_tail - h.n_dead, kept = (unsigned long long)c->opt.n_cut;
         UCC_TRY(cut_rebuild<KT>(c, s, record, resume - 1));
-        UCC_TRY(read_counters(c, s));
-        const unsigned long long after = s.h_cnt->n_tail - s.h_cnt->n_dead;
-        if (after != (unsigned long long)c->opt.n_cut)
-          return fail(UCC_ECUDA, "truncation kept " + std::to_string(after) + " entries, expected " +
-                                     std::to_string(c->opt.n_cut));
-        c->cut_total += (long long)(before - after);
+        known.n_tail = kept;
+        known.n_dead = 0;
+        if (record) known.tape_n = h.tape_n + (before - kept);
+        c->cut_total += (long long)(before - kept);
       }
-      UCC_TRY(ensure_room<KT>(c, s, record));
-      const int minus_one = -1, zero = 0;
-      CUDA_TRY(cudaMemcpyAsync(&s.d_cnt->stop_k, &minus_one, sizeof(int), cudaMemcpyHostToDevice, c->stream));
-      CUDA_TRY(cudaMemcpyAsync(&s.d_cnt->cut_pending, &zero, sizeof(int), cudaMemcpyHostToDevice, c->stream));
-      UCC_TRY(read_counters(c, s));
-      n_known = s.h_cnt->n_tail;
-      chunk = predicted_chunk(*s.h_cnt, s.cur.cap_n, s.cur.n_slots);
+      UCC_TRY(ensure_room_known<KT>(c, s, record, &known));
+      CUDA_TRY(cudaMemsetAsync(&s.d_cnt->stop_k, 0xFF, sizeof(int), c->stream));  // -1
+      CUDA_TRY(cudaMemsetAsync(&s.d_cnt->cut_pending, 0, sizeof(int), c->stream));
+      known.stop_k = -1;
+      known.cut_pending = 0;
+      *s.h_cnt = known;
+      n_known = known.n_tail;
+      chunk = predicted_chunk(known, s.cur.cap_n, s.cur.n_slots);
       k = resume;
       continue;
     }
@@ -714,7 +764,8 @@ ucc_status run_factors(ucc_ctx* c, TableSet& s, double eps, bool record, int k0,
     // Compact when a quarter of the stored entries are dropped ones.
     if (h.n_dead > 4096 && h.n_dead * 4 > h.n_tail) {
       UCC_TRY(rebuild<KT>(c, s, s.cur.cap_n));
-      UCC_TRY(read_counters(c, s));
+      s.h_cnt->n_tail = h.n_tail - h.n_dead;  // a compaction keeps exactly the live entries
+      s.h_cnt->n_dead = 0;
     }
     chunk = predicted_chunk(*s.h_cnt, s.cur.cap_n, s.cur.n_slots);
     k = end;
@@ -770,6 +821,7 @@ ucc_status run_forward(ucc_ctx* c, double eps, bool record) {
   }
   CUDA_TRY(cudaEventRecord(c->ev[1], c->stream));
   UCC_TRY(read_counters(c, s));
+  UCC_TRY(flush_timings(c));
   fill_forward_stats(c, *s.h_cnt);
   c->stats.tape_entries = (long long)s.h_cnt->tape_n;
   c->stats.capacity_entries = (long long)s.cur.cap_n;
@@ -1038,6 +1090,7 @@ ucc_status run_gradient(ucc_ctx* c, double eps, double* E, double* grad_out, int
 template <class KT>
 ucc_status run_gradient_once(ucc_ctx* c, double eps, double* E, double* grad_out, int on_device) {
   c->launches = 0;
+  drop_timings(c);
   c->stats = ucc_stats{};
   c->main = 0;
   UCC_TRY(run_forward<KT>(c, eps, true));
@@ -1084,6 +1137,7 @@ ucc_status run_gradient_once(ucc_ctx* c, double eps, double* E, double* grad_out
                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
   }
   UCC_TRY(read_counters(c, c->ts[c->main]));
+  UCC_TRY(flush_timings(c));
   float ms = 0.f;
   CUDA_TRY(cudaEventElapsedTime(&ms, c->ev[4], c->ev[5]));
   c->stats.reverse_ms = ms;
@@ -1188,7 +1242,7 @@ void destroy(ucc_ctx* c) {
     if (e) cudaEventDestroy(e);
   for (auto& e : c->kev)
     if (e) cudaEventDestroy(e);
-  for (auto& e : c->rev_)
+  for (auto& e : c->tev)
     if (e) cudaEventDestroy(e);
   delete c;
 }
@@ -1352,6 +1406,7 @@ ucc_status batch_persistent(const std::vector<int>& idx, ucc_ctx* const* jobs, d
     for (int x = 0; x < n; ++x) {
       ucc_ctx* c = jobs[idx[x]];
       c->launches = 0;
+      drop_timings(c);
       c->stats = ucc_stats{};
       c->cut_total = 0;
       c->tape_budget = 0;
@@ -1634,8 +1689,6 @@ ucc_status ucc_create(const ucc_hamiltonian* ham, const ucc_ansatz* an, void* cu
     if (cudaEventCreate(&e) != cudaSuccess) return bail(fail(UCC_ECUDA, "event creation failed"));
   for (auto& e : c->kev)
     if (cudaEventCreate(&e) != cudaSuccess) return bail(fail(UCC_ECUDA, "event creation failed"));
-  for (auto& e : c->rev_)
-    if (cudaEventCreate(&e) != cudaSuccess) return bail(fail(UCC_ECUDA, "event creation failed"));
   if (cudaMemcpyAsync(c->d_h, ham->h, n * n * sizeof(double), cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
       cudaMemcpyAsync(c->d_g, ham->g, n * n * n * n * sizeof(double), cudaMemcpyHostToDevice, c->stream) !=
           cudaSuccess)
@@ -1685,6 +1738,7 @@ ucc_status ucc_apply(ucc_ctx* c, double eps) {
   if (!c) return fail(UCC_EINVAL, "null context");
   CUDA_TRY(cudaSetDevice(c->device));
   c->launches = 0;
+  drop_timings(c);
   c->stats = ucc_stats{};
   UCC_TRY(c->wide ? run_forward<Key128>(c, eps, false) : run_forward<unsigned long long>(c, eps, false));
   c->stats.kernel_launches = c->launches;
@@ -1793,6 +1847,7 @@ ucc_status ucc_batch_run(int n_jobs, ucc_ctx* const* jobs, double eps, double* E
                         : run_gradient<unsigned long long>(c, eps, &E[j], grads[j], 0));
       } else {
         c->launches = 0;
+        drop_timings(c);
         c->stats = ucc_stats{};
         if (c->wide) {
           UCC_TRY(run_forward<Key128>(c, eps, false));

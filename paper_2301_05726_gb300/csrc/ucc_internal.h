@@ -71,7 +71,8 @@ enum ErrSite : int {
   SITE_BATCH_ALIVE = 6,   // the same, persistent batched reverse
   SITE_CREATE_DUP = 7,    // a created partner's key was already hashed
   SITE_REINSERT_DUP = 8,  // a re-inserted record's key was already hashed
-  SITE_REBUILD_DUP = 9    // a compaction kept a key twice
+  SITE_REBUILD_DUP = 9,   // a compaction kept a key twice
+  SITE_CUT_COUNT = 10     // a cut kept other than N_CUT entries (err_key: the count kept)
 };
 
 enum DeviceError : int {
@@ -255,7 +256,7 @@ cudaError_t launch_compact(const TableT<KT>& from, const TableT<KT>& to, int wit
 template <class KT>
 cudaError_t launch_rehash(const TableT<KT>& t, int grid, cudaStream_t st);
 template <class KT>
-cudaError_t launch_finish_rebuild(const TableT<KT>& t, cudaStream_t st);
+cudaError_t launch_finish_rebuild(const TableT<KT>& t, unsigned long long expect, cudaStream_t st);
 template <class KT>
 cudaError_t launch_export(const TableT<KT>& t, unsigned long long cap, KT* keys, double* amps, double* sigma,
                           int grid, cudaStream_t st);
