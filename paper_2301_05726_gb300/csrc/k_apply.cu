@@ -5,6 +5,8 @@
 // 16-byte slots {key, index} for partner lookups, and (gradient runs) born[]
 // (uint32, the factor that created each entry) plus an append-only kill tape.
 
+#include <algorithm>
+
 #include "ucc_steps.cuh"
 
 namespace ucc {
@@ -226,6 +228,105 @@ __global__ void k_finish_rebuild(TableT<KT> t, unsigned long long expect) {
   if (c->stop_k >= 0 && 2ull * n <= t.cap_n && 8ull * n <= 3ull * slots) c->stop_k = -1;
 }
 
+// Hash build by regions.  Inserting entries in table order claims one random
+// slot each (a DRAM sector read and written per entry); bucketing the entries
+// by the region of 2^kRegionBits slots their home slot falls in first lets one
+// block build each region in shared memory and write it out whole.  Linear
+// probing that runs past a region's end continues, after every region is
+// written, at the next region's first slot (all slots it passed are full).
+constexpr int kRegionSlots = 1 << kRegionBits;
+constexpr int kRegionThreads = 512;
+
+__device__ __forceinline__ unsigned long long region_of(const Table& t, unsigned long long key) {
+  return home_slot(t, key) >> kRegionBits;
+}
+
+__global__ void __launch_bounds__(kThreads) k_rr_count(Table t, unsigned int* __restrict__ rcnt) {
+  const unsigned long long n = min(*((volatile unsigned long long*)&t.cnt->new_n), t.cap_n);
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    atomicAdd(&rcnt[region_of(t, t.keys[i])], 1u);
+}
+
+__global__ void __launch_bounds__(kThreads) k_rr_scatter(Table t, const unsigned long long* __restrict__ roff,
+                                                         unsigned int* __restrict__ rfill,
+                                                         unsigned long long* __restrict__ pairs) {
+  const unsigned long long n = min(*((volatile unsigned long long*)&t.cnt->new_n), t.cap_n);
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const unsigned long long key = t.keys[i];
+    const unsigned long long r = region_of(t, key);
+    const unsigned long long at = roff[r] + atomicAdd(&rfill[r], 1u);
+    if (at >= roff[r + 1]) {  // more entries than counted: never written past the region's share
+      raise_error(t.cnt, ERR_CAPACITY);
+      continue;
+    }
+    *reinterpret_cast<ulonglong2*>(pairs + 2 * at) = make_ulonglong2(key, i);
+  }
+}
+
+// One block per region (grid-stride): the region's slots in shared memory,
+// its pairs inserted by linear probing with shared-memory CAS, then every slot
+// of the region written (empty ones as zero) and the keys added to the
+// filter.  A probe that reaches the region's end goes to the overflow list.
+__global__ void __launch_bounds__(kRegionThreads) k_rr_build(Table t, const unsigned long long* __restrict__ roff,
+                                                             const unsigned long long* __restrict__ pairs,
+                                                             unsigned long long* __restrict__ over,
+                                                             unsigned long long* __restrict__ over_n,
+                                                             unsigned long long regions) {
+  extern __shared__ __align__(16) unsigned char rr_smem[];
+  unsigned long long* sk = reinterpret_cast<unsigned long long*>(rr_smem);
+  unsigned int* si = reinterpret_cast<unsigned int*>(sk + kRegionSlots);
+  for (unsigned long long r = blockIdx.x; r < regions; r += gridDim.x) {
+    for (int x = (int)threadIdx.x; x < kRegionSlots; x += kRegionThreads) sk[x] = 0ull;
+    __syncthreads();
+    const unsigned long long lo = roff[r], hi = roff[r + 1];
+    for (unsigned long long p = lo + threadIdx.x; p < hi; p += kRegionThreads) {
+      const ulonglong2 kv = *reinterpret_cast<const ulonglong2*>(pairs + 2 * p);
+      int h = (int)(home_slot(t, kv.x) & (unsigned long long)(kRegionSlots - 1));
+      for (;;) {
+        const unsigned long long prev = atomicCAS(&sk[h], 0ull, kv.x);
+        if (prev == 0ull) {
+          si[h] = (unsigned int)kv.y;
+          break;
+        }
+        if (prev == kv.x) {
+          raise_consistency(t.cnt, SITE_REHASH_DUP, kv.x);
+          break;
+        }
+        if (++h == kRegionSlots) {
+          const unsigned long long o = atomicAdd(over_n, 1ull);
+          *reinterpret_cast<ulonglong2*>(over + 2 * o) = kv;
+          break;
+        }
+      }
+    }
+    __syncthreads();
+    Slot* out = t.slots + (r << kRegionBits);
+    for (int x = (int)threadIdx.x; x < kRegionSlots; x += kRegionThreads) {
+      const unsigned long long key = sk[x];
+      Slot sl;
+      sl.key = key;
+      sl.idx = key ? (unsigned long long)si[x] : 0ull;
+      out[x] = sl;
+      if (key) filter_add(t, key);
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_rr_overflow(Table t, const unsigned long long* __restrict__ over,
+                                                          const unsigned long long* __restrict__ over_n) {
+  const unsigned long long n = *over_n;
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long o = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += stride) {
+    const ulonglong2 kv = *reinterpret_cast<const ulonglong2*>(over + 2 * o);
+    const unsigned long long next = (region_of(t, kv.x) + 1ull) << kRegionBits;
+    const unsigned long long s = claim_slot(t, kv.x, next, SITE_REHASH_DUP);
+    if (s != ~0ull) t.slots[s].idx = kv.y;
+  }
+}
+
 // Gather live entries into caller buffers (unordered).
 template <class KT>
 __global__ void __launch_bounds__(kThreads) k_export(TableT<KT> t, unsigned long long cap, KT* keys, double* amps,
@@ -313,6 +414,29 @@ cudaError_t launch_compact(const TableT<KT>& from, const TableT<KT>& to, int wit
 template <class KT>
 cudaError_t launch_rehash(const TableT<KT>& t, int grid, cudaStream_t st) {
   k_rehash<KT><<<grid, kThreads, 0, st>>>(t);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rehash_regions(const Table& t, const RehashScratch& rs, int grid, int num_sms, cudaStream_t st) {
+  constexpr size_t smem = (size_t)kRegionSlots * (sizeof(unsigned long long) + sizeof(unsigned int));
+  static bool attr = false;
+  if (!attr) {
+    const cudaError_t e = cudaFuncSetAttribute(k_rr_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const unsigned long long regions = (t.slot_mask + 1ull) >> kRegionBits;
+  if (regions == 0 || regions > rs.regions) return cudaErrorInvalidValue;
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(rs.rcnt, 0, regions * sizeof(unsigned int), st)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(rs.rfill, 0, regions * sizeof(unsigned int), st)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(rs.over_n, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;
+  k_rr_count<<<grid, kThreads, 0, st>>>(t, rs.rcnt);
+  if ((e = launch_sb_scan(rs.rcnt, rs.roff, regions, st)) != cudaSuccess) return e;
+  k_rr_scatter<<<grid, kThreads, 0, st>>>(t, rs.roff, rs.rfill, rs.pairs);
+  const int bgrid = (int)std::min<unsigned long long>(regions, (unsigned long long)(2 * num_sms));
+  k_rr_build<<<bgrid, kRegionThreads, smem, st>>>(t, rs.roff, rs.pairs, rs.over, rs.over_n, regions);
+  k_rr_overflow<<<std::max(1, num_sms), kThreads, 0, st>>>(t, rs.over, rs.over_n);
   return cudaGetLastError();
 }
 

@@ -191,6 +191,7 @@ struct ucc_ctx {
   unsigned long long sb_parts = 0;
   unsigned char* d_sb_rec = nullptr;
   size_t sb_rec_cap = 0;  // bytes
+  RehashScratch rs;       // hash builds by regions
   SelectState* d_sel = nullptr;
   void* d_cand = nullptr;  // SelectCandT<KT>[kSelectCandCap]: candidates of the cut's last selection passes
   double* d_entropy = nullptr;  // [K] Eq. 6 after each factor of the last apply
@@ -322,6 +323,36 @@ unsigned long long slots_for(unsigned long long cap_n) {
   return next_pow2(std::max<unsigned long long>(64, (cap_n * 4 + 2) / 3));
 }
 
+// Tables whose hash is built by regions: one-word keys and at least 2^20
+// slots.  Their slot arrays need no clearing (every slot is written).
+bool regions_ok(const ucc_ctx* c, unsigned long long n_slots) { return !c->wide && n_slots >= (1ull << 20); }
+
+// Scratch of the region build for a table of cap entries and n_slots slots.
+ucc_status ensure_rehash_scratch(ucc_ctx* c, unsigned long long cap, unsigned long long n_slots) {
+  RehashScratch& r = c->rs;
+  const unsigned long long regions = n_slots >> kRegionBits;
+  if (r.regions < regions) {
+    dfree(r.rcnt);
+    dfree(r.rfill);
+    dfree(r.roff);
+    r.regions = 0;
+    UCC_TRY(dalloc(&r.rcnt, regions));
+    UCC_TRY(dalloc(&r.rfill, regions));
+    UCC_TRY(dalloc(&r.roff, regions + 1));
+    r.regions = regions;
+  }
+  if (!r.over_n) UCC_TRY(dalloc(&r.over_n, 1));
+  if (r.cap < cap) {
+    dfree(r.pairs);
+    dfree(r.over);
+    r.cap = 0;
+    UCC_TRY(dalloc(&r.pairs, 2 * cap));
+    UCC_TRY(dalloc(&r.over, 2 * cap));
+    r.cap = cap;
+  }
+  return UCC_OK;
+}
+
 // The spare arrays of table s, sized for new_cap entries and cleared, as the
 // target of a compaction; finish_rebuild hashes them and swaps them in.
 template <class KT>
@@ -361,7 +392,7 @@ ucc_status prepare_spare(ucc_ctx* c, TableSet& s, unsigned long long new_cap, Ta
   to.cap_n = new_cap;
   CUDA_TRY(cudaMemsetAsync(&s.d_cnt->new_n, 0, sizeof(unsigned long long), c->stream));
   if (!cleared) {
-    CUDA_TRY(cudaMemsetAsync(to.slots, 0, ns * sizeof(SlotT<KT>), c->stream));
+    if (!regions_ok(c, ns)) CUDA_TRY(cudaMemsetAsync(to.slots, 0, ns * sizeof(SlotT<KT>), c->stream));
     CUDA_TRY(cudaMemsetAsync(to.filt, 0, ns / 4 * sizeof(unsigned int), c->stream));
   }
   *out = to;
@@ -374,7 +405,8 @@ ucc_status clear_spare_async(ucc_ctx* c, TableSet& s) {
   if (!c->side || s.spare.cap_n == 0) return UCC_OK;
   CUDA_TRY(cudaEventRecord(s.clean, c->stream));
   CUDA_TRY(cudaStreamWaitEvent(c->side, s.clean, 0));
-  CUDA_TRY(cudaMemsetAsync(s.spare.slots, 0, s.spare.n_slots * s.spare.kw * sizeof(Slot), c->side));
+  if (!regions_ok(c, s.spare.n_slots))
+    CUDA_TRY(cudaMemsetAsync(s.spare.slots, 0, s.spare.n_slots * s.spare.kw * sizeof(Slot), c->side));
   CUDA_TRY(cudaMemsetAsync(s.spare.filt, 0, s.spare.n_slots / 4 * sizeof(unsigned int), c->side));
   CUDA_TRY(cudaEventRecord(s.clean, c->side));
   s.clean_pending = true;
@@ -393,9 +425,26 @@ ucc_status settle_spare(ucc_ctx* c, TableSet& s) {
 template <class KT>
 ucc_status finish_rebuild(ucc_ctx* c, TableSet& s, const TableT<KT>& to, unsigned long long expect = ~0ull) {
   const int grid = c->full_grid();
-  CUDA_TRY(launch_rehash(to, grid, c->stream));
+  const unsigned long long ns = to.slot_mask + 1ull;
+  bool by_regions = false;
+  if constexpr (sizeof(KT) == 8) {
+    if (regions_ok(c, ns)) {
+      if (ensure_rehash_scratch(c, to.cap_n, ns) == UCC_OK) {
+        CUDA_TRY(launch_rehash_regions(to, c->rs, grid, c->num_sms, c->stream));
+        c->launches += 5;
+        by_regions = true;
+      } else {
+        cudaGetLastError();  // a failed scratch allocation: the direct rehash needs a cleared slot array
+        CUDA_TRY(cudaMemsetAsync(to.slots, 0, ns * sizeof(SlotT<KT>), c->stream));
+      }
+    }
+  }
+  if (!by_regions) {
+    CUDA_TRY(launch_rehash(to, grid, c->stream));
+    c->launches++;
+  }
   CUDA_TRY(launch_finish_rebuild(to, expect, c->stream));
-  c->launches += 2;
+  c->launches += 1;
   std::swap(s.cur, s.spare);
   // After growth the old, smaller arrays are not reused: free them now.
   if (s.spare.cap_n != s.cur.cap_n)
@@ -1232,6 +1281,12 @@ void destroy(ucc_ctx* c) {
   dfree(c->d_sb_fill);
   dfree(c->d_sb_off);
   dfree(c->d_sb_rec);
+  dfree(c->rs.rcnt);
+  dfree(c->rs.rfill);
+  dfree(c->rs.roff);
+  dfree(c->rs.pairs);
+  dfree(c->rs.over);
+  dfree(c->rs.over_n);
   dfree(c->d_sel);
   dfree(c->d_cand);
   release_tape(c);

@@ -255,6 +255,27 @@ template <class KT>
 cudaError_t launch_compact(const TableT<KT>& from, const TableT<KT>& to, int with_born, int grid, cudaStream_t st);
 template <class KT>
 cudaError_t launch_rehash(const TableT<KT>& t, int grid, cudaStream_t st);
+
+// Scratch of the hash build by regions (one-word keys): per region of
+// 2^kRegionBits slots its entry count, fill counter and offset, the (key,
+// index) pairs bucketed by region, and the pairs whose probe runs past their
+// region's end.
+constexpr int kRegionBits = 13;
+struct RehashScratch {
+  unsigned int* rcnt = nullptr;         // [regions]
+  unsigned int* rfill = nullptr;        // [regions]
+  unsigned long long* roff = nullptr;   // [regions + 1]
+  unsigned long long* pairs = nullptr;  // [2 * cap]
+  unsigned long long* over = nullptr;   // [2 * cap]
+  unsigned long long* over_n = nullptr; // [1]
+  unsigned long long cap = 0, regions = 0;
+};
+// Hash the first new_n entries of t (a cleared slot array is not needed: every
+// slot is written) by regions: count, prefix sum, bucket, build each region in
+// shared memory, then claim slots for the overflow.  Needs
+// t.slot_mask + 1 >= 2^kRegionBits and scratch for t.cap_n entries.
+cudaError_t launch_rehash_regions(const TableT<unsigned long long>& t, const RehashScratch& rs, int grid,
+                                  int num_sms, cudaStream_t st);
 template <class KT>
 cudaError_t launch_finish_rebuild(const TableT<KT>& t, unsigned long long expect, cudaStream_t st);
 template <class KT>
