@@ -123,6 +123,13 @@ typedef struct {
   int32_t energy_test_buffer_records; /* test only: cap on the records one
                                          round of the bucketed energy holds
                                          (0 = sized by the library) */
+  int32_t rebuild_test_regions; /* test only: hash builds by regions (one-word
+                                   keys): 0 = for tables of at least 2^20
+                                   slots (and bulk re-insertions of at least
+                                   one record per eight slots), 1 = never,
+                                   2 = for every table of at least 8,192 slots
+                                   and every bulk re-insertion */
+  int32_t pad_;
 } ucc_options;
 
 /* Counters of the last apply / gradient call. */

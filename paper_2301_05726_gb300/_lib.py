@@ -38,7 +38,8 @@ class Options(ctypes.Structure):
                 ("tape_budget_mb", ctypes.c_int32), ("record_entropy", ctypes.c_int32),
                 ("batch_wait_ms", ctypes.c_int32), ("batch_test_skip_block", ctypes.c_int32),
                 ("batch_tiles", ctypes.c_int32), ("energy_route", ctypes.c_int32),
-                ("energy_test_partitions", ctypes.c_int32), ("energy_test_buffer_records", ctypes.c_int32)]
+                ("energy_test_partitions", ctypes.c_int32), ("energy_test_buffer_records", ctypes.c_int32),
+                ("rebuild_test_regions", ctypes.c_int32), ("pad_", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):

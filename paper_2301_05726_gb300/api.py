@@ -55,7 +55,8 @@ class UCCContext:
         self._opt = dict(n_max=int(getattr(prob, "n_max", 0)), n_cut=int(getattr(prob, "n_cut", 0)),
                          max_entries=int(max_entries), probe_width=int(probe_width), checkpoint_stride=0,
                          tape_budget_mb=0, record_entropy=0, batch_wait_ms=0, batch_test_skip_block=0,
-                         batch_tiles=0, energy_route=0, energy_test_partitions=0, energy_test_buffer_records=0)
+                         batch_tiles=0, energy_route=0, energy_test_partitions=0, energy_test_buffer_records=0,
+                         rebuild_test_regions=0)
         self.set_options()
 
     def close(self):
@@ -70,7 +71,7 @@ class UCCContext:
         """Update run options (the rest keep their values): n_max, n_cut,
         max_entries, probe_width, checkpoint_stride, tape_budget_mb,
         record_entropy, batch_wait_ms, batch_test_skip_block, batch_tiles, energy_route,
-        energy_test_partitions, energy_test_buffer_records.  The problem's
+        energy_test_partitions, energy_test_buffer_records, rebuild_test_regions.  The problem's
         own cut is the starting point."""
         unknown = set(changes) - set(self._opt)
         if unknown:
@@ -80,7 +81,7 @@ class UCCContext:
         o = Options(o["n_max"], o["n_cut"], o["max_entries"], o["probe_width"], o["checkpoint_stride"],
                     o["tape_budget_mb"], o["record_entropy"], o["batch_wait_ms"], o["batch_test_skip_block"],
                     o["batch_tiles"], o["energy_route"], o["energy_test_partitions"],
-                    o["energy_test_buffer_records"])
+                    o["energy_test_buffer_records"], o["rebuild_test_regions"], 0)
         check(self.lib.ucc_set_options(self.handle, ctypes.byref(o)))
 
     def set_theta(self, theta):

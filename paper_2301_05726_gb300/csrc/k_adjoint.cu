@@ -193,15 +193,28 @@ __global__ void __launch_bounds__(kStepThreads, 8) k_reverse(TableT<KT> t, const
 
 template <class KT>
 cudaError_t launch_tape_reinsert(const TableT<KT>& t, const TapeT<KT>& tape, int k, unsigned long long records,
-                                 int grid, cudaStream_t st, long long* launches) {
+                                 int grid, cudaStream_t st, long long* launches, const RehashScratch* rs,
+                                 int num_sms) {
   if (records < kBulkRecords) {
     k_tape_reinsert<KT><<<grid, kThreads, 0, st>>>(t, tape, k);
     *launches += 1;
   } else {
     k_mark_tail<KT><<<1, 32, 0, st>>>(t);
     k_tape_append<KT><<<grid, kThreads, 0, st>>>(t, tape, k);
-    k_link_tail<KT><<<grid, kThreads, 0, st>>>(t);
-    *launches += 3;
+    bool merged = false;
+    if constexpr (sizeof(KT) == 8) {
+      if (rs != nullptr) {
+        // the appended range hashed region by region into the existing hash
+        const cudaError_t e = launch_rehash_regions(t, *rs, grid, num_sms, st, true);
+        if (e != cudaSuccess) return e;
+        *launches += 7;
+        merged = true;
+      }
+    }
+    if (!merged) {
+      k_link_tail<KT><<<grid, kThreads, 0, st>>>(t);
+      *launches += 3;
+    }
   }
   return cudaGetLastError();
 }
@@ -233,7 +246,7 @@ cudaError_t launch_reverse(const TableT<KT>& t, const FactorT<KT>* factors, int 
 
 #define UCC_ADJOINT_INSTANTIATE(KT)                                                                               \
   template cudaError_t launch_tape_reinsert<KT>(const TableT<KT>&, const TapeT<KT>&, int, unsigned long long, int, \
-                                                cudaStream_t, long long*);                                       \
+                                                cudaStream_t, long long*, const RehashScratch*, int);            \
   template cudaError_t launch_reverse<KT>(const TableT<KT>&, const FactorT<KT>*, int, unsigned int, double*, int,  \
                                           int, cudaStream_t);
 UCC_ADJOINT_INSTANTIATE(unsigned long long)

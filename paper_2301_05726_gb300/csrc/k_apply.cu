@@ -241,19 +241,33 @@ __device__ __forceinline__ unsigned long long region_of(const Table& t, unsigned
   return home_slot(t, key) >> kRegionBits;
 }
 
-__global__ void __launch_bounds__(kThreads) k_rr_count(Table t, unsigned int* __restrict__ rcnt) {
-  const unsigned long long n = min(*((volatile unsigned long long*)&t.cnt->new_n), t.cap_n);
+// The entries a build hashes: a rebuild's [0, new_n), or (merge) the range
+// appended since k_mark_tail, [link_from, n_tail), into the existing hash.
+__device__ __forceinline__ void rr_range(const Table& t, bool merge, unsigned long long* lo, unsigned long long* hi) {
+  if (merge) {
+    *hi = min(*((volatile unsigned long long*)&t.cnt->n_tail), t.cap_n);
+    *lo = min(*((volatile unsigned long long*)&t.cnt->link_from), *hi);
+  } else {
+    *lo = 0ull;
+    *hi = min(*((volatile unsigned long long*)&t.cnt->new_n), t.cap_n);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_rr_count(Table t, unsigned int* __restrict__ rcnt, bool merge) {
+  unsigned long long lo, n;
+  rr_range(t, merge, &lo, &n);
   const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+  for (unsigned long long i = lo + (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
     atomicAdd(&rcnt[region_of(t, t.keys[i])], 1u);
 }
 
 __global__ void __launch_bounds__(kThreads) k_rr_scatter(Table t, const unsigned long long* __restrict__ roff,
                                                          unsigned int* __restrict__ rfill,
-                                                         unsigned long long* __restrict__ pairs) {
-  const unsigned long long n = min(*((volatile unsigned long long*)&t.cnt->new_n), t.cap_n);
+                                                         unsigned long long* __restrict__ pairs, bool merge) {
+  unsigned long long lo, n;
+  rr_range(t, merge, &lo, &n);
   const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+  for (unsigned long long i = lo + (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     const unsigned long long key = t.keys[i];
     const unsigned long long r = region_of(t, key);
     const unsigned long long at = roff[r] + atomicAdd(&rfill[r], 1u);
@@ -265,22 +279,35 @@ __global__ void __launch_bounds__(kThreads) k_rr_scatter(Table t, const unsigned
   }
 }
 
-// One block per region (grid-stride): the region's slots in shared memory,
-// its pairs inserted by linear probing with shared-memory CAS, then every slot
-// of the region written (empty ones as zero) and the keys added to the
-// filter.  A probe that reaches the region's end goes to the overflow list.
+// One block per region (grid-stride): the region's slots in shared memory
+// (empty, or with merge the hash's current slots), its pairs inserted by
+// linear probing with shared-memory CAS (each new key added to the filter),
+// then every slot of the region written back.  A probe that reaches the
+// region's end goes to the overflow list.  A key met twice is an error in a
+// rebuild and left as it is in a merge (insert-if-absent).  With merge a
+// region without new pairs is left untouched.
 __global__ void __launch_bounds__(kRegionThreads) k_rr_build(Table t, const unsigned long long* __restrict__ roff,
                                                              const unsigned long long* __restrict__ pairs,
                                                              unsigned long long* __restrict__ over,
                                                              unsigned long long* __restrict__ over_n,
-                                                             unsigned long long regions) {
+                                                             unsigned long long regions, bool merge) {
   extern __shared__ __align__(16) unsigned char rr_smem[];
   unsigned long long* sk = reinterpret_cast<unsigned long long*>(rr_smem);
   unsigned int* si = reinterpret_cast<unsigned int*>(sk + kRegionSlots);
   for (unsigned long long r = blockIdx.x; r < regions; r += gridDim.x) {
-    for (int x = (int)threadIdx.x; x < kRegionSlots; x += kRegionThreads) sk[x] = 0ull;
-    __syncthreads();
     const unsigned long long lo = roff[r], hi = roff[r + 1];
+    if (merge && lo == hi) continue;
+    Slot* out = t.slots + (r << kRegionBits);
+    for (int x = (int)threadIdx.x; x < kRegionSlots; x += kRegionThreads) {
+      if (merge) {
+        const Slot sl = out[x];
+        sk[x] = sl.key;
+        si[x] = (unsigned int)sl.idx;
+      } else {
+        sk[x] = 0ull;
+      }
+    }
+    __syncthreads();
     for (unsigned long long p = lo + threadIdx.x; p < hi; p += kRegionThreads) {
       const ulonglong2 kv = *reinterpret_cast<const ulonglong2*>(pairs + 2 * p);
       int h = (int)(home_slot(t, kv.x) & (unsigned long long)(kRegionSlots - 1));
@@ -288,10 +315,11 @@ __global__ void __launch_bounds__(kRegionThreads) k_rr_build(Table t, const unsi
         const unsigned long long prev = atomicCAS(&sk[h], 0ull, kv.x);
         if (prev == 0ull) {
           si[h] = (unsigned int)kv.y;
+          filter_add(t, kv.x);
           break;
         }
         if (prev == kv.x) {
-          raise_consistency(t.cnt, SITE_REHASH_DUP, kv.x);
+          if (!merge) raise_consistency(t.cnt, SITE_REHASH_DUP, kv.x);
           break;
         }
         if (++h == kRegionSlots) {
@@ -302,28 +330,30 @@ __global__ void __launch_bounds__(kRegionThreads) k_rr_build(Table t, const unsi
       }
     }
     __syncthreads();
-    Slot* out = t.slots + (r << kRegionBits);
     for (int x = (int)threadIdx.x; x < kRegionSlots; x += kRegionThreads) {
       const unsigned long long key = sk[x];
       Slot sl;
       sl.key = key;
       sl.idx = key ? (unsigned long long)si[x] : 0ull;
       out[x] = sl;
-      if (key) filter_add(t, key);
     }
     __syncthreads();
   }
 }
 
 __global__ void __launch_bounds__(kThreads) k_rr_overflow(Table t, const unsigned long long* __restrict__ over,
-                                                          const unsigned long long* __restrict__ over_n) {
+                                                          const unsigned long long* __restrict__ over_n, bool merge) {
   const unsigned long long n = *over_n;
   const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
   for (unsigned long long o = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += stride) {
     const ulonglong2 kv = *reinterpret_cast<const ulonglong2*>(over + 2 * o);
     const unsigned long long next = (region_of(t, kv.x) + 1ull) << kRegionBits;
-    const unsigned long long s = claim_slot(t, kv.x, next, SITE_REHASH_DUP);
-    if (s != ~0ull) t.slots[s].idx = kv.y;
+    if (merge) {
+      link_from_slot(t, kv.x, kv.y, next);
+    } else {
+      const unsigned long long s = claim_slot(t, kv.x, next, SITE_REHASH_DUP);
+      if (s != ~0ull) t.slots[s].idx = kv.y;
+    }
   }
 }
 
@@ -417,7 +447,8 @@ cudaError_t launch_rehash(const TableT<KT>& t, int grid, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_rehash_regions(const Table& t, const RehashScratch& rs, int grid, int num_sms, cudaStream_t st) {
+cudaError_t launch_rehash_regions(const Table& t, const RehashScratch& rs, int grid, int num_sms, cudaStream_t st,
+                                  bool merge) {
   constexpr size_t smem = (size_t)kRegionSlots * (sizeof(unsigned long long) + sizeof(unsigned int));
   static bool attr = false;
   if (!attr) {
@@ -431,12 +462,12 @@ cudaError_t launch_rehash_regions(const Table& t, const RehashScratch& rs, int g
   if ((e = cudaMemsetAsync(rs.rcnt, 0, regions * sizeof(unsigned int), st)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(rs.rfill, 0, regions * sizeof(unsigned int), st)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(rs.over_n, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;
-  k_rr_count<<<grid, kThreads, 0, st>>>(t, rs.rcnt);
+  k_rr_count<<<grid, kThreads, 0, st>>>(t, rs.rcnt, merge);
   if ((e = launch_sb_scan(rs.rcnt, rs.roff, regions, st)) != cudaSuccess) return e;
-  k_rr_scatter<<<grid, kThreads, 0, st>>>(t, rs.roff, rs.rfill, rs.pairs);
+  k_rr_scatter<<<grid, kThreads, 0, st>>>(t, rs.roff, rs.rfill, rs.pairs, merge);
   const int bgrid = (int)std::min<unsigned long long>(regions, (unsigned long long)(2 * num_sms));
-  k_rr_build<<<bgrid, kRegionThreads, smem, st>>>(t, rs.roff, rs.pairs, rs.over, rs.over_n, regions);
-  k_rr_overflow<<<std::max(1, num_sms), kThreads, 0, st>>>(t, rs.over, rs.over_n);
+  k_rr_build<<<bgrid, kRegionThreads, smem, st>>>(t, rs.roff, rs.pairs, rs.over, rs.over_n, regions, merge);
+  k_rr_overflow<<<std::max(1, num_sms), kThreads, 0, st>>>(t, rs.over, rs.over_n, merge);
   return cudaGetLastError();
 }
 

@@ -85,6 +85,7 @@ struct Arrays {
   double* sigma = nullptr;
   Slot* slots = nullptr;
   unsigned int* filt = nullptr;  // one 32-bit word per 4 slots
+  bool slots_clean = false;      // the slot array is known to be all empty
   void release() {
     dfree(filt);
     dfree(keys);
@@ -94,6 +95,7 @@ struct Arrays {
     dfree(sigma);
     dfree(slots);
     cap_n = n_slots = 0;
+    slots_clean = false;
   }
   ucc_status allocate(unsigned long long cn, unsigned long long ns) {
     release();
@@ -325,7 +327,10 @@ unsigned long long slots_for(unsigned long long cap_n) {
 
 // Tables whose hash is built by regions: one-word keys and at least 2^20
 // slots.  Their slot arrays need no clearing (every slot is written).
-bool regions_ok(const ucc_ctx* c, unsigned long long n_slots) { return !c->wide && n_slots >= (1ull << 20); }
+bool regions_ok(const ucc_ctx* c, unsigned long long n_slots) {
+  if (c->wide || c->opt.rebuild_test_regions == 1) return false;
+  return n_slots >= (c->opt.rebuild_test_regions == 2 ? (1ull << kRegionBits) : (1ull << 20));
+}
 
 // Scratch of the region build for a table of cap entries and n_slots slots.
 ucc_status ensure_rehash_scratch(ucc_ctx* c, unsigned long long cap, unsigned long long n_slots) {
@@ -392,7 +397,10 @@ ucc_status prepare_spare(ucc_ctx* c, TableSet& s, unsigned long long new_cap, Ta
   to.cap_n = new_cap;
   CUDA_TRY(cudaMemsetAsync(&s.d_cnt->new_n, 0, sizeof(unsigned long long), c->stream));
   if (!cleared) {
-    if (!regions_ok(c, ns)) CUDA_TRY(cudaMemsetAsync(to.slots, 0, ns * sizeof(SlotT<KT>), c->stream));
+    if (!regions_ok(c, ns)) {
+      CUDA_TRY(cudaMemsetAsync(to.slots, 0, ns * sizeof(SlotT<KT>), c->stream));
+      s.spare.slots_clean = true;
+    }
     CUDA_TRY(cudaMemsetAsync(to.filt, 0, ns / 4 * sizeof(unsigned int), c->stream));
   }
   *out = to;
@@ -405,8 +413,10 @@ ucc_status clear_spare_async(ucc_ctx* c, TableSet& s) {
   if (!c->side || s.spare.cap_n == 0) return UCC_OK;
   CUDA_TRY(cudaEventRecord(s.clean, c->stream));
   CUDA_TRY(cudaStreamWaitEvent(c->side, s.clean, 0));
-  if (!regions_ok(c, s.spare.n_slots))
+  if (!regions_ok(c, s.spare.n_slots)) {
     CUDA_TRY(cudaMemsetAsync(s.spare.slots, 0, s.spare.n_slots * s.spare.kw * sizeof(Slot), c->side));
+    s.spare.slots_clean = true;
+  }
   CUDA_TRY(cudaMemsetAsync(s.spare.filt, 0, s.spare.n_slots / 4 * sizeof(unsigned int), c->side));
   CUDA_TRY(cudaEventRecord(s.clean, c->side));
   s.clean_pending = true;
@@ -434,18 +444,21 @@ ucc_status finish_rebuild(ucc_ctx* c, TableSet& s, const TableT<KT>& to, unsigne
         c->launches += 5;
         by_regions = true;
       } else {
-        cudaGetLastError();  // a failed scratch allocation: the direct rehash needs a cleared slot array
-        CUDA_TRY(cudaMemsetAsync(to.slots, 0, ns * sizeof(SlotT<KT>), c->stream));
+        cudaGetLastError();  // a failed scratch allocation: the direct rehash below
       }
     }
   }
   if (!by_regions) {
+    // the direct rehash claims slots in a cleared array
+    if (!s.spare.slots_clean) CUDA_TRY(cudaMemsetAsync(to.slots, 0, ns * sizeof(SlotT<KT>), c->stream));
     CUDA_TRY(launch_rehash(to, grid, c->stream));
     c->launches++;
   }
   CUDA_TRY(launch_finish_rebuild(to, expect, c->stream));
   c->launches += 1;
   std::swap(s.cur, s.spare);
+  s.cur.slots_clean = false;  // the live hash
+  s.spare.slots_clean = false;  // the previous live hash, until cleared
   // After growth the old, smaller arrays are not reused: free them now.
   if (s.spare.cap_n != s.cur.cap_n)
     s.spare.release();
@@ -1092,8 +1105,16 @@ ucc_status reverse_segment(ucc_ctx* c, TableSet& s, int k0, int k1) {
     }
     if (rec) {
       const int g2 = (int)std::min<unsigned long long>((unsigned long long)grid_full, (rec + 255) / 256);
+      // A bulk re-insertion of at least one record per eight slots (a cut's
+      // records) into a large one-word table is hashed region by region: the
+      // regions are read and written whole, which beats one random claim per
+      // record only when most regions receive many records.
+      const bool by_regions = (8 * rec >= s.cur.n_slots || c->opt.rebuild_test_regions == 2) &&
+                              regions_ok(c, s.cur.n_slots) &&
+                              ensure_rehash_scratch(c, s.cur.cap_n, s.cur.n_slots) == UCC_OK;
+      if (!by_regions) cudaGetLastError();
       CUDA_TRY(launch_tape_reinsert(c->template table<KT>(s), c->template tape<KT>(), k, rec, std::max(g2, 1),
-                                    c->stream, &c->launches));
+                                    c->stream, &c->launches, by_regions ? &c->rs : nullptr, c->num_sms));
     }
     CUDA_TRY(launch_reverse(c->template table<KT>(s), c->template dfactors<KT>(), k, stamp, c->d_grad,
                             pick_probe_width(c), grid, c->stream));
@@ -1445,6 +1466,8 @@ ucc_status batch_persistent(const std::vector<int>& idx, ucc_ctx* const* jobs, d
       const unsigned long long ns = slots_for(cap);
       TableSet& ts = c->ts[0];
       UCC_TRY(settle_spare(c, ts));  // the kernels use the spare arrays directly
+      ts.cur.slots_clean = false;     // ... and write both slot arrays
+      ts.spare.slots_clean = false;
       if (ts.cur.cap_n != cap || ts.cur.n_slots != ns) UCC_TRY(ts.cur.allocate(cap, ns));
       if (ts.spare.cap_n != cap || ts.spare.n_slots != ns) UCC_TRY(ts.spare.allocate(cap, ns));
       c->main = 0;
@@ -1785,6 +1808,8 @@ ucc_status ucc_set_options(ucc_ctx* c, const ucc_options* opt) {
       o.energy_test_partitions > (1 << 24))
     return fail(UCC_EINVAL, "energy_test_partitions must be 0 or a power of two up to 2^24");
   if (o.energy_test_buffer_records < 0) return fail(UCC_EINVAL, "negative option");
+  if (o.rebuild_test_regions < 0 || o.rebuild_test_regions > 2)
+    return fail(UCC_EINVAL, "rebuild_test_regions must be 0, 1 or 2");
   c->opt = o;
   return UCC_OK;
 }

@@ -272,10 +272,12 @@ struct RehashScratch {
 };
 // Hash the first new_n entries of t (a cleared slot array is not needed: every
 // slot is written) by regions: count, prefix sum, bucket, build each region in
-// shared memory, then claim slots for the overflow.  Needs
-// t.slot_mask + 1 >= 2^kRegionBits and scratch for t.cap_n entries.
+// shared memory, then claim slots for the overflow.  With merge, hash instead
+// the entries appended since k_mark_tail into the existing hash (insert if
+// absent).  Needs t.slot_mask + 1 >= 2^kRegionBits and scratch for t.cap_n
+// entries.
 cudaError_t launch_rehash_regions(const TableT<unsigned long long>& t, const RehashScratch& rs, int grid,
-                                  int num_sms, cudaStream_t st);
+                                  int num_sms, cudaStream_t st, bool merge = false);
 template <class KT>
 cudaError_t launch_finish_rebuild(const TableT<KT>& t, unsigned long long expect, cudaStream_t st);
 template <class KT>
@@ -304,9 +306,12 @@ cudaError_t launch_sb_finish(const TableT<KT>& t, const Integrals& in, int grid,
 size_t sb_record_bytes(int key_words);
 int sb_blocks_per_sm(int key_words);
 int sb_partition_target();  // mean records per partition the host aims for
+// rs (may be null): scratch of a hash build by regions, used to hash a bulk
+// re-insertion's appended range into a large one-word table.
 template <class KT>
 cudaError_t launch_tape_reinsert(const TableT<KT>& t, const TapeT<KT>& tape, int k, unsigned long long records,
-                                 int grid, cudaStream_t st, long long* launches);
+                                 int grid, cudaStream_t st, long long* launches, const RehashScratch* rs = nullptr,
+                                 int num_sms = 0);
 template <class KT>
 cudaError_t launch_reverse(const TableT<KT>& t, const FactorT<KT>* factors, int k, unsigned int stamp, double* grad,
                            int probe_width, int grid, cudaStream_t st);

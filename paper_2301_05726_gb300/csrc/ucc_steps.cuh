@@ -113,6 +113,25 @@ __device__ __forceinline__ void link_appended(const TableT<KT>& t, KT key, unsig
   raise_error(t.cnt, ERR_PROBE_BOUND);
 }
 
+// link_appended from slot `start` on (the hash's probe sequence for key passes
+// through start with every slot before it full).
+template <class KT>
+__device__ __forceinline__ void link_from_slot(const TableT<KT>& t, KT key, unsigned long long idx,
+                                               unsigned long long start) {
+  unsigned long long h = start & t.slot_mask;
+  for (int step = 0; step < MAX_PROBE; ++step) {
+    const KT prev = key_cas(&t.slots[h].key, KeyOps<KT>::zero(), key);
+    if (KeyOps<KT>::is_zero(prev)) {
+      t.slots[h].idx = idx;
+      filter_add(t, key);
+      return;
+    }
+    if (prev == key) return;
+    h = (h + 1) & t.slot_mask;
+  }
+  raise_error(t.cnt, ERR_PROBE_BOUND);
+}
+
 // DEFER: created entries are appended unlinked (link_appended runs after the
 // step); otherwise they are hashed at once.
 template <bool RECORD, bool DEFER = false, class KT>
