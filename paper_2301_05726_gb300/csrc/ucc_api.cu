@@ -325,11 +325,16 @@ unsigned long long slots_for(unsigned long long cap_n) {
   return next_pow2(std::max<unsigned long long>(64, (cap_n * 4 + 2) / 3));
 }
 
-// Tables whose hash is built by regions: one-word keys and at least 2^20
-// slots.  Their slot arrays need no clearing (every slot is written).
-bool regions_ok(const ucc_ctx* c, unsigned long long n_slots) {
+// Whether a hash of n_slots slots receiving `entries` keys is built region by
+// region: one-word keys, at least 2^20 slots, and the entries filling at least
+// a quarter of the slots (a region build writes every slot, a direct rehash
+// claims one random slot per entry; on the 64-so workload's 2^25-slot table
+// with 6.25e6 entries after a cut the direct rehash is faster).  entries =
+// ~0 when not known: direct.  The test option forces either way.
+bool regions_ok(const ucc_ctx* c, unsigned long long n_slots, unsigned long long entries) {
   if (c->wide || c->opt.rebuild_test_regions == 1) return false;
-  return n_slots >= (c->opt.rebuild_test_regions == 2 ? (1ull << kRegionBits) : (1ull << 20));
+  if (c->opt.rebuild_test_regions == 2) return n_slots >= (1ull << kRegionBits);
+  return n_slots >= (1ull << 20) && entries != ~0ull && 4 * entries >= n_slots;
 }
 
 // Scratch of the region build for a table of cap entries and n_slots slots.
@@ -397,11 +402,9 @@ ucc_status prepare_spare(ucc_ctx* c, TableSet& s, unsigned long long new_cap, Ta
   to.cap_n = new_cap;
   CUDA_TRY(cudaMemsetAsync(&s.d_cnt->new_n, 0, sizeof(unsigned long long), c->stream));
   if (!cleared) {
-    if (!regions_ok(c, ns)) {
-      CUDA_TRY(cudaMemsetAsync(to.slots, 0, ns * sizeof(SlotT<KT>), c->stream));
-      s.spare.slots_clean = true;
-    }
+    CUDA_TRY(cudaMemsetAsync(to.slots, 0, ns * sizeof(SlotT<KT>), c->stream));
     CUDA_TRY(cudaMemsetAsync(to.filt, 0, ns / 4 * sizeof(unsigned int), c->stream));
+    s.spare.slots_clean = true;
   }
   *out = to;
   return UCC_OK;
@@ -413,10 +416,8 @@ ucc_status clear_spare_async(ucc_ctx* c, TableSet& s) {
   if (!c->side || s.spare.cap_n == 0) return UCC_OK;
   CUDA_TRY(cudaEventRecord(s.clean, c->stream));
   CUDA_TRY(cudaStreamWaitEvent(c->side, s.clean, 0));
-  if (!regions_ok(c, s.spare.n_slots)) {
-    CUDA_TRY(cudaMemsetAsync(s.spare.slots, 0, s.spare.n_slots * s.spare.kw * sizeof(Slot), c->side));
-    s.spare.slots_clean = true;
-  }
+  CUDA_TRY(cudaMemsetAsync(s.spare.slots, 0, s.spare.n_slots * s.spare.kw * sizeof(Slot), c->side));
+  s.spare.slots_clean = true;
   CUDA_TRY(cudaMemsetAsync(s.spare.filt, 0, s.spare.n_slots / 4 * sizeof(unsigned int), c->side));
   CUDA_TRY(cudaEventRecord(s.clean, c->side));
   s.clean_pending = true;
@@ -433,12 +434,13 @@ ucc_status settle_spare(ucc_ctx* c, TableSet& s) {
 
 // Hash the compacted spare arrays `to` and make them the current ones.
 template <class KT>
-ucc_status finish_rebuild(ucc_ctx* c, TableSet& s, const TableT<KT>& to, unsigned long long expect = ~0ull) {
+ucc_status finish_rebuild(ucc_ctx* c, TableSet& s, const TableT<KT>& to, unsigned long long expect = ~0ull,
+                          unsigned long long entries = ~0ull) {
   const int grid = c->full_grid();
   const unsigned long long ns = to.slot_mask + 1ull;
   bool by_regions = false;
   if constexpr (sizeof(KT) == 8) {
-    if (regions_ok(c, ns)) {
+    if (regions_ok(c, ns, entries)) {
       if (ensure_rehash_scratch(c, to.cap_n, ns) == UCC_OK) {
         CUDA_TRY(launch_rehash_regions(to, c->rs, grid, c->num_sms, c->stream));
         c->launches += 5;
@@ -513,14 +515,16 @@ ucc_status timed_end(ucc_ctx* c, double* acc) {
   return UCC_OK;
 }
 
+// entries: the live entries the compaction keeps, when the host knows them.
 template <class KT>
-ucc_status rebuild(ucc_ctx* c, TableSet& s, unsigned long long new_cap, bool with_lam = false) {
+ucc_status rebuild(ucc_ctx* c, TableSet& s, unsigned long long new_cap, bool with_lam = false,
+                   unsigned long long entries = ~0ull) {
   TableT<KT> to;
   UCC_TRY(timed_begin(c));
   UCC_TRY(prepare_spare(c, s, new_cap, &to));
   CUDA_TRY(launch_compact(c->template table<KT>(s), to, with_lam ? 2 : 1, c->full_grid(), c->stream));
   c->launches++;
-  UCC_TRY(finish_rebuild(c, s, to));
+  UCC_TRY(finish_rebuild(c, s, to, ~0ull, entries));
   return timed_end(c, &c->stats.rebuild_ms);
 }
 
@@ -540,7 +544,7 @@ ucc_status cut_rebuild(ucc_ctx* c, TableSet& s, bool record, int k) {
                               grid, c->stream));
   c->launches++;
   // the kept count must be N_CUT (checked on the device: no round trip here)
-  UCC_TRY(finish_rebuild(c, s, to, (unsigned long long)c->opt.n_cut));
+  UCC_TRY(finish_rebuild(c, s, to, (unsigned long long)c->opt.n_cut, (unsigned long long)c->opt.n_cut));
   return timed_end(c, &c->stats.cut_ms);
 }
 
@@ -723,7 +727,7 @@ ucc_status ensure_room_known(ucc_ctx* c, TableSet& s, bool record, Counters* h) 
   if (!room || sparse) {
     unsigned long long cap = s.cur.cap_n;
     if (2 * live > cap || 8 * live > 3 * s.cur.n_slots) cap = std::max<unsigned long long>(5 * live / 2, 1 << 12);
-    UCC_TRY(rebuild<KT>(c, s, cap));
+    UCC_TRY(rebuild<KT>(c, s, cap, false, live));
     h->n_tail = live;  // a compaction keeps exactly the live entries
     h->n_dead = 0;
   }
@@ -825,7 +829,7 @@ ucc_status run_factors(ucc_ctx* c, TableSet& s, double eps, bool record, int k0,
     UCC_TRY(autotune<KT>(c, s, end, h.n_tail));
     // Compact when a quarter of the stored entries are dropped ones.
     if (h.n_dead > 4096 && h.n_dead * 4 > h.n_tail) {
-      UCC_TRY(rebuild<KT>(c, s, s.cur.cap_n));
+      UCC_TRY(rebuild<KT>(c, s, s.cur.cap_n, false, h.n_tail - h.n_dead));
       s.h_cnt->n_tail = h.n_tail - h.n_dead;  // a compaction keeps exactly the live entries
       s.h_cnt->n_dead = 0;
     }
@@ -1090,12 +1094,13 @@ ucc_status reverse_segment(ucc_ctx* c, TableSet& s, int k0, int k1) {
       CUDA_TRY(cudaEventElapsedTime(&ms, c->kev[0], c->kev[1]));
       kernel_ms += ms;
       // Live entries now: stored minus those the sweep or the forward dropped.
-      UCC_TRY(rebuild<KT>(c, s, s.cur.cap_n, true));
+      UCC_TRY(rebuild<KT>(c, s, s.cur.cap_n, true, s.h_cnt->n_tail - s.h_cnt->n_dead));
       c->stats.reverse_compactions++;
       UCC_TRY(read_counters(c, s));
       bound = s.h_cnt->n_tail;
       if (bound + rec > s.cur.cap_n || 4ull * (bound + rec) > 3ull * s.cur.n_slots) {
-        UCC_TRY(rebuild<KT>(c, s, std::max<unsigned long long>(2 * s.cur.cap_n, 2 * (bound + rec) + 64), true));
+        UCC_TRY(rebuild<KT>(c, s, std::max<unsigned long long>(2 * s.cur.cap_n, 2 * (bound + rec) + 64), true,
+                            s.h_cnt->n_tail - s.h_cnt->n_dead));
         UCC_TRY(read_counters(c, s));
         bound = s.h_cnt->n_tail;
       }
@@ -1110,7 +1115,7 @@ ucc_status reverse_segment(ucc_ctx* c, TableSet& s, int k0, int k1) {
       // regions are read and written whole, which beats one random claim per
       // record only when most regions receive many records.
       const bool by_regions = (8 * rec >= s.cur.n_slots || c->opt.rebuild_test_regions == 2) &&
-                              regions_ok(c, s.cur.n_slots) &&
+                              regions_ok(c, s.cur.n_slots, s.cur.n_slots) &&
                               ensure_rehash_scratch(c, s.cur.cap_n, s.cur.n_slots) == UCC_OK;
       if (!by_regions) cudaGetLastError();
       CUDA_TRY(launch_tape_reinsert(c->template table<KT>(s), c->template tape<KT>(), k, rec, std::max(g2, 1),
