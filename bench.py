@@ -636,7 +636,11 @@ def run_ours(args, prob):
                      "reverse_incl_recompute": tot["reverse_ms"] / n_steps,
                      "forward_kernels": tot["forward_kernel_ms"] / n_steps,
                      "reverse_kernels": tot["reverse_kernel_ms"] / n_steps,
-                     "cuts": tot["cut_ms"] / n_steps, "other_rebuilds": tot["rebuild_ms"] / n_steps},
+                     "cuts": tot["cut_ms"] / n_steps, "other_rebuilds": tot["rebuild_ms"] / n_steps,
+                     # the step minus the device time of every library kernel inside it (the factor
+                     # steps, energy, cuts and rebuilds): host round trips and launch gaps
+                     "host_gaps": (ms - (tot["forward_kernel_ms"] + tot["energy_ms"] + tot["reverse_kernel_ms"]
+                                         + tot["cut_ms"] + tot["rebuild_ms"]) / n_steps)},
         "vs_plain": plain,
         "n1_40so": n1,
         "batched": batched,
