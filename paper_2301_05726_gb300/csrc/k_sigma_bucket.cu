@@ -161,12 +161,24 @@ __device__ __forceinline__ bool pair_element(const Integrals& in, KT K, unsigned
   if ((unsigned int)q == kSingle) {
     double v = h_so(in, r, p);
     for_each_bit(K, 0, [&](int k) { v += anti(in, r, k, p, k); });
-    *h = single_parity(K | Ko::bit(p), p, r) ? -v : v;
+    *h = neg_if(v, single_parity(K | Ko::bit(p), p, r));
     return true;
   }
   if (p == r || p == s || q == r || q == s) return false;
-  const double v = anti(in, r, s, p, q);
-  *h = double_parity(K | Ko::bit(p) | Ko::bit(q), p, q, r, s) ? -v : v;
+  // <rs||pq> = (rp|sq) [spins of r, p and of s, q agree] - (rq|sp) [spins of
+  // r, q and of s, p agree]: one term for opposite spins, two for equal ones.
+  // FP64 is a narrow pipe on this GPU, so the zero start, the negations and
+  // the sign are not FP64 operations (same values as anti()).
+  const bool t1 = ((r ^ p) & 1) == 0 && ((s ^ q) & 1) == 0;
+  const bool t2 = ((r ^ q) & 1) == 0 && ((s ^ p) & 1) == 0;
+  double v = 0.0;
+  if (t1 && t2)
+    v = __dsub_rn(chem(in, r >> 1, p >> 1, s >> 1, q >> 1), chem(in, r >> 1, q >> 1, s >> 1, p >> 1));
+  else if (t1)
+    v = chem(in, r >> 1, p >> 1, s >> 1, q >> 1);
+  else if (t2)
+    v = neg_if(chem(in, r >> 1, q >> 1, s >> 1, p >> 1), 1);
+  *h = neg_if(v, double_parity(K | Ko::bit(p) | Ko::bit(q), p, q, r, s));
   return true;
 }
 
@@ -189,7 +201,7 @@ __device__ unsigned long long pairs_in_global(const TableT<KT>& t, const Integra
         ++pairs;
       }
     }
-    if (acc != 0.0) atomicAdd(&t.sigma[a.i], acc);
+    if (nonzero(acc)) atomicAdd(&t.sigma[a.i], acc);
   }
   return pairs;
 }
@@ -343,7 +355,7 @@ __global__ void __launch_bounds__(kSbThreads) k_sb_pairs(TableT<KT> t, Integrals
         // the next bin holding a pair
         if (++v == u) ++v;
         if (v >= mb) {
-          if (acc != 0.0) atomicAdd(&t.sigma[si[x]], acc);
+          if (nonzero(acc)) atomicAdd(&t.sigma[si[x]], acc);
           acc = 0.0;
           if (++u >= mb) {
             if (j + 1u >= j_end) break;
@@ -359,7 +371,7 @@ __global__ void __launch_bounds__(kSbThreads) k_sb_pairs(TableT<KT> t, Integrals
           rx = sp[x];
         }
       }
-      if (acc != 0.0) atomicAdd(&t.sigma[si[x]], acc);
+      if (nonzero(acc)) atomicAdd(&t.sigma[si[x]], acc);
     }
     __syncthreads();  // shared arrays are refilled for the next partition
   }
