@@ -14,11 +14,12 @@
 // K1 group, or the determinant itself).  The diagonal is added per entry.
 // E = <psi|H|psi> / <psi|psi> (Results section) follows from sigma.
 //
-// Layout: records are 24 bytes for one-word keys (32 for two-word ones) in
-// HBM, written partition by partition in rounds whose records fit a fixed
-// buffer; a partition's records are read once into shared memory, grouped by
-// a counting sort on 11 further bits of the core's hash, and each record's
-// group is walked from shared memory.
+// Layout: records are 32 bytes (one DRAM sector, one 256-bit store) for
+// either key width in HBM, written partition by partition in rounds whose
+// records fit a fixed buffer; a partition's records are counted into bins on
+// 11 further bits of the core's hash (a core's records share a bin), placed
+// into shared memory in bin order, and the ordered pairs of every bin are
+// split evenly over the block's threads.
 
 #include "ucc_steps.cuh"
 
