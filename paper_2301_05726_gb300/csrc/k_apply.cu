@@ -450,11 +450,10 @@ cudaError_t launch_rehash(const TableT<KT>& t, int grid, cudaStream_t st) {
 cudaError_t launch_rehash_regions(const Table& t, const RehashScratch& rs, int grid, int num_sms, cudaStream_t st,
                                   bool merge) {
   constexpr size_t smem = (size_t)kRegionSlots * (sizeof(unsigned long long) + sizeof(unsigned int));
-  static bool attr = false;
-  if (!attr) {
+  {
+    // per device (the current one): set on every launch
     const cudaError_t e = cudaFuncSetAttribute(k_rr_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    attr = true;
   }
   const unsigned long long regions = (t.slot_mask + 1ull) >> kRegionBits;
   if (regions == 0 || regions > rs.regions) return cudaErrorInvalidValue;

@@ -449,15 +449,10 @@ cudaError_t launch_sb_scatter(const TableT<KT>& t, const unsigned long long* off
 }
 
 // The pairs kernel's dynamic shared memory is above the default 48 KB limit:
-// raised once per key width, before any launch or occupancy query.
+// raised (for the current device) before every launch and occupancy query.
 template <class KT>
 cudaError_t sb_allow_smem() {
-  static bool done = false;
-  if (done) return cudaSuccess;
-  const cudaError_t e =
-      cudaFuncSetAttribute(k_sb_pairs<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb_smem_bytes<KT>());
-  if (e == cudaSuccess) done = true;
-  return e;
+  return cudaFuncSetAttribute(k_sb_pairs<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb_smem_bytes<KT>());
 }
 
 template <class KT>
